@@ -1,0 +1,161 @@
+/*
+ * eddy_theta.h -- C ABI of the GB300 theta-method library for eddy-current
+ * transients, after arXiv 2407.11993 (Chiariello et al., "Modal Decomposition
+ * in Numerical Computation of Eddy Current Transients").
+ *
+ * The library integrates the discrete eddy-current system (Sec. 3.1,
+ * Eq. discrete_version_1a/b)
+ *
+ *     R I + L dI/dt + E^T phi = V_0 + V_D,      E I = i_D,
+ *     V_0 = -M di_0/dt,  V_D = -M^D di_D/dt     (Eq. induced_voltages_d/0)
+ *
+ * with the theta-method of Sec. 3.3, in one of two forms:
+ *
+ *   EC_FORM_PLAIN  Sec. 3.3.1, Eq. time_integration: Z = L_i + theta dt R_i is
+ *                  factored once, Z = C C^T, and every step does a forward and a
+ *                  backward substitution.
+ *   EC_FORM_MODAL  Sec. 3.2 (Eq. generalized_eigenvalues_discrete,
+ *                  modal_decomposition_discrete) and Sec. 3.3.2: the pencil
+ *                  L_i u = tau R_i u is solved once; every mode then follows a
+ *                  scalar theta-recurrence.
+ *
+ * Electrode constraints are eliminated as in Sec. 3.1 (Eq. current_electrodes,
+ * discrete_version_2, circuit_equations_v2): I = K I_i + E^T (E E^T)^{-1} i_D
+ * with K an orthonormal basis of ker E (built from Householder reflectors).
+ *
+ * Conventions for every entry point:
+ *   - All floating-point data are IEEE binary64 (double).
+ *   - Dense matrices are row-major with the shapes stated below; L and R are
+ *     symmetric and only their lower triangle (row >= column) is read.
+ *   - `mem` says where the caller's pointers live: EC_MEM_HOST (pageable or
+ *     pinned host memory) or EC_MEM_DEVICE (device memory on the context's
+ *     GPU).  The library copies inputs into storage it owns; the caller keeps
+ *     ownership of its buffers and may free them when the call returns.
+ *   - Work is enqueued on the context's CUDA stream.  Calls that return data
+ *     to host memory synchronise that stream; calls with device outputs do not
+ *     (use ec_sync to wait and collect errors raised inside kernels).
+ *   - Every call returns an ec_status; nothing throws across the ABI and
+ *     nothing calls exit().  A failed call leaves the context usable for
+ *     ec_destroy, and for a new ec_setup.
+ */
+#ifndef EDDY_THETA_H
+#define EDDY_THETA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define EC_API __attribute__((visibility("default")))
+#else
+#define EC_API
+#endif
+
+typedef struct ec_ctx ec_ctx;
+
+typedef enum ec_status {
+  EC_OK = 0,
+  EC_ERR_ARG = 1,          /* invalid argument (null pointer, theta outside [0,1], dt <= 0, ...) */
+  EC_ERR_SHAPE = 2,        /* inconsistent sizes */
+  EC_ERR_NOT_SPD = 3,      /* Z (plain) or R_i (modal) is not positive definite; see ec_last_info */
+  EC_ERR_RANK = 4,         /* E does not have full row rank */
+  EC_ERR_OOM = 5,          /* device allocation failed */
+  EC_ERR_CUDA = 6,         /* CUDA runtime error */
+  EC_ERR_TIMEOUT = 7,      /* a bounded inter-block wait inside a kernel gave up */
+  EC_ERR_STATE = 8,        /* call out of order (e.g. ec_run before ec_setup) */
+  EC_ERR_NOT_CONVERGED = 9,/* an iterative eigen step did not converge */
+  EC_ERR_UNSUPPORTED = 10  /* valid request this build does not implement */
+} ec_status;
+
+typedef enum ec_form { EC_FORM_PLAIN = 0, EC_FORM_MODAL = 1 } ec_form;
+typedef enum ec_mem { EC_MEM_HOST = 0, EC_MEM_DEVICE = 1 } ec_mem;
+
+typedef struct ec_config {
+  int form;               /* ec_form */
+  double theta;           /* theta of Sec. 3.3, in [0, 1] */
+  double dt;              /* time step [s], > 0 */
+  void* stream;           /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+  int device;             /* CUDA device ordinal */
+  long long spin_limit;   /* polls before a kernel-side wait gives up (EC_ERR_TIMEOUT); 0 = default */
+} ec_config;
+
+/* Wall-clock phases of the last ec_setup / ec_run, in milliseconds, measured
+ * with CUDA events on the context's stream.  Phases a form does not run are 0. */
+typedef struct ec_timing {
+  double elim_ms;         /* constraint elimination (Householder reflectors, Sec. 3.1) */
+  double factor_ms;       /* plain: Cholesky of Z (Sec. 3.3.1); modal: Cholesky of R_i */
+  double reduce_ms;       /* modal: A = C_R^{-1} L_i C_R^{-T} */
+  double tridiag_ms;      /* modal: Householder tridiagonalisation of A */
+  double eig_ms;          /* modal: tridiagonal eigensolver (reported on its own) */
+  double backtransform_ms;/* modal: U = C_R^{-T} Q S */
+  double project_ms;      /* modal: source / probe projections and per-mode coefficients */
+  double setup_ms;        /* whole ec_setup */
+  double run_ms;          /* whole last ec_run */
+  int64_t run_steps;      /* steps of the last ec_run */
+} ec_timing;
+
+/* Create a context on cfg->device.  *out receives the handle. */
+EC_API ec_status ec_create(ec_ctx** out, const ec_config* cfg);
+
+/* One-time setup (Sec. 3.3.1 for the plain form; Sec. 3.2 for the modal form).
+ *   n        number of current unknowns N (>= 1)
+ *   L, R     n x n, symmetric positive definite inductance / resistance
+ *   m, E     reduced electrode incidence, m x n (m = N_e - 1 >= 0, E may be NULL if m = 0);
+ *            Eq. definition_E.  Must have full row rank (else EC_ERR_RANK).
+ *   s, M     coil mutuals, s x n (row k is the mutual between coil k and the n unknowns);
+ *            the coils induce V_0 = -M^T di_0/dt.  M may be NULL if s = 0.
+ *   MD       electrode-source mutuals, m x n (row j: M^D column j), or NULL for zero.
+ *   p, C     probe rows, p x n; probe outputs are y = C I.  C may be NULL if p = 0.
+ * Copies every input; the caller's buffers are not retained.  Resets the state to I = 0. */
+EC_API ec_status ec_setup(ec_ctx* ctx, int64_t n, const double* L, const double* R, int64_t m,
+                          const double* E, int64_t s, const double* M, const double* MD,
+                          int64_t p, const double* C, int mem);
+
+/* Change theta and dt.  Plain form: re-forms and re-factors Z (O(N^3)).
+ * Modal form: recomputes the per-mode coefficients only (O(N)); the modes do not
+ * depend on dt (Sec. 5). */
+EC_API ec_status ec_set_step(ec_ctx* ctx, double theta, double dt);
+
+/* Advance T steps of Eq. time_integration (plain) or its modal image (modal).
+ *   src     s x (T+1) coil currents i_0 at t_k = k dt, k = 0..T (row-major; NULL if s = 0)
+ *   iD      m x (T+1) electrode currents i_D (row-major; NULL if m = 0)
+ *   probes  T x p output, row k-1 = C I^k for k = 1..T (NULL if p = 0)
+ *   snap_stride, snaps   if snap_stride > 0: (T / snap_stride) x n output, row j = I^{(j+1) stride}
+ * Starts from the current state and leaves I^T as the new state. */
+EC_API ec_status ec_run(ec_ctx* ctx, int64_t T, const double* src, const double* iD,
+                        double* probes, int64_t snap_stride, double* snaps, int mem);
+
+/* Set the state from a physical current I (length n): I_i = K^T I (the particular
+ * part is rebuilt from i_D at the next step). */
+EC_API ec_status ec_set_current(ec_ctx* ctx, const double* I, int mem);
+
+/* Internal state of length ec_state_size(): I_i (plain) or the modal amplitudes x
+ * (modal).  ec_set_state(ec_get_state()) resumes bit-identically. */
+EC_API int64_t ec_state_size(const ec_ctx* ctx);
+EC_API ec_status ec_get_state(ec_ctx* ctx, double* state, int mem);
+EC_API ec_status ec_set_state(ec_ctx* ctx, const double* state, int mem);
+
+/* Modal form only: tau (N_0, decreasing) and U (N_0 x N_0, column j = mode j,
+ * column-major, U^T R_i U = 1) in the internal basis of ker E. */
+EC_API ec_status ec_get_modes(ec_ctx* ctx, double* tau, double* U, int mem);
+
+EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
+/* Wait for the context's stream and report any error raised inside kernels. */
+EC_API ec_status ec_sync(ec_ctx* ctx);
+/* Extra information about the last error (global pivot index for EC_ERR_NOT_SPD). */
+EC_API int64_t ec_last_info(const ec_ctx* ctx);
+EC_API const char* ec_error_string(ec_status status);
+EC_API void ec_destroy(ec_ctx* ctx);
+
+/* Self-test of the bounded kernel-side wait: launches one wait on a flag that
+ * nothing sets, with at most spin_limit polls, and stores the status the kernel
+ * reported (EC_ERR_TIMEOUT when the bound works) in *code_out. */
+EC_API ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDDY_THETA_H */

@@ -1,0 +1,569 @@
+// C ABI of the theta-method library (include/eddy_theta.h): context, setup
+// and run orchestration for the plain and modal forms.
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ec_kernels.h"
+#include "ec_modal.h"
+
+using namespace ec;
+
+struct ec_ctx {
+  ec_config cfg{};
+  cudaStream_t stream = nullptr;
+  DevStatus* st = nullptr;
+  long long spin_limit = 1ll << 24;
+  int64_t n = 0, n0 = 0;
+  int m = 0, S = 0, P = 0, D = 0;
+  bool ready = false;
+  // transformed matrices Q^T L Q, Q^T R Q (full, n x n)
+  double* dL = nullptr;
+  double* dR = nullptr;
+  // plain
+  double* dZ = nullptr;      // n0 x n0 Cholesky factor of L_i + theta dt R_i
+  double* dDinv = nullptr;   // inverses of its 64 x 64 diagonal blocks
+  // elimination
+  double* dE = nullptr;
+  double* dV = nullptr;
+  double* dWR = nullptr;
+  double* dT = nullptr;
+  double* dVtWR = nullptr;
+  double* dRrinvT = nullptr;
+  double* dPE = nullptr;
+  double* dCPE = nullptr;
+  double* dRD = nullptr;     // n0 x m
+  double* dLD = nullptr;     // n0 x m
+  double* dM = nullptr;      // n x S   (Q^T M)
+  double* dMD = nullptr;     // n x m   (Q^T M^D)
+  double* dC = nullptr;      // n x P   (Q^T C^T)
+  double* dY = nullptr;      // n x m scratch
+  double* dX = nullptr;      // n x m scratch
+  double* dSm = nullptr;     // small scratch
+  double* dZm = nullptr;
+  double* dGsrc = nullptr;
+  double* dDmat = nullptr;
+  double* dIi = nullptr;
+  double* dWork = nullptr;
+  double* dDots = nullptr;
+  double* dPartial = nullptr;
+  double* dTmpN = nullptr;
+  unsigned* dCounter = nullptr;
+  int64_t* dK = nullptr;
+  Csr csr;
+  int* dFlags = nullptr;      // 2 x nblk
+  unsigned* dTickets = nullptr;
+  int* dEpoch = nullptr;
+  // run buffers
+  double* dSrc = nullptr;
+  size_t srcCap = 0;
+  double* dIDs = nullptr;
+  size_t idsCap = 0;
+  double* dProbes = nullptr;
+  size_t probesCap = 0;
+  double* dSnaps = nullptr;
+  size_t snapsCap = 0;
+  int update_grid = 1;
+  int trsv_grid = 1;
+  ec_timing tim{};
+  int64_t last_info = -1;
+  ModalState* modal = nullptr;
+};
+
+namespace {
+
+cudaError_t dev_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 8); }
+
+template <typename T>
+ec_status alloc(T** p, size_t count) {
+  if (*p) return EC_OK;
+  if (dev_alloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return EC_ERR_OOM;
+  }
+  return EC_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+ec_status grow(T** p, size_t& cap, size_t count) {
+  if (count <= cap && *p) return EC_OK;
+  dfree(*p);
+  cap = 0;
+  ec_status s = alloc(p, count);
+  if (s == EC_OK) cap = count;
+  return s;
+}
+
+void free_setup(ec_ctx* c) {
+  dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
+  dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
+  dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
+  dfree(c->dY); dfree(c->dX); dfree(c->dSm); dfree(c->dZm); dfree(c->dGsrc); dfree(c->dDmat);
+  dfree(c->dIi); dfree(c->dWork); dfree(c->dDots); dfree(c->dPartial); dfree(c->dTmpN);
+  dfree(c->dCounter); dfree(c->dK); dfree(c->csr.ptr); dfree(c->csr.col); dfree(c->csr.val);
+  c->csr.nnz = 0;
+  dfree(c->dFlags); dfree(c->dTickets); dfree(c->dEpoch);
+  if (c->modal) { modal_free(c->modal); c->modal = nullptr; }
+  c->ready = false;
+}
+
+ec_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return EC_OK;
+  if (e == cudaErrorMemoryAllocation) return EC_ERR_OOM;
+  return EC_ERR_CUDA;
+}
+
+// Synchronise and collect the first error (CUDA or kernel-side status).
+ec_status collect(ec_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  DevStatus h{};
+  e = cudaMemcpy(&h, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (h.code != 0) {
+    c->last_info = h.info;
+    return (ec_status)h.code;
+  }
+  return EC_OK;
+}
+
+ec_status copy_in(ec_ctx* c, double* dst, const double* src, size_t count, int mem) {
+  if (count == 0) return EC_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                  mem == EC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                                  c->stream);
+  return cuda_status(e);
+}
+
+ec_status copy_out(ec_ctx* c, double* dst, const double* src, size_t count, int mem) {
+  if (count == 0) return EC_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                  mem == EC_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  return cuda_status(e);
+}
+
+struct EventTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit EventTimer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop_ms() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~EventTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+#define EC_TRY(x)                      \
+  do {                                 \
+    ec_status _s = (x);                \
+    if (_s != EC_OK) return _s;        \
+  } while (0)
+
+StepArgs step_args(ec_ctx* c, int64_t T, double* probes, double* snaps, int64_t stride) {
+  StepArgs a{};
+  a.n = c->n; a.n0 = c->n0; a.m = c->m; a.S = c->S; a.P = c->P; a.D = c->D;
+  a.theta = c->cfg.theta; a.dt = c->cfg.dt;
+  a.src = c->dSrc; a.iD = c->dIDs; a.T = T; a.kstep = c->dK;
+  a.V = c->dV; a.WR = c->dWR; a.Tm = c->dT; a.VtWR = c->dVtWR; a.PE = c->dPE; a.CPE = c->dCPE;
+  a.R = c->csr; a.Gsrc = c->dGsrc; a.Dmat = c->dDmat; a.Ii = c->dIi; a.work = c->dWork;
+  a.dots = c->dDots; a.partial = c->dPartial; a.counter = c->dCounter;
+  a.probes = probes; a.snaps = snaps; a.snap_stride = stride;
+  a.tickets = c->dTickets; a.epoch = c->dEpoch; a.st = c->st;
+  return a;
+}
+
+}  // namespace
+
+namespace {
+
+ec_status form_sources(ec_ctx* c) {
+  const int64_t n0 = c->n0;
+  const int m = c->m;
+  if (m > 0) {
+    copy_matrix(c->stream, n0, m, c->dRD, n0, c->dGsrc, n0);
+    copy_matrix(c->stream, n0, m, c->dLD, n0, c->dGsrc + n0 * m, n0);
+    axpy_matrix(c->stream, n0, m, c->cfg.theta * c->cfg.dt, c->dRD, n0, c->dGsrc + n0 * m, n0);
+  }
+  if (c->S > 0) copy_matrix(c->stream, n0, c->S, c->dM + m, c->n, c->dGsrc + n0 * 2 * m, n0);
+  return EC_OK;
+}
+
+ec_status plain_factor(ec_ctx* c) {
+  const int64_t n = c->n, n0 = c->n0;
+  const int m = c->m;
+  EC_TRY(alloc(&c->dZ, (size_t)n0 * n0));
+  EC_TRY(alloc(&c->dDinv, (size_t)((n0 + NB - 1) / NB) * NB * NB));
+  EventTimer t(c->stream);
+  copy_matrix(c->stream, n0, n0, c->dL + m + m * n, n, c->dZ, n0);
+  add_lower(c->stream, n0, c->dZ, n0, c->dR + m + m * n, n, c->cfg.theta * c->cfg.dt);
+  potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st);
+  c->tim.factor_ms = t.stop_ms();
+  return collect(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ec_error_string(ec_status s) {
+  switch (s) {
+    case EC_OK: return "ok";
+    case EC_ERR_ARG: return "invalid argument";
+    case EC_ERR_SHAPE: return "inconsistent sizes";
+    case EC_ERR_NOT_SPD: return "matrix is not symmetric positive definite";
+    case EC_ERR_RANK: return "electrode operator E is rank deficient";
+    case EC_ERR_OOM: return "device out of memory";
+    case EC_ERR_CUDA: return "CUDA runtime error";
+    case EC_ERR_TIMEOUT: return "bounded kernel-side wait timed out";
+    case EC_ERR_STATE: return "call out of order";
+    case EC_ERR_NOT_CONVERGED: return "eigen iteration did not converge";
+    case EC_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
+  if (!out || !cfg) return EC_ERR_ARG;
+  *out = nullptr;
+  if (cfg->form != EC_FORM_PLAIN && cfg->form != EC_FORM_MODAL) return EC_ERR_ARG;
+  if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    return EC_ERR_CUDA;
+  }
+  ec_ctx* c = new (std::nothrow) ec_ctx();
+  if (!c) return EC_ERR_OOM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cfg->stream;
+  if (cfg->spin_limit > 0) c->spin_limit = cfg->spin_limit;
+  if (alloc(&c->st, 1) != EC_OK) {
+    delete c;
+    return EC_ERR_OOM;
+  }
+  cudaMemset(c->st, 0, sizeof(DevStatus));
+  *out = c;
+  return EC_OK;
+}
+
+void ec_destroy(ec_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  cudaStreamSynchronize(c->stream);
+  free_setup(c);
+  dfree(c->dSrc); dfree(c->dIDs); dfree(c->dProbes); dfree(c->dSnaps);
+  dfree(c->st);
+  delete c;
+}
+
+int64_t ec_last_info(const ec_ctx* c) { return c ? c->last_info : -1; }
+
+int64_t ec_state_size(const ec_ctx* c) { return (c && c->ready) ? c->n0 : 0; }
+
+ec_status ec_sync(ec_ctx* c) {
+  if (!c) return EC_ERR_ARG;
+  return collect(c);
+}
+
+ec_status ec_timings(ec_ctx* c, ec_timing* out) {
+  if (!c || !out) return EC_ERR_ARG;
+  *out = c->tim;
+  return EC_OK;
+}
+
+ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64_t m,
+                   const double* E, int64_t s, const double* M, const double* MD, int64_t p,
+                   const double* C, int mem) {
+  if (!c || n < 1 || !L || !R || m < 0 || s < 0 || p < 0) return EC_ERR_ARG;
+  if ((m > 0 && !E) || (s > 0 && !M) || (p > 0 && !C)) return EC_ERR_ARG;
+  if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
+  if (m >= n) return EC_ERR_SHAPE;
+  if (m > MAXM || s > 64 || p + 2 * m > MAXD) return EC_ERR_UNSUPPORTED;
+  cudaSetDevice(c->cfg.device);
+  free_setup(c);
+  cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+  c->last_info = -1;
+  c->tim = ec_timing{};
+  c->n = n; c->m = (int)m; c->S = (int)s; c->P = (int)p; c->n0 = n - m;
+  c->D = c->P + 2 * c->m;
+  const int64_t n0 = c->n0;
+  const size_t nn = (size_t)n * n;
+  EventTimer whole(c->stream);
+
+  EC_TRY(alloc(&c->dL, nn));
+  EC_TRY(alloc(&c->dR, nn));
+  EC_TRY(copy_in(c, c->dL, L, nn, mem));
+  EC_TRY(copy_in(c, c->dR, R, nn, mem));
+  // row-major lower triangle == column-major upper triangle
+  sym_from_upper(c->stream, n, c->dL, n);
+  sym_from_upper(c->stream, n, c->dR, n);
+  EC_TRY(alloc(&c->dM, (size_t)n * (s > 0 ? s : 1)));
+  EC_TRY(alloc(&c->dMD, (size_t)n * (m > 0 ? m : 1)));
+  EC_TRY(alloc(&c->dC, (size_t)n * (p > 0 ? p : 1)));
+  EC_TRY(copy_in(c, c->dM, M, (size_t)n * s, mem));
+  if (m > 0) {
+    if (MD) EC_TRY(copy_in(c, c->dMD, MD, (size_t)n * m, mem));
+    else cudaMemsetAsync(c->dMD, 0, sizeof(double) * n * m, c->stream);
+  }
+  EC_TRY(copy_in(c, c->dC, C, (size_t)n * p, mem));
+
+  // CSR of the original R, for the O(nnz) R_i products of the plain step
+  {
+    ec_status st = build_csr(c->stream, n, c->dR, c->csr, dev_alloc);
+    if (st != EC_OK) return st;
+  }
+
+  EventTimer te(c->stream);
+  const int mm = c->m > 0 ? c->m : 1;
+  EC_TRY(alloc(&c->dV, (size_t)n * mm));
+  EC_TRY(alloc(&c->dWR, (size_t)n * mm));
+  EC_TRY(alloc(&c->dT, (size_t)mm * mm));
+  EC_TRY(alloc(&c->dVtWR, (size_t)mm * mm));
+  EC_TRY(alloc(&c->dRrinvT, (size_t)mm * mm));
+  EC_TRY(alloc(&c->dPE, (size_t)n * mm));
+  EC_TRY(alloc(&c->dCPE, (size_t)(p > 0 ? p : 1) * mm));
+  EC_TRY(alloc(&c->dRD, (size_t)n0 * mm));
+  EC_TRY(alloc(&c->dLD, (size_t)n0 * mm));
+  if (m > 0) {
+    const int mi = c->m;
+    const int64_t wcols = (s > mi ? s : mi) > p ? (s > mi ? s : mi) : p;
+    EC_TRY(alloc(&c->dE, (size_t)n * mi));
+    EC_TRY(alloc(&c->dY, (size_t)n * mi));
+    EC_TRY(alloc(&c->dX, (size_t)n * mi));
+    EC_TRY(alloc(&c->dSm, (size_t)mi * (wcols > mi ? wcols : mi)));
+    EC_TRY(alloc(&c->dZm, (size_t)mi * (wcols > mi ? wcols : mi)));
+    EC_TRY(copy_in(c, c->dE, E, (size_t)n * mi, mem));
+    house_qr(c->stream, n, mi, c->dE, c->dV, c->dT, c->dRrinvT, c->st);
+    // WR = R V with the original R, and V^T WR
+    dgemm(c->stream, N_, N_, n, mi, n, 1.0, c->dR, n, c->dV, n, 0.0, c->dWR, n, 0, c->st);
+    dgemm(c->stream, T_, N_, mi, mi, n, 1.0, c->dV, n, c->dWR, n, 0.0, c->dVtWR, mi, 0, c->st);
+    two_sided_update(c->stream, n, mi, c->dL, c->dV, c->dT, c->dY, c->dX, c->dSm, c->dZm, c->st);
+    two_sided_update(c->stream, n, mi, c->dR, c->dV, c->dT, c->dY, c->dX, c->dSm, c->dZm, c->st);
+    one_sided_qt(c->stream, n, mi, c->dM, s, c->dV, c->dT, c->dSm, c->dZm, c->st);
+    one_sided_qt(c->stream, n, mi, c->dMD, mi, c->dV, c->dT, c->dSm, c->dZm, c->st);
+    one_sided_qt(c->stream, n, mi, c->dC, p, c->dV, c->dT, c->dSm, c->dZm, c->st);
+    // particular field PE = Q [Rr^{-T}; 0]
+    cudaMemsetAsync(c->dPE, 0, sizeof(double) * n * mi, c->stream);
+    copy_matrix(c->stream, mi, mi, c->dRrinvT, mi, c->dPE, n);
+    one_sided_q(c->stream, n, mi, c->dPE, mi, c->dV, c->dT, c->dSm, c->dZm, c->st);
+    // C PE = (C'[0:m, :])^T Rr^{-T}  (P x m)
+    if (p > 0)
+      dgemm(c->stream, T_, N_, p, mi, mi, 1.0, c->dC, n, c->dRrinvT, mi, 0.0, c->dCPE, p, 0, c->st);
+    // R_D = R'[m:, 0:m] Rr^{-T},  L_D = L'[m:, 0:m] Rr^{-T} + MD'[m:, :]
+    dgemm(c->stream, N_, N_, n0, mi, mi, 1.0, c->dR + mi, n, c->dRrinvT, mi, 0.0, c->dRD, n0, 0, c->st);
+    copy_matrix(c->stream, n0, mi, c->dMD + mi, n, c->dLD, n0);
+    dgemm(c->stream, N_, N_, n0, mi, mi, 1.0, c->dL + mi, n, c->dRrinvT, mi, 1.0, c->dLD, n0, 0, c->st);
+  }
+  c->tim.elim_ms = te.stop_ms();
+  EC_TRY(collect(c));
+
+  // source columns and dot-product rows
+  EC_TRY(alloc(&c->dGsrc, (size_t)n0 * (2 * c->m + c->S > 0 ? 2 * c->m + c->S : 1)));
+  EC_TRY(alloc(&c->dDmat, (size_t)n0 * (c->D > 0 ? c->D : 1)));
+  form_sources(c);
+  if (p > 0) copy_matrix(c->stream, n0, p, c->dC + c->m, n, c->dDmat, n0);
+  if (m > 0) {
+    copy_matrix(c->stream, n0, c->m, c->dV + c->m, n, c->dDmat + n0 * p, n0);
+    copy_matrix(c->stream, n0, c->m, c->dWR + c->m, n, c->dDmat + n0 * (p + c->m), n0);
+  }
+  // state
+  c->update_grid = (int)((n0 + 1023) / 1024);
+  if (c->update_grid > num_sms() * 2) c->update_grid = num_sms() * 2;
+  if (c->update_grid < 1) c->update_grid = 1;
+  c->trsv_grid = num_sms() * 2;
+  EC_TRY(alloc(&c->dIi, (size_t)n0));
+  EC_TRY(alloc(&c->dWork, (size_t)n0));
+  EC_TRY(alloc(&c->dTmpN, (size_t)n));
+  EC_TRY(alloc(&c->dDots, (size_t)MAXD));
+  EC_TRY(alloc(&c->dPartial, (size_t)c->update_grid * (c->D > 0 ? c->D : 1)));
+  EC_TRY(alloc(&c->dCounter, 1));
+  EC_TRY(alloc(&c->dK, 1));
+  const int64_t nblk = (n0 + NB - 1) / NB;
+  EC_TRY(alloc(&c->dFlags, (size_t)2 * nblk));
+  EC_TRY(alloc(&c->dTickets, 2));
+  EC_TRY(alloc(&c->dEpoch, 1));
+  cudaMemsetAsync(c->dIi, 0, sizeof(double) * n0, c->stream);
+  cudaMemsetAsync(c->dDots, 0, sizeof(double) * MAXD, c->stream);
+  cudaMemsetAsync(c->dCounter, 0, sizeof(unsigned), c->stream);
+  cudaMemsetAsync(c->dK, 0, sizeof(int64_t), c->stream);
+  cudaMemsetAsync(c->dFlags, 0, sizeof(int) * 2 * nblk, c->stream);
+  cudaMemsetAsync(c->dTickets, 0, sizeof(unsigned) * 2, c->stream);
+  cudaMemsetAsync(c->dEpoch, 0, sizeof(int), c->stream);
+  EC_TRY(collect(c));
+
+  if (c->cfg.form == EC_FORM_PLAIN) {
+    EC_TRY(plain_factor(c));
+  } else {
+    c->modal = modal_create();
+    if (!c->modal) return EC_ERR_OOM;
+    ModalSetupArgs ma{};
+    ma.n = n; ma.n0 = n0; ma.m = c->m; ma.S = c->S; ma.P = c->P;
+    ma.Li = c->dL + c->m + c->m * n; ma.Ri = c->dR + c->m + c->m * n; ma.ld = n;
+    ma.Gsrc = c->dGsrc; ma.RD = c->dRD; ma.LD = c->dLD; ma.Msrc = c->dM + c->m; ma.ldM = n;
+    ma.CK = c->dC + c->m; ma.ldC = n;
+    ma.theta = c->cfg.theta; ma.dt = c->cfg.dt;
+    ma.st = c->st;
+    EC_TRY(modal_setup(c->stream, c->modal, ma, &c->tim));
+    EC_TRY(collect(c));
+  }
+  c->tim.setup_ms = whole.stop_ms();
+  c->ready = true;
+  return EC_OK;
+}
+
+ec_status ec_set_step(ec_ctx* c, double theta, double dt) {
+  if (!c) return EC_ERR_ARG;
+  if (!(theta >= 0.0 && theta <= 1.0) || !(dt > 0.0)) return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  c->cfg.theta = theta;
+  c->cfg.dt = dt;
+  form_sources(c);
+  if (c->cfg.form == EC_FORM_PLAIN) return plain_factor(c);
+  EC_TRY(modal_set_step(c->stream, c->modal, theta, dt));
+  return collect(c);
+}
+
+ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, double* probes,
+                 int64_t stride, double* snaps, int mem) {
+  if (!c) return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  if (T < 0 || stride < 0) return EC_ERR_ARG;
+  if ((c->S > 0 && !src) || (c->m > 0 && !iD)) return EC_ERR_ARG;
+  if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
+  cudaSetDevice(c->cfg.device);
+  if (T == 0) return EC_OK;
+  const int64_t n = c->n;
+  const int64_t nsnap = (stride > 0 && snaps) ? T / stride : 0;
+  EC_TRY(grow(&c->dSrc, c->srcCap, (size_t)(c->S > 0 ? c->S : 1) * (T + 1)));
+  EC_TRY(grow(&c->dIDs, c->idsCap, (size_t)(c->m > 0 ? c->m : 1) * (T + 1)));
+  EC_TRY(copy_in(c, c->dSrc, src, (size_t)c->S * (T + 1), mem));
+  EC_TRY(copy_in(c, c->dIDs, iD, (size_t)c->m * (T + 1), mem));
+  double* outP = nullptr;
+  double* outS = nullptr;
+  if (probes && c->P > 0) {
+    if (mem == EC_MEM_DEVICE) outP = probes;
+    else {
+      EC_TRY(grow(&c->dProbes, c->probesCap, (size_t)T * c->P));
+      outP = c->dProbes;
+    }
+  }
+  if (nsnap > 0) {
+    if (mem == EC_MEM_DEVICE) outS = snaps;
+    else {
+      EC_TRY(grow(&c->dSnaps, c->snapsCap, (size_t)nsnap * n));
+      outS = c->dSnaps;
+    }
+  }
+  cudaMemsetAsync(c->dK, 0, sizeof(int64_t), c->stream);
+  StepArgs a = step_args(c, T, outP, outS, nsnap > 0 ? stride : 0);
+  EventTimer t(c->stream);
+  if (c->cfg.form == EC_FORM_PLAIN) {
+    TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
+    for (int64_t k = 0; k < T; ++k) {
+      plain_rhs(c->stream, a);
+      trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
+                c->trsv_grid, c->spin_limit, c->st);
+      plain_update(c->stream, a, c->update_grid, 0);
+      if (outS) plain_snapshot(c->stream, a);
+    }
+  } else {
+    EC_TRY(modal_run(c->stream, c->modal, a));
+  }
+  c->tim.run_ms = t.stop_ms();
+  c->tim.run_steps = T;
+  EC_TRY(collect(c));
+  if (outP && outP != probes) EC_TRY(copy_out(c, probes, outP, (size_t)T * c->P, mem));
+  if (outS && outS != snaps) EC_TRY(copy_out(c, snaps, outS, (size_t)nsnap * n, mem));
+  return collect(c);
+}
+
+ec_status ec_get_state(ec_ctx* c, double* state, int mem) {
+  if (!c || !state) return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  const double* src = c->cfg.form == EC_FORM_PLAIN ? c->dIi : modal_state(c->modal);
+  EC_TRY(copy_out(c, state, src, (size_t)c->n0, mem));
+  return collect(c);
+}
+
+ec_status ec_set_state(ec_ctx* c, const double* state, int mem) {
+  if (!c || !state) return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  if (c->cfg.form == EC_FORM_PLAIN) {
+    EC_TRY(copy_in(c, c->dIi, state, (size_t)c->n0, mem));
+    StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
+    plain_update(c->stream, a, c->update_grid, 1);
+  } else {
+    EC_TRY(copy_in(c, modal_state(c->modal), state, (size_t)c->n0, mem));
+  }
+  return collect(c);
+}
+
+ec_status ec_set_current(ec_ctx* c, const double* I, int mem) {
+  if (!c || !I) return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  EC_TRY(copy_in(c, c->dTmpN, I, (size_t)c->n, mem));
+  if (c->m > 0)
+    one_sided_qt(c->stream, c->n, c->m, c->dTmpN, 1, c->dV, c->dT, c->dSm, c->dZm, c->st);
+  if (c->cfg.form == EC_FORM_PLAIN) {
+    copy_matrix(c->stream, c->n0, 1, c->dTmpN + c->m, c->n, c->dIi, c->n0);
+    StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
+    plain_update(c->stream, a, c->update_grid, 1);
+  } else {
+    modal_set_internal_current(c->stream, c->modal, c->dTmpN + c->m);
+  }
+  return collect(c);
+}
+
+ec_status ec_get_modes(ec_ctx* c, double* tau, double* U, int mem) {
+  if (!c) return EC_ERR_ARG;
+  if (!c->ready || c->cfg.form != EC_FORM_MODAL) return EC_ERR_STATE;
+  if (tau) EC_TRY(copy_out(c, tau, modal_tau(c->modal), (size_t)c->n0, mem));
+  if (U) EC_TRY(copy_out(c, U, modal_U(c->modal), (size_t)c->n0 * c->n0, mem));
+  return collect(c);
+}
+
+ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {
+  if (!code_out || spin_limit < 1) return EC_ERR_ARG;
+  DevStatus* st = nullptr;
+  int* flag = nullptr;
+  if (dev_alloc((void**)&st, sizeof(DevStatus)) != cudaSuccess) return EC_ERR_OOM;
+  if (dev_alloc((void**)&flag, sizeof(int)) != cudaSuccess) {
+    cudaFree(st);
+    return EC_ERR_OOM;
+  }
+  cudaMemset(st, 0, sizeof(DevStatus));
+  cudaMemset(flag, 0, sizeof(int));
+  wait_timeout_probe(0, flag, spin_limit, st);
+  cudaError_t e = cudaDeviceSynchronize();
+  DevStatus h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(st);
+  cudaFree(flag);
+  if (e != cudaSuccess) return cuda_status(e);
+  *code_out = h.code;
+  return EC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,353 @@
+// FP64 dense kernels: a register-tiled GEMM and the blocked Cholesky /
+// triangular-solve drivers built on it.  All matrices are column-major.
+//
+// On GB300 the FP64 pipe retires about two DFMA per SM per clock (1.2 TFLOP/s
+// for the GPU), so every FP64 contraction here is arithmetic-bound: a 64 x 64
+// output tile with a 16-deep shared-memory stage reads 2 x 8 KB per 16 K of
+// DFMA work, far below what HBM or L2 deliver.  The design goal is simply to
+// keep the DFMA pipe busy: 16 independent accumulators per thread and a
+// register prefetch of the next K chunk while the current one is consumed.
+
+#include <cmath>
+#include <cstdio>
+
+#include "ec_internal.h"
+
+namespace ec {
+
+namespace {
+
+__device__ __forceinline__ bool failed(const DevStatus* st) {
+  return st != nullptr && *(volatile const int*)&st->code != 0;
+}
+
+// Lower-triangle tile enumeration: t -> (i, j) with i >= j.
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t& i, int64_t& j) {
+  int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  i = r;
+  j = t - r * (r + 1) / 2;
+}
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                    const double* A, int64_t lda, const double* B,
+                                                    int64_t ldb, double beta, double* C,
+                                                    int64_t ldc, int tri, const DevStatus* st) {
+  if (failed(st)) return;
+  int64_t tm, tn;
+  if (tri) {
+    tri_tile(blockIdx.x, tm, tn);
+  } else {
+    tm = blockIdx.x;
+    tn = blockIdx.y;
+  }
+  const int64_t row0 = tm * GEMM_TILE, col0 = tn * GEMM_TILE;
+  __shared__ double As[GEMM_KC][GEMM_TILE + 1];
+  __shared__ double Bs[GEMM_KC][GEMM_TILE + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  double ra[4], rb[4];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q;
+      int r, kk;
+      if (TA == 0) { r = idx & 63; kk = idx >> 6; } else { r = idx >> 4; kk = idx & 15; }
+      int64_t gr = row0 + r, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < M && gk < K) v = (TA == 0) ? A[gr + gk * lda] : A[gk + gr * lda];
+      ra[q] = v;
+      int c;
+      if (TB == 0) { kk = idx & 15; c = idx >> 4; } else { c = idx & 63; kk = idx >> 6; }
+      int64_t gc = col0 + c;
+      gk = k0 + kk;
+      v = 0.0;
+      if (gc < N && gk < K) v = (TB == 0) ? B[gk + gc * ldb] : B[gc + gk * ldb];
+      rb[q] = v;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q;
+      int r, kk, c;
+      if (TA == 0) { r = idx & 63; kk = idx >> 6; } else { r = idx >> 4; kk = idx & 15; }
+      As[kk][r] = ra[q];
+      if (TB == 0) { kk = idx & 15; c = idx >> 4; } else { c = idx & 63; kk = idx >> 6; }
+      Bs[kk][c] = rb[q];
+    }
+  };
+
+  if (K > 0) load(0);
+  for (int64_t k0 = 0; k0 < K; k0 += GEMM_KC) {
+    stash();
+    __syncthreads();
+    if (k0 + GEMM_KC < K) load(k0 + GEMM_KC);
+#pragma unroll
+    for (int kk = 0; kk < GEMM_KC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int64_t gc = col0 + ty + 16 * j;
+    if (gc >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int64_t gr = row0 + tx + 16 * i;
+      if (gr >= M || (tri && gr < gc)) continue;
+      double* p = C + gr + gc * ldc;
+      double v = alpha * acc[i][j];
+      if (beta != 0.0) v = fma(beta, *p, v);
+      *p = v;
+    }
+  }
+}
+
+// Cholesky of one diagonal block (kb <= 64) in shared memory, plus the inverse
+// of the resulting lower-triangular factor.  One CTA of 256 threads.
+__global__ void __launch_bounds__(256) potf2_diag_kernel(double* A, int64_t lda, int kb,
+                                                         double* Dinv, DevStatus* st,
+                                                         int64_t gk) {
+  if (failed(st)) return;
+  extern __shared__ double sm[];
+  double* S = sm;                 // S[c * 65 + r] = L(r, c)
+  double* X = sm + 64 * 65;       // X[c * 65 + r] = Linv(r, c)
+  __shared__ int bad;
+  __shared__ double rpiv;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    int r = idx % kb, c = idx / kb;
+    S[c * 65 + r] = (r >= c) ? A[r + (int64_t)c * lda] : 0.0;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      double d = S[j * 65 + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        if (atomicCAS(&st->code, 0, (int)EC_ERR_NOT_SPD) == 0) st->info = (int)(gk + j);
+      } else {
+        double p = sqrt(d);
+        S[j * 65 + j] = p;
+        rpiv = 1.0 / p;
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    for (int r = j + 1 + tid; r < kb; r += blockDim.x) S[j * 65 + r] *= rpiv;
+    __syncthreads();
+    const int n2 = kb - j - 1;
+    for (int idx = tid; idx < n2 * n2; idx += blockDim.x) {
+      int c = j + 1 + idx / n2, r = j + 1 + idx % n2;
+      if (r >= c) S[c * 65 + r] = fma(-S[j * 65 + r], S[j * 65 + c], S[c * 65 + r]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
+    int r = idx % kb, c = idx / kb;
+    if (r >= c) A[r + (int64_t)c * lda] = S[c * 65 + r];
+  }
+  // Inverse by forward substitution, one column per thread.
+  if (tid < kb) {
+    const int c = tid;
+    for (int r = 0; r < c; ++r) X[c * 65 + r] = 0.0;
+    X[c * 65 + c] = 1.0 / S[c * 65 + c];
+    for (int r = c + 1; r < kb; ++r) {
+      double s0 = 0.0, s1 = 0.0;
+      int k = c;
+      for (; k + 1 < r; k += 2) {
+        s0 = fma(S[k * 65 + r], X[c * 65 + k], s0);
+        s1 = fma(S[(k + 1) * 65 + r], X[c * 65 + k + 1], s1);
+      }
+      if (k < r) s0 = fma(S[k * 65 + r], X[c * 65 + k], s0);
+      X[c * 65 + r] = -(s0 + s1) / S[r * 65 + r];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    int r = idx % NB, c = idx / NB;
+    Dinv[idx] = (r < kb && c < kb && r >= c) ? X[c * 65 + r] : 0.0;
+  }
+}
+
+__global__ void symmetrize_kernel(int64_t n, double* A, int64_t lda) {
+  int64_t c = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < n && c < n && r < c) A[r + c * lda] = A[c + r * lda];
+}
+
+__global__ void add_lower_kernel(int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
+                                 double alpha) {
+  for (int64_t c = blockIdx.y; c < n; c += gridDim.y)
+    for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+      A[r + c * lda] = fma(alpha, B[r + c * ldb], A[r + c * lda]);
+}
+
+__global__ void copy_kernel(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                            int64_t ldb) {
+  for (int64_t c = blockIdx.y; c < n; c += gridDim.y)
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x)
+      B[r + c * ldb] = A[r + c * lda];
+}
+
+__global__ void axpy_kernel(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                            double* B, int64_t ldb) {
+  for (int64_t c = blockIdx.y; c < n; c += gridDim.y)
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+         r += (int64_t)gridDim.x * blockDim.x)
+      B[r + c * ldb] = fma(alpha, A[r + c * lda], B[r + c * ldb]);
+}
+
+}  // namespace
+
+void axpy_matrix(cudaStream_t s, int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                 double* B, int64_t ldb) {
+  if (m <= 0 || n <= 0) return;
+  dim3 grid((unsigned)((m + 255) / 256 < 64 ? (m + 255) / 256 : 64),
+            (unsigned)(n < 65535 ? n : 65535));
+  axpy_kernel<<<grid, 256, 0, s>>>(m, n, alpha, A, lda, B, ldb);
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
+           const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+           int64_t ldc, int tri, const DevStatus* st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid;
+  if (tri) {
+    int64_t nt = (M + GEMM_TILE - 1) / GEMM_TILE;
+    grid = dim3((unsigned)(nt * (nt + 1) / 2), 1, 1);
+  } else {
+    grid = dim3((unsigned)((M + GEMM_TILE - 1) / GEMM_TILE), (unsigned)((N + GEMM_TILE - 1) / GEMM_TILE), 1);
+  }
+  if (ta == N_ && tb == N_)
+    dgemm_kernel<0, 0><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+  else if (ta == N_ && tb == T_)
+    dgemm_kernel<0, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+  else if (ta == T_ && tb == N_)
+    dgemm_kernel<1, 0><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+  else
+    dgemm_kernel<1, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+}
+
+void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {
+  static bool attr = false;
+  const int smem = 2 * 64 * 65 * (int)sizeof(double);
+  if (!attr) {
+    cudaFuncSetAttribute(potf2_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  for (int64_t k = 0; k < n; k += NB) {
+    const int kb = (int)((n - k) < NB ? (n - k) : NB);
+    double* Akk = A + k + k * lda;
+    double* Dk = Dinv + (k / NB) * NB * NB;
+    potf2_diag_kernel<<<1, 256, smem, s>>>(Akk, lda, kb, Dk, st, k);
+    const int64_t rest = n - k - kb;
+    if (rest > 0) {
+      double* P = A + (k + kb) + k * lda;
+      // panel: P <- P Lkk^{-T}  (in place; each CTA owns whole rows of the panel)
+      dgemm(s, N_, T_, rest, kb, kb, 1.0, P, lda, Dk, NB, 0.0, P, lda, 0, st);
+      // trailing lower update: A22 <- A22 - P P^T
+      dgemm(s, N_, T_, rest, rest, kb, -1.0, P, lda, P, lda, 1.0, A + (k + kb) + (k + kb) * lda,
+            lda, 1, st);
+    }
+  }
+}
+
+void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
+                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+  for (int64_t k = 0; k < n; k += NB) {
+    const int kb = (int)((n - k) < NB ? (n - k) : NB);
+    const double* Dk = Dinv + (k / NB) * NB * NB;
+    double* Bk = B + k;
+    dgemm(s, N_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+    const int64_t rest = n - k - kb;
+    if (rest > 0)
+      dgemm(s, N_, N_, rest, nrhs, kb, -1.0, Lf + (k + kb) + k * ldl, ldl, Bk, ldb, 1.0,
+            B + k + kb, ldb, 0, st);
+  }
+}
+
+void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
+                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+  const int64_t nblk = (n + NB - 1) / NB;
+  for (int64_t b = nblk - 1; b >= 0; --b) {
+    const int64_t k = b * NB;
+    const int kb = (int)((n - k) < NB ? (n - k) : NB);
+    const double* Dk = Dinv + b * NB * NB;
+    double* Bk = B + k;
+    dgemm(s, T_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+    if (k > 0)  // B[0:k] -= L[k:k+kb, 0:k]^T B_k
+      dgemm(s, T_, N_, k, nrhs, kb, -1.0, Lf + k, ldl, Bk, ldb, 1.0, B, ldb, 0, st);
+  }
+}
+
+void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* Lf, int64_t ldl,
+                        const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+  for (int64_t k = 0; k < n; k += NB) {
+    const int kb = (int)((n - k) < NB ? (n - k) : NB);
+    const double* Dk = Dinv + (k / NB) * NB * NB;
+    double* Bk = B + k * ldb;
+    dgemm(s, N_, T_, nrows, kb, kb, 1.0, Bk, ldb, Dk, NB, 0.0, Bk, ldb, 0, st);
+    const int64_t rest = n - k - kb;
+    if (rest > 0)  // B[:, k+kb:] -= B_k L[k+kb:, k:k+kb]^T
+      dgemm(s, N_, T_, nrows, rest, kb, -1.0, Bk, ldb, Lf + (k + kb) + k * ldl, ldl, 1.0,
+            B + (k + kb) * ldb, ldb, 0, st);
+  }
+}
+
+void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda) {
+  dim3 blk(32, 8);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
+  symmetrize_kernel<<<grid, blk, 0, s>>>(n, A, lda);
+}
+
+void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
+               double alpha) {
+  if (n <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64),
+            (unsigned)(n < 65535 ? n : 65535));
+  add_lower_kernel<<<grid, 256, 0, s>>>(n, A, lda, B, ldb, alpha);
+}
+
+void copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                 int64_t ldb) {
+  if (m <= 0 || n <= 0) return;
+  dim3 grid((unsigned)((m + 255) / 256 < 64 ? (m + 255) / 256 : 64),
+            (unsigned)(n < 65535 ? n : 65535));
+  copy_kernel<<<grid, 256, 0, s>>>(m, n, A, lda, B, ldb);
+}
+
+}  // namespace ec

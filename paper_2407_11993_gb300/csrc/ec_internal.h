@@ -1,0 +1,83 @@
+// Internal declarations shared by the translation units of the eddy-current
+// theta-method library.  Not part of the C ABI (that is include/eddy_theta.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/eddy_theta.h"
+
+namespace ec {
+
+// Device-side status block.  Kernels write the first error they see and later
+// kernels of the same pipeline return early once it is set.
+struct DevStatus {
+  int code;        // ec_status value, 0 = OK
+  int info;        // e.g. the global index of a non-positive pivot
+  int where;       // which kernel / wait gave up (diagnostics)
+  int pad;
+};
+
+constexpr int NB = 64;              // block size of every blocked FP64 algorithm here
+constexpr int GEMM_TILE = 64;       // output tile of the FP64 GEMM kernel
+constexpr int GEMM_KC = 16;         // K chunk staged through shared memory
+
+enum Op { N_ = 0, T_ = 1 };
+
+// ---- FP64 dense kernels (ec_blas.cu); all column-major -------------------
+// C[MxN] = alpha op(A) op(B) + beta C.  tri = 1 restricts work to the lower
+// triangle of C (tiles above the diagonal skipped, diagonal tiles masked).
+void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
+           const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+           double* C, int64_t ldc, int tri, const DevStatus* st);
+
+// Blocked right-looking Cholesky of the lower triangle of A (n x n, ld lda), in
+// place.  Dinv receives, per NB block, the inverse of the diagonal block of the
+// factor (NB x NB column-major, zero above the diagonal).  A non-positive pivot
+// sets st->code = EC_ERR_NOT_SPD and st->info = its global index.
+void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st);
+
+// B <- Lfac^{-1} B  (left, lower, no transpose); B is n x nrhs.
+void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac, int64_t ldl,
+                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+// B <- Lfac^{-T} B  (left, lower factor, transposed = upper solve).
+void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac, int64_t ldl,
+                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+// B <- B Lfac^{-T}  (right side, lower factor transposed); B is nrows x n.
+void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* Lfac,
+                        int64_t ldl, const double* Dinv, double* B, int64_t ldb,
+                        const DevStatus* st);
+
+// Symmetrise: copy the lower triangle onto the upper one.
+void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda);
+// A <- A + alpha B on the lower triangle (n x n).
+void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
+               double alpha);
+void copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                 int64_t ldb);
+
+// ---- persistent blocked triangular solves (ec_trsv.cu) --------------------
+struct TrsvSync {
+  int* flags_fwd;     // one per NB block: epoch of the last published block
+  int* flags_bwd;
+  unsigned* tickets;  // [0] forward, [1] backward
+  int* epoch;         // device epoch, bumped once per solve pair
+};
+// Lfac y = b then Lfac^T x = y, x and y of length n.  b and x may alias.
+void trsv_pair(cudaStream_t s, int64_t n, const double* Lfac, int64_t ldl, const double* Dinv,
+               const double* b, double* y, double* x, const TrsvSync& sync, int grid,
+               long long spin_limit, DevStatus* st);
+void trsv_begin(cudaStream_t s, const TrsvSync& sync);   // resets tickets, bumps epoch
+
+// Test hook: a wait on a flag nothing sets, bounded by spin_limit.
+void wait_timeout_probe(cudaStream_t s, int* flag, long long spin_limit, DevStatus* st);
+
+int num_sms();
+
+}  // namespace ec
+
+namespace ec {
+// B <- B + alpha A  (m x n blocks).
+void axpy_matrix(cudaStream_t s, int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                 double* B, int64_t ldb);
+}  // namespace ec

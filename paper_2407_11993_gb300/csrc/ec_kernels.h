@@ -1,0 +1,71 @@
+// Declarations of the setup and stepping kernels used by the C ABI layer.
+#pragma once
+
+#include "ec_internal.h"
+
+namespace ec {
+
+constexpr int MAXM = 16;   // most electrode rows (N_e - 1) supported
+constexpr int MAXD = 64;   // most dot products per step (probes + 2 m)
+
+struct Csr {
+  long long* ptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  long long nnz = 0;
+};
+
+// ---- ec_elim.cu ------------------------------------------------------------
+void house_qr(cudaStream_t s, int64_t n, int m, const double* E, double* V, double* T,
+              double* RrinvT, DevStatus* st);
+void sym_from_upper(cudaStream_t s, int64_t n, double* A, int64_t lda);
+void two_sided_update(cudaStream_t s, int64_t n, int m, double* A, const double* V,
+                      const double* T, double* Y, double* X, double* Sm, double* Zm,
+                      const DevStatus* st);
+void one_sided_qt(cudaStream_t s, int64_t n, int m, double* B, int64_t ncol, const double* V,
+                  const double* T, double* S1, double* S2, const DevStatus* st);
+void one_sided_q(cudaStream_t s, int64_t n, int m, double* B, int64_t ncol, const double* V,
+                 const double* T, double* S1, double* S2, const DevStatus* st);
+ec_status build_csr(cudaStream_t s, int64_t n, const double* A, Csr& out,
+                    cudaError_t (*alloc)(void**, size_t));
+
+// ---- ec_step.cu: per-step kernels of both forms ----------------------------
+// Everything a step kernel needs, by value (device pointers + sizes).
+struct StepArgs {
+  int64_t n, n0;
+  int m, S, P, D;              // D = P + 2 m dot products per step
+  double theta, dt;
+  // sources (device): src S x (T+1), iD m x (T+1), row-major
+  const double* src;
+  const double* iD;
+  int64_t T;
+  int64_t* kstep;              // device step counter within the run
+  // elimination pieces (m > 0)
+  const double* V;             // n x m
+  const double* WR;            // n x m  (R V)
+  const double* Tm;            // m x m
+  const double* VtWR;          // m x m  (V^T R V)
+  const double* PE;            // n x m  particular field
+  const double* CPE;           // P x m  column-major: C E^T (E E^T)^{-1}
+  // plain form
+  Csr R;                        // CSR of the original R
+  const double* Gsrc;          // n0 x (2m + S): [R_D | L_D + theta dt R_D | M_0]
+  const double* Dmat;          // n0 x D: [ (C K)^T | V[m:,:] | WR[m:,:] ]
+  double* Ii;                  // n0 state (plain)
+  double* work;                // n0 right-hand side / solution
+  double* dots;                // D values for the current state
+  double* partial;             // grid x D partial sums
+  unsigned* counter;           // last-block counter
+  double* probes;              // T x P output (may be null)
+  double* snaps;               // nsnap x n output (may be null)
+  int64_t snap_stride;
+  unsigned* tickets;
+  int* epoch;
+  DevStatus* st;
+};
+
+void plain_rhs(cudaStream_t s, const StepArgs& a);
+void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode);  // mode 0: += work; 1: dots only
+void plain_snapshot(cudaStream_t s, const StepArgs& a);
+
+}  // namespace ec

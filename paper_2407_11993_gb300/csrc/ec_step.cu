@@ -1,0 +1,177 @@
+// Per-step kernels of the plain (Cholesky) form, Sec. 3.3.1, Eq. time_integration:
+//
+//   (L_i + dt theta R_i) dI = -dt R_i I_i^k - dt R_D i_D^k - (L_D + dt theta R_D) d i_D - M_0 d i_0
+//
+// The right-hand side needs R_i I_i = [Q^T R Q x]_{m:} with x = [0; I_i].  R
+// is applied from its CSR (sparse for the FEM / synthetic R) and Q^T R Q - R
+// is the rank-2m correction  -WR T (V^T x) - V T^T (WR^T x) + V T^T (V^T WR) T (V^T x),
+// WR = R V.  The 2m dot products V^T x, WR^T x are produced, together with the
+// probe outputs C K I_i, by the update kernel of the previous step, with a
+// deterministic two-level reduction (per-CTA partials summed in CTA order by
+// the last CTA to finish).
+
+#include "ec_kernels.h"
+
+namespace ec {
+
+namespace {
+
+__device__ __forceinline__ double src_at(const double* a, int64_t T, int row, int64_t k) {
+  return a[(int64_t)row * (T + 1) + k];
+}
+
+__global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
+  __shared__ double alpha[MAXM], beta[MAXM], coef[2 * MAXM + 64];
+  const int64_t k = *a.kstep;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.tickets[0] = 0u;
+    a.tickets[1] = 0u;
+    *a.epoch = *a.epoch + 1;
+  }
+  const int m = a.m, P = a.P;
+  const int ncoef = 2 * m + a.S;
+  if (threadIdx.x == 0) {
+    if (m > 0) {
+      const double* p = a.dots + P;
+      const double* q = a.dots + P + m;
+      double Tp[MAXM], u[MAXM];
+      for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += a.Tm[i + j * m] * p[j];
+        Tp[i] = s;
+        alpha[i] = -s;
+      }
+      for (int i = 0; i < m; ++i) {
+        double s = -q[i];
+        for (int j = 0; j < m; ++j) s += a.VtWR[i + j * m] * Tp[j];
+        u[i] = s;
+      }
+      for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += a.Tm[j + i * m] * u[j];   // T^T u
+        beta[i] = s;
+      }
+    }
+    for (int j = 0; j < m; ++j) {
+      const double d0 = src_at(a.iD, a.T, j, k), d1 = src_at(a.iD, a.T, j, k + 1);
+      coef[j] = -a.dt * d0;
+      coef[m + j] = -(d1 - d0);
+    }
+    for (int l = 0; l < a.S; ++l)
+      coef[2 * m + l] = -(src_at(a.src, a.T, l, k + 1) - src_at(a.src, a.T, l, k));
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i + m;
+    double s = 0.0;
+    for (long long e = a.R.ptr[row]; e < a.R.ptr[row + 1]; ++e) {
+      const int c = a.R.col[e];
+      if (c >= m) s = fma(a.R.val[e], a.Ii[c - m], s);
+    }
+    for (int j = 0; j < m; ++j)
+      s = fma(a.WR[row + (int64_t)j * a.n], alpha[j], fma(a.V[row + (int64_t)j * a.n], beta[j], s));
+    double b = -a.dt * s;
+    for (int c = 0; c < ncoef; ++c) b = fma(coef[c], a.Gsrc[i + (int64_t)c * a.n0], b);
+    a.work[i] = b;
+  }
+}
+
+__global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode) {
+  __shared__ double sh[33];
+  __shared__ bool last;
+  const int64_t n0 = a.n0;
+  const int64_t chunk = (n0 + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b1 = (b0 + chunk < n0) ? b0 + chunk : n0;
+  if (mode == 0)
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = 0; d < a.D; ++d) {
+    const double* col = a.Dmat + (int64_t)d * n0;
+    double s = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s = fma(col[i], a.Ii[i], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[w] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+      a.partial[(int64_t)blockIdx.x * a.D + d] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(a.counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t k = *a.kstep;   // this update produces state k + 1 (mode 0)
+  for (int d = threadIdx.x; d < a.D; d += blockDim.x) {
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(a.partial + (int64_t)b * a.D + d);
+    a.dots[d] = t;
+    if (mode == 0 && d < a.P && a.probes != nullptr) {
+      double y = t;
+      for (int j = 0; j < a.m; ++j) y = fma(a.CPE[d + (int64_t)j * a.P], src_at(a.iD, a.T, j, k + 1), y);
+      a.probes[k * a.P + d] = y;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *a.counter = 0u;
+    if (mode == 0) *a.kstep = k + 1;
+  }
+}
+
+__global__ void plain_snapshot_kernel(StepArgs a) {
+  const int64_t k = *a.kstep;
+  if (a.snap_stride <= 0 || a.snaps == nullptr || k == 0 || k % a.snap_stride != 0) return;
+  const int64_t j = k / a.snap_stride - 1;
+  __shared__ double Tp[MAXM], iDk[MAXM];
+  const int m = a.m;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < m; ++c) s += a.Tm[i + c * m] * a.dots[a.P + c];
+      Tp[i] = s;
+      iDk[i] = src_at(a.iD, a.T, i, k);
+    }
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (i >= m) ? a.Ii[i - m] : 0.0;
+    for (int c = 0; c < m; ++c)
+      v = fma(-a.V[i + (int64_t)c * a.n], Tp[c], fma(a.PE[i + (int64_t)c * a.n], iDk[c], v));
+    a.snaps[j * a.n + i] = v;
+  }
+}
+
+int rows_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void plain_rhs(cudaStream_t s, const StepArgs& a) {
+  plain_rhs_kernel<<<rows_grid(a.n0), 256, 0, s>>>(a);
+}
+
+void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode) {
+  plain_update_kernel<<<grid, 256, 0, s>>>(a, mode);
+}
+
+void plain_snapshot(cudaStream_t s, const StepArgs& a) {
+  plain_snapshot_kernel<<<rows_grid(a.n), 256, 0, s>>>(a);
+}
+
+}  // namespace ec

@@ -1,0 +1,225 @@
+"""Python binding of the C ABI in include/eddy_theta.h (ctypes; marshalling only).
+
+Every step of the theta-method runs in the CUDA library; this module only turns
+numpy arrays (host memory) or CUDA torch tensors (device memory) into pointers
+and sizes.  Importing it does not load the library; the first call does, and
+raises if the compiled library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int64, c_longlong, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libeddy_theta.so")
+
+EC_FORM_PLAIN, EC_FORM_MODAL = 0, 1
+EC_MEM_HOST, EC_MEM_DEVICE = 0, 1
+
+STATUS = {
+    0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_SHAPE", 3: "EC_ERR_NOT_SPD", 4: "EC_ERR_RANK",
+    5: "EC_ERR_OOM", 6: "EC_ERR_CUDA", 7: "EC_ERR_TIMEOUT", 8: "EC_ERR_STATE",
+    9: "EC_ERR_NOT_CONVERGED", 10: "EC_ERR_UNSUPPORTED",
+}
+
+EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "ec_state_size",
+           "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
+           "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout")
+
+
+class ec_config(ctypes.Structure):
+    _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
+                ("device", c_int), ("spin_limit", c_longlong)]
+
+
+class ec_timing(ctypes.Structure):
+    _fields_ = [("elim_ms", c_double), ("factor_ms", c_double), ("reduce_ms", c_double),
+                ("tridiag_ms", c_double), ("eig_ms", c_double), ("backtransform_ms", c_double),
+                ("project_ms", c_double), ("setup_ms", c_double), ("run_ms", c_double),
+                ("run_steps", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EcError(RuntimeError):
+    def __init__(self, code: int, where: str, info: int = -1):
+        self.code = code
+        self.info = info
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_text(code)}) info={info}")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P = c_void_p
+        sig = {
+            "ec_create": (c_int, [POINTER(c_void_p), POINTER(ec_config)]),
+            "ec_setup": (c_int, [P, c_int64, P, P, c_int64, P, c_int64, P, P, c_int64, P, c_int]),
+            "ec_set_step": (c_int, [P, c_double, c_double]),
+            "ec_run": (c_int, [P, c_int64, P, P, P, c_int64, P, c_int]),
+            "ec_set_current": (c_int, [P, P, c_int]),
+            "ec_state_size": (c_int64, [P]),
+            "ec_get_state": (c_int, [P, P, c_int]),
+            "ec_set_state": (c_int, [P, P, c_int]),
+            "ec_get_modes": (c_int, [P, P, P, c_int]),
+            "ec_timings": (c_int, [P, POINTER(ec_timing)]),
+            "ec_sync": (c_int, [P]),
+            "ec_last_info": (c_int64, [P]),
+            "ec_error_string": (ctypes.c_char_p, [c_int]),
+            "ec_destroy": (None, [P]),
+            "ec_selftest_wait_timeout": (c_int, [c_longlong, POINTER(c_int)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _text(code: int) -> str:
+    try:
+        return lib().ec_error_string(code).decode()
+    except Exception:  # noqa: BLE001 - best-effort message only
+        return ""
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, mem: int):
+    """(pointer, keepalive) for an array in the requested memory space."""
+    if x is None:
+        return None, None
+    if mem == EC_MEM_DEVICE:
+        if not _is_torch(x) or not x.is_cuda:
+            raise TypeError("device memory requires a CUDA torch tensor")
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return c_void_p(a.ctypes.data), a
+
+
+def check(code: int, where: str, ctx=None) -> None:
+    if code != 0:
+        info = lib().ec_last_info(ctx) if ctx else -1
+        raise EcError(code, where, info)
+
+
+def selftest_wait_timeout(spin_limit: int) -> int:
+    out = c_int(-1)
+    check(lib().ec_selftest_wait_timeout(spin_limit, ctypes.byref(out)), "ec_selftest_wait_timeout")
+    return out.value
+
+
+class ThetaMethod:
+    """One context of the C library: setup once, then run / continue.
+
+    Array conventions follow the oracle: L, R (N, N); E (m, N); M (N, S) coil
+    mutual columns; MD (N, m); C (P, N); src (S, T+1); iD (m, T+1).  Results:
+    probes (P, T) and snaps (N, T // stride).  ``mem`` selects host numpy
+    arrays or CUDA torch tensors for inputs and outputs alike.
+    """
+
+    def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
+                 device: int = 0, stream: int | None = None, spin_limit: int = 0):
+        cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
+                        float(dt), c_void_p(stream or 0), int(device), int(spin_limit))
+        h = c_void_p()
+        check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
+        self._h = h
+        self.form = form
+        self.n = self.m = self.S = self.P = 0
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def setup(self, L, R, E=None, M=None, MD=None, C=None, mem: int = EC_MEM_HOST) -> None:
+        n = int(L.shape[0])
+        m = 0 if E is None else int(E.shape[0])
+        S = 0 if M is None else int(M.shape[1])
+        P = 0 if C is None else int(C.shape[0])
+        tr = (lambda a: a.t().contiguous()) if mem == EC_MEM_DEVICE else (lambda a: np.ascontiguousarray(a.T))
+        keep = []
+        pL, k = _ptr(L, mem); keep.append(k)
+        pR, k = _ptr(R, mem); keep.append(k)
+        pE, k = _ptr(E if m else None, mem); keep.append(k)
+        pM, k = _ptr(tr(M) if S else None, mem); keep.append(k)
+        pMD, k = _ptr(tr(MD) if (m and MD is not None) else None, mem); keep.append(k)
+        pC, k = _ptr(C if P else None, mem); keep.append(k)
+        check(lib().ec_setup(self._h, n, pL, pR, m, pE, S, pM, pMD, P, pC, mem), "ec_setup", self._h)
+        self.n, self.m, self.S, self.P = n, m, S, P
+
+    def set_step(self, theta: float, dt: float) -> None:
+        check(lib().ec_set_step(self._h, float(theta), float(dt)), "ec_set_step", self._h)
+
+    def run(self, T: int, src=None, iD=None, snap_stride: int = 0, mem: int = EC_MEM_HOST,
+            probes_out=None, snaps_out=None):
+        """Advance T steps; returns (probes (P, T), snaps (N, nsnap))."""
+        nsnap = T // snap_stride if snap_stride else 0
+        if mem == EC_MEM_DEVICE:
+            import torch
+            dev = torch.device("cuda")
+            probes = probes_out if probes_out is not None else torch.empty((T, self.P), dtype=torch.float64, device=dev)
+            snaps = snaps_out if snaps_out is not None else torch.empty((nsnap, self.n), dtype=torch.float64, device=dev)
+        else:
+            probes = np.empty((T, self.P)) if probes_out is None else probes_out
+            snaps = np.empty((nsnap, self.n)) if snaps_out is None else snaps_out
+        ps, k1 = _ptr(src if self.S else None, mem)
+        pi, k2 = _ptr(iD if self.m else None, mem)
+        pp = c_void_p(probes.data_ptr() if mem == EC_MEM_DEVICE else probes.ctypes.data) if self.P else None
+        pn = c_void_p(snaps.data_ptr() if mem == EC_MEM_DEVICE else snaps.ctypes.data) if nsnap else None
+        check(lib().ec_run(self._h, int(T), ps, pi, pp, int(snap_stride) if nsnap else 0, pn, mem),
+              "ec_run", self._h)
+        return probes.T, snaps.T
+
+    def state_size(self) -> int:
+        return int(lib().ec_state_size(self._h))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(self.state_size())
+        check(lib().ec_get_state(self._h, c_void_p(out.ctypes.data), EC_MEM_HOST), "ec_get_state", self._h)
+        return out
+
+    def set_state(self, state) -> None:
+        p, k = _ptr(state, EC_MEM_HOST)
+        check(lib().ec_set_state(self._h, p, EC_MEM_HOST), "ec_set_state", self._h)
+
+    def set_current(self, I) -> None:
+        p, k = _ptr(I, EC_MEM_HOST)
+        check(lib().ec_set_current(self._h, p, EC_MEM_HOST), "ec_set_current", self._h)
+
+    def modes(self):
+        n0 = self.state_size()
+        tau = np.empty(n0)
+        U = np.empty((n0, n0))
+        check(lib().ec_get_modes(self._h, c_void_p(tau.ctypes.data), c_void_p(U.ctypes.data),
+                                 EC_MEM_HOST), "ec_get_modes", self._h)
+        return tau, U.T   # column-major in the ABI
+
+    def timings(self) -> dict:
+        t = ec_timing()
+        check(lib().ec_timings(self._h, ctypes.byref(t)), "ec_timings", self._h)
+        return t.as_dict()
+
+    def sync(self) -> None:
+        check(lib().ec_sync(self._h), "ec_sync", self._h)

@@ -1,0 +1,124 @@
+"""Plain (Cholesky) form on the GPU against the FP64 oracle (Sec. 3.3.1).
+
+Tolerance: 1e-10 relative in the 2-norm per output (the FP64 bar); the
+oracle's own plain and modal forms agree to ~1e-15 on these inputs, so any
+larger gap is a kernel error, not conditioning.
+"""
+import numpy as np
+import pytest
+
+from oracle import theta as orc
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def eddy():
+    from paper_2407_11993_gb300 import build, eddy as e
+    build.build()
+    return e
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def run_gpu(eddy, p, form="plain", T=None, I0=None):
+    T = p.T if T is None else T
+    tm = eddy.ThetaMethod(form, p.theta, p.dt)
+    tm.setup(p.L, p.R, p.E if p.E.shape[0] else None, p.M if p.M.shape[1] else None,
+             p.MD if p.E.shape[0] else None, p.C)
+    if I0 is not None:
+        tm.set_current(I0)
+    probes, snaps = tm.run(T, p.src[:, :T + 1] if p.M.shape[1] else None,
+                           p.iD[:, :T + 1] if p.E.shape[0] else None, p.snap_stride)
+    return tm, probes, snaps
+
+
+def test_config1_coil_n512(eddy):
+    p = synth.config1()
+    ref = orc.run_problem(p, "plain")
+    _, probes, _ = run_gpu(eddy, p)
+    assert probes.shape == ref.probes.shape
+    assert rel(probes, ref.probes) < TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 200, 517])
+def test_ragged_sizes_with_electrode_and_coil(eddy, n):
+    electrodes = n >= 4
+    p = synth.small(n, T=40, seed=n, electrodes=electrodes, coil=True, snap_stride=7)
+    ref = orc.run_problem(p, "plain")
+    _, probes, snaps = run_gpu(eddy, p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+
+
+def test_two_electrode_rows(eddy):
+    p = synth.small(150, T=30, seed=4, electrodes=True, coil=True, snap_stride=5)
+    rng = np.random.default_rng(0)
+    E2 = np.zeros((2, 150))
+    E2[0] = p.E[0]
+    face = p.geom.ijk[:, 0] == p.geom.grid[0] - 1
+    E2[1, face] = np.cos(p.geom.phi[face])
+    p.E = E2
+    p.MD = np.concatenate([p.MD, 0.5 * p.MD], axis=1)
+    p.iD = np.stack([p.iD[0], 0.3 * np.sin(np.arange(31) * 0.2)])
+    ref = orc.run_problem(p, "plain")
+    _, probes, snaps = run_gpu(eddy, p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+    # constraint E I = i_D holds on the GPU snapshots
+    assert np.allclose(p.E @ snaps, p.iD[:, 5::5], atol=1e-12)
+
+
+def test_initial_current_and_zero_source_decay(eddy):
+    p = synth.small(96, T=25, seed=8, electrodes=False, coil=False, snap_stride=1)
+    I0 = np.random.default_rng(3).standard_normal(96)
+    ref = orc.run_problem(p, "plain", I0=I0)
+    _, probes, snaps = run_gpu(eddy, p, I0=I0)
+    assert rel(snaps, ref.snaps) < TOL
+    W = [orc.magnetic_energy(p.L, snaps[:, k]) for k in range(25)]
+    assert np.all(np.diff(W) <= 1e-12 * W[0])
+
+
+def test_resume_is_bitwise(eddy):
+    p = synth.small(130, T=60, seed=9, electrodes=True, coil=True)
+    tm, full, _ = run_gpu(eddy, p)
+    state_full = tm.get_state()
+    tm2 = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm2.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
+    a, _ = tm2.run(25, p.src[:, :26], p.iD[:, :26])
+    st = tm2.get_state()
+    tm3 = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm3.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
+    tm3.set_state(st)
+    b, _ = tm3.run(35, p.src[:, 25:], p.iD[:, 25:])
+    assert np.array_equal(np.concatenate([a, b], axis=1), full)
+    assert np.array_equal(tm3.get_state(), state_full)
+
+
+def test_not_spd_is_reported(eddy):
+    p = synth.small(80, T=2, seed=1, electrodes=False, coil=True)
+    L = p.L.copy()
+    L[37, 37] = -1.0
+    tm = eddy.ThetaMethod("plain", 0.5, p.dt)
+    with pytest.raises(eddy.EcError) as e:
+        tm.setup(L, p.R, None, p.M, None, p.C)
+    assert e.value.code == 3
+    assert 0 <= e.value.info <= 37
+
+
+def test_bounded_wait_times_out(eddy):
+    assert eddy.selftest_wait_timeout(2000) == 7   # EC_ERR_TIMEOUT
+
+
+def test_config2_electrodes_n8192_first_steps(eddy):
+    """N = 8192 with the electrode step, 16 pickups: first 40 steps + snapshots."""
+    p = synth.config2(T=40, snap_stride=20)
+    ref = orc.run_problem(p, "plain")
+    _, probes, snaps = run_gpu(eddy, p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
