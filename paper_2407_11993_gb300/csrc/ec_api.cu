@@ -531,7 +531,11 @@ ec_status ec_set_current(ec_ctx* c, const double* I, int mem) {
     StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
     plain_update(c->stream, a, c->update_grid, 1);
   } else {
-    modal_set_internal_current(c->stream, c->modal, c->dTmpN + c->m);
+    copy_matrix(c->stream, c->n0, 1, c->dTmpN + c->m, c->n, c->dIi, c->n0);
+    StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
+    plain_update(c->stream, a, c->update_grid, 1);
+    ri_apply(c->stream, a, c->dWork);
+    modal_set_internal_current(c->stream, c->modal, c->dWork);
   }
   return collect(c);
 }

@@ -31,18 +31,10 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t& i, int64_t& j) {
 }
 
 template <int TA, int TB>
-__global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
-                                                    const double* A, int64_t lda, const double* B,
-                                                    int64_t ldb, double beta, double* C,
-                                                    int64_t ldc, int tri, const DevStatus* st) {
-  if (failed(st)) return;
-  int64_t tm, tn;
-  if (tri) {
-    tri_tile(blockIdx.x, tm, tn);
-  } else {
-    tm = blockIdx.x;
-    tn = blockIdx.y;
-  }
+__device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, double alpha,
+                                          const double* A, int64_t lda, const double* B,
+                                          int64_t ldb, double beta, double* C, int64_t ldc,
+                                          int tri, int64_t tm, int64_t tn) {
   const int64_t row0 = tm * GEMM_TILE, col0 = tn * GEMM_TILE;
   __shared__ double As[GEMM_KC][GEMM_TILE + 1];
   __shared__ double Bs[GEMM_KC][GEMM_TILE + 1];
@@ -122,6 +114,36 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
   }
 }
 
+template <int TA, int TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                    const double* A, int64_t lda, const double* B,
+                                                    int64_t ldb, double beta, double* C,
+                                                    int64_t ldc, int tri, const DevStatus* st) {
+  if (failed(st)) return;
+  int64_t tm, tn;
+  if (tri) {
+    tri_tile(blockIdx.x, tm, tn);
+  } else {
+    tm = blockIdx.x;
+    tn = blockIdx.y;
+  }
+  gemm_tile<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, tm, tn);
+}
+
+// Block-diagonal batch: group z covers rows/cols [z*bs, min((z+1)*bs, n)) of
+// three n x n matrices; C_z = A_z B_z.
+__global__ void __launch_bounds__(256) dgemm_grouped_kernel(int64_t n, int64_t bs, const double* A,
+                                                            const double* B, double* C, int64_t ld,
+                                                            const DevStatus* st) {
+  if (failed(st)) return;
+  const int64_t s0 = (int64_t)blockIdx.z * bs;
+  const int64_t nb = (n - s0) < bs ? (n - s0) : bs;
+  if ((int64_t)blockIdx.x * GEMM_TILE >= nb || (int64_t)blockIdx.y * GEMM_TILE >= nb) return;
+  const int64_t off = s0 + s0 * ld;
+  gemm_tile<0, 0>(nb, nb, nb, 1.0, A + off, ld, B + off, ld, 0.0, C + off, ld, 0, blockIdx.x,
+                  blockIdx.y);
+}
+
 // Cholesky of one diagonal block (kb <= 64) in shared memory, plus the inverse
 // of the resulting lower-triangular factor.  One CTA of 256 threads.
 __global__ void __launch_bounds__(256) potf2_diag_kernel(double* A, int64_t lda, int kb,
@@ -187,6 +209,16 @@ __global__ void __launch_bounds__(256) potf2_diag_kernel(double* A, int64_t lda,
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     int r = idx % NB, c = idx / NB;
     Dinv[idx] = (r < kb && c < kb && r >= c) ? X[c * 65 + r] : 0.0;
+  }
+}
+
+__global__ void symmetrize_avg_kernel(int64_t n, double* A, int64_t lda) {
+  const int64_t c = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < n && c < n && r > c) {
+    const double v = 0.5 * (A[r + c * lda] + A[c + r * lda]);
+    A[r + c * lda] = v;
+    A[c + r * lda] = v;
   }
 }
 
@@ -262,6 +294,13 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
     dgemm_kernel<1, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
 }
 
+void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,
+                   const double* B, double* C, int64_t ld, const DevStatus* st) {
+  if (groups <= 0) return;
+  const unsigned t = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
+  dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, s>>>(n, bs, A, B, C, ld, st);
+}
+
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {
   static bool attr = false;
   const int smem = 2 * 64 * 65 * (int)sizeof(double);
@@ -332,6 +371,12 @@ void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
   symmetrize_kernel<<<grid, blk, 0, s>>>(n, A, lda);
+}
+
+void symmetrize_avg(cudaStream_t s, int64_t n, double* A, int64_t lda) {
+  dim3 blk(32, 8);
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
+  symmetrize_avg_kernel<<<grid, blk, 0, s>>>(n, A, lda);
 }
 
 void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,

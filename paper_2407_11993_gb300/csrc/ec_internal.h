@@ -31,6 +31,11 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
            double* C, int64_t ldc, int tri, const DevStatus* st);
 
+// Block-diagonal batched product: for z < groups, the bs x bs diagonal block z
+// (clipped at n) of C = A B, all three n x n with leading dimension ld.
+void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,
+                   const double* B, double* C, int64_t ld, const DevStatus* st);
+
 // Blocked right-looking Cholesky of the lower triangle of A (n x n, ld lda), in
 // place.  Dinv receives, per NB block, the inverse of the diagonal block of the
 // factor (NB x NB column-major, zero above the diagonal).  A non-positive pivot
@@ -50,6 +55,8 @@ void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* 
 
 // Symmetrise: copy the lower triangle onto the upper one.
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda);
+// A <- (A + A^T) / 2.
+void symmetrize_avg(cudaStream_t s, int64_t n, double* A, int64_t lda);
 // A <- A + alpha B on the lower triangle (n x n).
 void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
                double alpha);

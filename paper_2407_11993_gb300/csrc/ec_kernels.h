@@ -67,5 +67,7 @@ struct StepArgs {
 void plain_rhs(cudaStream_t s, const StepArgs& a);
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode);  // mode 0: += work; 1: dots only
 void plain_snapshot(cudaStream_t s, const StepArgs& a);
+// out = R_i I_i for the state in a.Ii (needs a.dots current for that state).
+void ri_apply(cudaStream_t s, const StepArgs& a, double* out);
 
 }  // namespace ec

@@ -1,22 +1,427 @@
-// Modal form: placeholder until the eigen pipeline lands.
+// Modal form (Sec. 3.2, Eq. generalized_eigenvalues_discrete and
+// modal_decomposition_discrete; Sec. 3.3.2).
+//
+// Setup, all FP64 on the GPU:
+//   R_i = C_R C_R^T                       (blocked Cholesky)
+//   A   = C_R^{-1} L_i C_R^{-T}           (two blocked triangular solves)
+//   A   = Q T Q^T                         (Householder tridiagonalisation)
+//   T   = S diag(lambda) S^T              (divide and conquer; timed on its own)
+//   U   = C_R^{-T} Q S,  tau = lambda     (columns reordered by decreasing tau)
+// so that U^T R_i U = 1 and U^T L_i U = diag(tau): R_n = 1, L_n = tau_n.
+//
+// Projections (Delta t independent, Sec. 5):  B = U^T [R_D | L_D | M_0],
+// G^T = U^T (C K)^T.  With I_i = U x the theta-step of Eq. time_integration
+// becomes, mode by mode,
+//   x_n^{k+1} = a_n x_n^k + c_n beta_n^k,
+//   a_n = (tau_n - (1 - theta) dt) / (tau_n + theta dt),  c_n = 1 / (tau_n + theta dt),
+//   beta^k  = B_R (-dt i_D^k - theta dt d i_D) + B_L (-d i_D) + B_M (-d i_0),
+// and the probes are y^k = G x^k + C E^T (E E^T)^{-1} i_D^k.
+//
+// Run: one thread per mode walks the time steps of a chunk with x in a
+// register; the probe contraction G x^k is reduced per warp with shuffles,
+// buffered in shared memory for 32 steps, and summed across warps; per-CTA
+// partial sums are then added in CTA order by a second kernel (deterministic).
+// Snapshot amplitudes are stored and turned into currents by one GEMM.
+
+#include <cmath>
+
 #include "ec_modal.h"
+#include "ec_sytrd.h"
 
 namespace ec {
 
 struct ModalState {
-  double* x = nullptr;
+  int64_t n = 0, n0 = 0;
+  int m = 0, S = 0, P = 0, ncoef = 0;
+  double theta = 0.5, dt = 0.0;
+  double* U = nullptr;
+  double* tau = nullptr;
+  double* ac = nullptr;       // a_n (n0) then c_n (n0)
+  double* B = nullptr;        // n0 x ncoef
+  double* Gt = nullptr;       // n0 x P
+  double* x = nullptr;        // n0
+  double* work = nullptr;     // n0
+  double* Xsnap = nullptr;
+  size_t xsnapCap = 0;
+  double* partial = nullptr;
+  size_t partialCap = 0;
+  double* small = nullptr;    // m x nsnap scratch (x2)
+  size_t smallCap = 0;
+  // setup scratch
+  double* DinvR = nullptr;
+  const double* CR = nullptr;
+  int64_t ldCR = 0;
 };
 
-ModalState* modal_create() { return new ModalState(); }
-void modal_free(ModalState* ms) { delete ms; }
-ec_status modal_setup(cudaStream_t, ModalState*, const ModalSetupArgs&, ec_timing*) {
-  return EC_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int MT = 256;          // modes per CTA
+constexpr int TCHUNK = 4096;     // time steps per scan launch
+constexpr int TSUB = 32;         // steps buffered in shared memory per reduction
+
+cudaError_t dalloc(void** p, size_t b) { return cudaMalloc(p, b ? b : 8); }
+
+template <typename T>
+ec_status alloc_n(T** p, size_t count) {
+  if (*p) return EC_OK;
+  if (dalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return EC_ERR_OOM;
+  }
+  return EC_OK;
 }
-ec_status modal_set_step(cudaStream_t, ModalState*, double, double) { return EC_ERR_UNSUPPORTED; }
-ec_status modal_run(cudaStream_t, ModalState*, const StepArgs&) { return EC_ERR_UNSUPPORTED; }
+
+template <typename T>
+ec_status grow_n(T** p, size_t& cap, size_t count) {
+  if (*p && count <= cap) return EC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cap = 0;
+  ec_status s = alloc_n(p, count);
+  if (s == EC_OK) cap = count;
+  return s;
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double ms() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    cudaEventRecord(a, s);
+    return t;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// Reverse the column order (ascending -> descending eigenvalues).
+__global__ void reverse_kernel(int64_t n, const double* lam, const double* Q, double* tau,
+                               double* U) {
+  const int64_t c = blockIdx.y;
+  for (int64_t cc = c; cc < n; cc += gridDim.y) {
+    const int64_t src = n - 1 - cc;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+      U[r + cc * n] = Q[r + src * n];
+    if (blockIdx.x == 0 && threadIdx.x == 0) tau[cc] = lam[src];
+  }
+}
+
+__global__ void coef_kernel(int64_t n0, const double* tau, double theta, double dt, double* ac) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n0;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = tau[i];
+    const double den = t + theta * dt;
+    ac[i] = (t - (1.0 - theta) * dt) / den;
+    ac[n0 + i] = 1.0 / den;
+  }
+}
+
+__device__ __forceinline__ double srcv(const double* a, int64_t T, int row, int64_t k) {
+  return a[(int64_t)row * (T + 1) + k];
+}
+
+struct ScanArgs {
+  int64_t n0, T, k0, kn;      // steps k0 .. k0+kn-1 of a run of T steps
+  int m, S, P, ncoef;
+  double theta, dt;
+  const double* ac;
+  const double* B;
+  const double* Gt;
+  const double* src;
+  const double* iD;
+  double* x;
+  double* partial;            // nblk x kn x P
+  double* Xsnap;              // n0 x nsnap
+  int64_t stride;
+};
+
+__global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
+  extern __shared__ double smem[];
+  const int nc = a.ncoef;
+  const int ncs = nc > 0 ? nc : 1;
+  const int Ps = a.P > 0 ? a.P : 1;
+  double* coef = smem;                           // [TSUB][ncs]
+  double* red = smem + TSUB * ncs;               // [MT/32][TSUB][Ps]
+  const int64_t nmode = blockIdx.x * (int64_t)MT + threadIdx.x;
+  const bool live = nmode < a.n0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double an = 0.0, cn = 0.0, x = 0.0;
+  double b[2 * MAXM + 64];
+  double g[MAXD];
+  if (live) {
+    an = a.ac[nmode];
+    cn = a.ac[a.n0 + nmode];
+    x = a.x[nmode];
+    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
+    for (int p = 0; p < a.P; ++p) g[p] = a.Gt[nmode + (int64_t)p * a.n0];
+  } else {
+    for (int c = 0; c < nc; ++c) b[c] = 0.0;
+    for (int p = 0; p < a.P; ++p) g[p] = 0.0;
+  }
+  const int m = a.m;
+  for (int64_t t0 = 0; t0 < a.kn; t0 += TSUB) {
+    const int nt = (int)((a.kn - t0) < TSUB ? (a.kn - t0) : TSUB);
+    // per-step source coefficients of beta^k for this sub-chunk
+    for (int idx = threadIdx.x; idx < nt * nc; idx += MT) {
+      const int tt = idx / nc, c = idx % nc;
+      const int64_t k = a.k0 + t0 + tt;
+      double v;
+      if (c < m) {
+        const double d0 = srcv(a.iD, a.T, c, k), d1 = srcv(a.iD, a.T, c, k + 1);
+        v = -a.dt * d0 - a.theta * a.dt * (d1 - d0);
+      } else if (c < 2 * m) {
+        v = -(srcv(a.iD, a.T, c - m, k + 1) - srcv(a.iD, a.T, c - m, k));
+      } else {
+        v = -(srcv(a.src, a.T, c - 2 * m, k + 1) - srcv(a.src, a.T, c - 2 * m, k));
+      }
+      coef[tt * ncs + c] = v;
+    }
+    __syncthreads();
+    for (int tt = 0; tt < nt; ++tt) {
+      double beta = 0.0;
+      for (int c = 0; c < nc; ++c) beta = fma(b[c], coef[tt * ncs + c], beta);
+      x = fma(an, x, cn * beta);
+      const int64_t k1 = a.k0 + t0 + tt + 1;   // state index after this step
+      if (live && a.stride > 0 && a.Xsnap && k1 % a.stride == 0)
+        a.Xsnap[nmode + (k1 / a.stride - 1) * a.n0] = x;
+      for (int p = 0; p < a.P; ++p) {
+        double v = g[p] * x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[(w * TSUB + tt) * Ps + p] = v;
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nt * a.P; idx += MT) {
+      const int tt = idx / a.P, p = idx % a.P;
+      double v = 0.0;
+#pragma unroll
+      for (int ww = 0; ww < MT / 32; ++ww) v += red[(ww * TSUB + tt) * Ps + p];
+      a.partial[((int64_t)blockIdx.x * a.kn + t0 + tt) * a.P + p] = v;
+    }
+    __syncthreads();
+  }
+  if (live) a.x[nmode] = x;
+}
+
+__global__ void probe_reduce_kernel(ScanArgs a, int nblk, const double* CPE, double* probes) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= a.kn * a.P) return;
+  const int64_t tt = idx / a.P;
+  const int p = (int)(idx % a.P);
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += a.partial[((int64_t)b * a.kn + tt) * a.P + p];
+  const int64_t k1 = a.k0 + tt + 1;
+  for (int j = 0; j < a.m; ++j) v = fma(CPE[p + (int64_t)j * a.P], srcv(a.iD, a.T, j, k1), v);
+  probes[(a.k0 + tt) * a.P + p] = v;
+}
+
+// snaps (n x nsnap, ld n): add PE i_D at the snapshot times.
+__global__ void snap_particular_kernel(int64_t n, int m, int64_t nsnap, int64_t stride, int64_t T,
+                                       const double* PE, const double* iD, double* snaps) {
+  const int64_t j = blockIdx.y;
+  for (int64_t jj = j; jj < nsnap; jj += gridDim.y) {
+    const int64_t k = (jj + 1) * stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double v = snaps[i + jj * n];
+      for (int c = 0; c < m; ++c) v = fma(PE[i + (int64_t)c * n], srcv(iD, T, c, k), v);
+      snaps[i + jj * n] = v;
+    }
+  }
+}
+
+}  // namespace
+
+ModalState* modal_create() { return new ModalState(); }
+
+void modal_free(ModalState* ms) {
+  if (!ms) return;
+  double* ps[] = {ms->U, ms->tau, ms->ac, ms->B, ms->Gt, ms->x, ms->work, ms->Xsnap, ms->partial,
+                  ms->small, ms->DinvR};
+  for (double* p : ps)
+    if (p) cudaFree(p);
+  delete ms;
+}
+
 double* modal_state(ModalState* ms) { return ms->x; }
-const double* modal_tau(ModalState*) { return nullptr; }
-const double* modal_U(ModalState*) { return nullptr; }
-void modal_set_internal_current(cudaStream_t, ModalState*, const double*) {}
+const double* modal_tau(ModalState* ms) { return ms->tau; }
+const double* modal_U(ModalState* ms) { return ms->U; }
+
+#define MS_TRY(x)               \
+  do {                          \
+    ec_status _s = (x);         \
+    if (_s != EC_OK) return _s; \
+  } while (0)
+
+ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, ec_timing* tim) {
+  const int64_t n0 = a.n0, ld = a.ld;
+  ms->n = a.n; ms->n0 = n0; ms->m = a.m; ms->S = a.S; ms->P = a.P;
+  ms->ncoef = 2 * a.m + a.S;
+  ms->theta = a.theta; ms->dt = a.dt;
+  const size_t nn = (size_t)n0 * n0;
+  const int64_t nblk = (n0 + NB - 1) / NB;
+  MS_TRY(alloc_n(&ms->DinvR, (size_t)nblk * NB * NB));
+  MS_TRY(alloc_n(&ms->U, nn));
+  MS_TRY(alloc_n(&ms->tau, (size_t)n0));
+  MS_TRY(alloc_n(&ms->ac, (size_t)2 * n0));
+  MS_TRY(alloc_n(&ms->B, (size_t)n0 * (ms->ncoef > 0 ? ms->ncoef : 1)));
+  MS_TRY(alloc_n(&ms->Gt, (size_t)n0 * (a.P > 0 ? a.P : 1)));
+  MS_TRY(alloc_n(&ms->x, (size_t)n0));
+  MS_TRY(alloc_n(&ms->work, (size_t)n0));
+  cudaMemsetAsync(ms->x, 0, sizeof(double) * n0, s);
+  ms->CR = a.Ri;
+  ms->ldCR = ld;
+
+  Timer t(s);
+  // a4: R_i = C_R C_R^T
+  potrf(s, n0, a.Ri, ld, ms->DinvR, a.st);
+  tim->factor_ms = t.ms();
+  {
+    DevStatus h{};
+    cudaMemcpy(&h, a.st, sizeof(h), cudaMemcpyDeviceToHost);
+    if (h.code != 0) return EC_OK;   // reported by the caller's status collection
+  }
+  // a5: A = C_R^{-1} L_i C_R^{-T}
+  trsm_left_lower(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
+  trsm_right_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
+  symmetrize_avg(s, n0, a.Li, ld);
+  tim->reduce_ms = t.ms();
+  // a6: tridiagonalisation
+  double *d = nullptr, *e = nullptr, *th = nullptr, *v = nullptr, *w = nullptr, *part = nullptr;
+  double *lam = nullptr, *Q1 = nullptr, *Q2 = nullptr, *Wm = nullptr;
+  double *Vb = nullptr, *Gb = nullptr, *Tb = nullptr, *W1 = nullptr, *W2 = nullptr;
+  const int64_t pcap = (int64_t)(4 * num_sms() + 8) * n0;
+  ec_status rc = EC_OK;
+  auto cleanup = [&]() {
+    double* ps[] = {d, e, th, v, w, part, lam, Q1, Q2, Wm, Vb, Gb, Tb, W1, W2};
+    for (double* p : ps)
+      if (p) cudaFree(p);
+  };
+  if (alloc_n(&d, n0) || alloc_n(&e, n0) || alloc_n(&th, n0) || alloc_n(&v, n0) ||
+      alloc_n(&w, n0) || alloc_n(&part, (size_t)pcap) || alloc_n(&lam, n0) ||
+      alloc_n(&Q1, nn) || alloc_n(&Q2, nn) || alloc_n(&Wm, nn) ||
+      alloc_n(&Vb, (size_t)n0 * NB) || alloc_n(&Gb, (size_t)NB * NB) ||
+      alloc_n(&Tb, (size_t)NB * NB) || alloc_n(&W1, (size_t)NB * n0) ||
+      alloc_n(&W2, (size_t)NB * n0)) {
+    cleanup();
+    return EC_ERR_OOM;
+  }
+  sytrd_lower(s, n0, a.Li, ld, d, e, th, v, w, part, pcap, a.st);
+  tim->tridiag_ms = t.ms();
+  DcWork* dcw = dc_alloc(n0, dalloc);
+  if (!dcw) {
+    cleanup();
+    return EC_ERR_OOM;
+  }
+  rc = dc_solve(s, n0, d, e, lam, Q1, Q2, Wm, dcw, a.st);
+  tim->eig_ms = t.ms();
+  dc_free(dcw);
+  if (rc != EC_OK) {
+    cleanup();
+    return rc;
+  }
+  // descending order, then U = C_R^{-T} Q S
+  {
+    dim3 g((unsigned)((n0 + 255) / 256 < 16 ? (n0 + 255) / 256 : 16),
+           (unsigned)(n0 < 65535 ? n0 : 65535));
+    reverse_kernel<<<g, 256, 0, s>>>(n0, lam, Q1, ms->tau, ms->U);
+  }
+  ormtr_lower(s, n0, a.Li, ld, th, ms->U, n0, n0, Vb, Gb, Tb, W1, W2, a.st);
+  trsm_left_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, ms->U, n0, a.st);
+  tim->backtransform_ms = t.ms();
+  cleanup();
+  // a7: projections and per-mode coefficients
+  if (ms->ncoef > 0) {
+    double* Gm = nullptr;
+    if (alloc_n(&Gm, (size_t)n0 * ms->ncoef)) return EC_ERR_OOM;
+    if (a.m > 0) {
+      copy_matrix(s, n0, a.m, a.RD, n0, Gm, n0);
+      copy_matrix(s, n0, a.m, a.LD, n0, Gm + n0 * a.m, n0);
+    }
+    if (a.S > 0) copy_matrix(s, n0, a.S, a.Msrc, a.ldM, Gm + n0 * 2 * a.m, n0);
+    dgemm(s, T_, N_, n0, ms->ncoef, n0, 1.0, ms->U, n0, Gm, n0, 0.0, ms->B, n0, 0, a.st);
+    cudaStreamSynchronize(s);
+    cudaFree(Gm);
+  }
+  if (a.P > 0) dgemm(s, T_, N_, n0, a.P, n0, 1.0, ms->U, n0, a.CK, a.ldC, 0.0, ms->Gt, n0, 0, a.st);
+  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, s>>>(
+      n0, ms->tau, ms->theta, ms->dt, ms->ac);
+  tim->project_ms = t.ms();
+  return EC_OK;
+}
+
+ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt) {
+  ms->theta = theta;
+  ms->dt = dt;
+  const int64_t n0 = ms->n0;
+  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, s>>>(
+      n0, ms->tau, theta, dt, ms->ac);
+  return EC_OK;
+}
+
+ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa) {
+  const int64_t n0 = ms->n0, T = sa.T;
+  const int nblk = (int)((n0 + MT - 1) / MT);
+  const int64_t nsnap = (sa.snap_stride > 0 && sa.snaps) ? T / sa.snap_stride : 0;
+  if (nsnap > 0) MS_TRY(grow_n(&ms->Xsnap, ms->xsnapCap, (size_t)n0 * nsnap));
+  const int64_t kmax = T < TCHUNK ? T : TCHUNK;
+  MS_TRY(grow_n(&ms->partial, ms->partialCap, (size_t)nblk * kmax * (ms->P > 0 ? ms->P : 1)));
+  ScanArgs a{};
+  a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P; a.ncoef = ms->ncoef;
+  a.theta = ms->theta; a.dt = ms->dt; a.ac = ms->ac; a.B = ms->B; a.Gt = ms->Gt;
+  a.src = sa.src; a.iD = sa.iD; a.x = ms->x; a.partial = ms->partial;
+  a.Xsnap = nsnap > 0 ? ms->Xsnap : nullptr; a.stride = nsnap > 0 ? sa.snap_stride : 0;
+  const size_t smem = sizeof(double) * (size_t)(TSUB * (ms->ncoef > 0 ? ms->ncoef : 1) +
+                                                (MT / 32) * TSUB * (ms->P > 0 ? ms->P : 1));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  for (int64_t k0 = 0; k0 < T; k0 += TCHUNK) {
+    a.k0 = k0;
+    a.kn = (T - k0) < TCHUNK ? (T - k0) : TCHUNK;
+    modal_scan_kernel<<<nblk, MT, smem, s>>>(a);
+    if (ms->P > 0 && sa.probes) {
+      const int64_t tot = a.kn * ms->P;
+      probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a, nblk, sa.CPE, sa.probes);
+    }
+  }
+  if (nsnap > 0) {
+    const int64_t n = ms->n;
+    const int m = ms->m;
+    // rows m.. of each snapshot: U x; rows 0..m-1: 0; then apply Q and add the particular field
+    if (m > 0) cudaMemsetAsync(sa.snaps, 0, sizeof(double) * (size_t)n * nsnap, s);
+    dgemm(s, N_, N_, n0, nsnap, n0, 1.0, ms->U, n0, ms->Xsnap, n0, 0.0, sa.snaps + m, n, 0, sa.st);
+    if (m > 0) {
+      MS_TRY(grow_n(&ms->small, ms->smallCap, (size_t)2 * m * nsnap));
+      one_sided_q(s, n, m, sa.snaps, nsnap, sa.V, sa.Tm, ms->small, ms->small + m * nsnap, sa.st);
+      dim3 g((unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16),
+             (unsigned)(nsnap < 65535 ? nsnap : 65535));
+      snap_particular_kernel<<<g, 256, 0, s>>>(n, m, nsnap, sa.snap_stride, T, sa.PE, sa.iD,
+                                               sa.snaps);
+    }
+  }
+  return EC_OK;
+}
+
+void modal_set_internal_current(cudaStream_t s, ModalState* ms, const double* RiIi) {
+  // x = U^T (R_i I_i): the caller passes R_i I_i.
+  dgemm(s, T_, N_, ms->n0, 1, ms->n0, 1.0, ms->U, ms->n0, RiIi, ms->n0, 0.0, ms->x, ms->n0, 0,
+        nullptr);
+}
 
 }  // namespace ec

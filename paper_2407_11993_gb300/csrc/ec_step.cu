@@ -20,18 +20,11 @@ __device__ __forceinline__ double src_at(const double* a, int64_t T, int row, in
   return a[(int64_t)row * (T + 1) + k];
 }
 
-__global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
-  __shared__ double alpha[MAXM], beta[MAXM], coef[2 * MAXM + 64];
-  const int64_t k = *a.kstep;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.tickets[0] = 0u;
-    a.tickets[1] = 0u;
-    *a.epoch = *a.epoch + 1;
-  }
+// alpha = -T p, beta = T^T (-q + (V^T WR) T p) for the rank-2m part of Q^T R Q.
+__device__ void lowrank_coefs(const StepArgs& a, double* alpha, double* beta) {
   const int m = a.m, P = a.P;
-  const int ncoef = 2 * m + a.S;
-  if (threadIdx.x == 0) {
-    if (m > 0) {
+  {
+    {
       const double* p = a.dots + P;
       const double* q = a.dots + P + m;
       double Tp[MAXM], u[MAXM];
@@ -52,6 +45,36 @@ __global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
         beta[i] = s;
       }
     }
+  }
+}
+
+// (R_i I_i)_i for internal row i: CSR of R on x = [0; I_i] plus the rank-2m correction.
+__device__ __forceinline__ double ri_row(const StepArgs& a, int64_t i, const double* alpha,
+                                         const double* beta) {
+  const int m = a.m;
+  const int64_t row = i + m;
+  double s = 0.0;
+  for (long long e = a.R.ptr[row]; e < a.R.ptr[row + 1]; ++e) {
+    const int c = a.R.col[e];
+    if (c >= m) s = fma(a.R.val[e], a.Ii[c - m], s);
+  }
+  for (int j = 0; j < m; ++j)
+    s = fma(a.WR[row + (int64_t)j * a.n], alpha[j], fma(a.V[row + (int64_t)j * a.n], beta[j], s));
+  return s;
+}
+
+__global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
+  __shared__ double alpha[MAXM], beta[MAXM], coef[2 * MAXM + 64];
+  const int64_t k = *a.kstep;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.tickets[0] = 0u;
+    a.tickets[1] = 0u;
+    *a.epoch = *a.epoch + 1;
+  }
+  const int m = a.m;
+  const int ncoef = 2 * m + a.S;
+  if (threadIdx.x == 0) {
+    if (m > 0) lowrank_coefs(a, alpha, beta);
     for (int j = 0; j < m; ++j) {
       const double d0 = src_at(a.iD, a.T, j, k), d1 = src_at(a.iD, a.T, j, k + 1);
       coef[j] = -a.dt * d0;
@@ -63,18 +86,19 @@ __global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i + m;
-    double s = 0.0;
-    for (long long e = a.R.ptr[row]; e < a.R.ptr[row + 1]; ++e) {
-      const int c = a.R.col[e];
-      if (c >= m) s = fma(a.R.val[e], a.Ii[c - m], s);
-    }
-    for (int j = 0; j < m; ++j)
-      s = fma(a.WR[row + (int64_t)j * a.n], alpha[j], fma(a.V[row + (int64_t)j * a.n], beta[j], s));
-    double b = -a.dt * s;
+    double b = -a.dt * ri_row(a, i, alpha, beta);
     for (int c = 0; c < ncoef; ++c) b = fma(coef[c], a.Gsrc[i + (int64_t)c * a.n0], b);
     a.work[i] = b;
   }
+}
+
+__global__ void __launch_bounds__(256) ri_apply_kernel(StepArgs a, double* out) {
+  __shared__ double alpha[MAXM], beta[MAXM];
+  if (threadIdx.x == 0 && a.m > 0) lowrank_coefs(a, alpha, beta);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = ri_row(a, i, alpha, beta);
 }
 
 __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode) {
@@ -168,6 +192,10 @@ void plain_rhs(cudaStream_t s, const StepArgs& a) {
 
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode) {
   plain_update_kernel<<<grid, 256, 0, s>>>(a, mode);
+}
+
+void ri_apply(cudaStream_t s, const StepArgs& a, double* out) {
+  ri_apply_kernel<<<rows_grid(a.n0), 256, 0, s>>>(a, out);
 }
 
 void plain_snapshot(cudaStream_t s, const StepArgs& a) {

@@ -1,0 +1,229 @@
+// Householder tridiagonalisation A = Q T Q^T of a symmetric matrix (lower
+// reflectors, the first stage of the standard symmetric eigensolver used for
+// the pencil of Sec. 3.2 after its reduction to standard form) and the
+// application of Q to a block of vectors with compact-WY blocks of 64
+// reflectors.
+//
+// Column j: reflector H_j = I - tau_j v_j v_j^T with v_j = 0 above row j+1,
+// v_j[j+1] = 1, annihilating A[j+2:, j]; then
+//   p = tau A22 v,  w = p - (tau/2)(p^T v) v,  A22 <- A22 - v w^T - w v^T.
+// The full symmetric matrix is kept up to date so that A22 v is a coalesced
+// column-major GEMV.  v_j[j+2:] is stored back into A[j+2:, j].
+
+#include <cmath>
+
+#include "ec_internal.h"
+#include "ec_sytrd.h"
+
+namespace ec {
+
+namespace {
+
+constexpr int HT = 1024;
+
+__device__ double block_sum1024(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__global__ void __launch_bounds__(HT) house_col_kernel(int64_t n, double* A, int64_t lda,
+                                                       int64_t j, double* v, double* d, double* e,
+                                                       double* tau, const DevStatus* st) {
+  if (st->code) return;
+  __shared__ double sh[40];
+  __shared__ double s_scale;
+  double* col = A + j * lda;
+  double sig = 0.0;
+  for (int64_t i = j + 2 + threadIdx.x; i < n; i += HT) sig = fma(col[i], col[i], sig);
+  sig = block_sum1024(sig, sh);
+  const double alpha = col[j + 1];
+  double beta, t, scale;
+  if (sig == 0.0) {
+    beta = alpha;
+    t = 0.0;
+    scale = 0.0;
+  } else {
+    const double nx = sqrt(alpha * alpha + sig);
+    beta = alpha >= 0.0 ? -nx : nx;
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  if (threadIdx.x == 0) {
+    d[j] = col[j];
+    e[j] = beta;
+    tau[j] = t;
+    s_scale = scale;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += HT) {
+    double vi;
+    if (i <= j) vi = 0.0;
+    else if (i == j + 1) vi = 1.0;
+    else {
+      vi = col[i] * s_scale;
+      col[i] = vi;
+    }
+    v[i] = vi;
+  }
+}
+
+// partial[c * n + i] = sum over column chunk c of A[i, k] v[k], i, k in [j+1, n)
+__global__ void __launch_bounds__(256) symv_partial_kernel(int64_t n, const double* A, int64_t lda,
+                                                           int64_t j, const double* v,
+                                                           double* partial, int64_t kc) {
+  const int64_t i = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t k0 = j + 1 + blockIdx.y * kc;
+  int64_t k1 = k0 + kc;
+  if (k1 > n) k1 = n;
+  if (i >= n) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t k = k0;
+  for (; k + 3 < k1; k += 4) {
+    s0 = fma(A[i + k * lda], v[k], s0);
+    s1 = fma(A[i + (k + 1) * lda], v[k + 1], s1);
+    s2 = fma(A[i + (k + 2) * lda], v[k + 2], s2);
+    s3 = fma(A[i + (k + 3) * lda], v[k + 3], s3);
+  }
+  for (; k < k1; ++k) s0 = fma(A[i + k * lda], v[k], s0);
+  partial[blockIdx.y * n + i] = (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(HT) w_kernel(int64_t n, int64_t j, const double* v,
+                                               const double* tau, const double* partial,
+                                               int nchunk, double* w) {
+  __shared__ double sh[40];
+  const double t = tau[j];
+  double dot = 0.0;
+  for (int64_t i = j + 1 + threadIdx.x; i < n; i += HT) {
+    double p = 0.0;
+    for (int c = 0; c < nchunk; ++c) p += partial[c * n + i];
+    p *= t;
+    w[i] = p;
+    dot = fma(p, v[i], dot);
+  }
+  dot = block_sum1024(dot, sh);
+  const double f = 0.5 * t * dot;
+  for (int64_t i = j + 1 + threadIdx.x; i < n; i += HT) w[i] = fma(-f, v[i], w[i]);
+}
+
+__global__ void syr2_kernel(int64_t n, double* A, int64_t lda, int64_t j, const double* v,
+                            const double* w, const double* tau) {
+  if (tau[j] == 0.0) return;
+  const int64_t len = n - j - 1;
+  for (int64_t kk = blockIdx.y; kk < len; kk += gridDim.y) {
+    const int64_t k = j + 1 + kk;
+    const double vk = v[k], wk = w[k];
+    double* colk = A + k * lda;
+    for (int64_t i = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      colk[i] = fma(-v[i], wk, fma(-w[i], vk, colk[i]));
+  }
+}
+
+__global__ void tail_kernel(int64_t n, const double* A, int64_t lda, double* d, double* e) {
+  if (n >= 2) {
+    d[n - 2] = A[(n - 2) + (n - 2) * lda];
+    d[n - 1] = A[(n - 1) + (n - 1) * lda];
+    e[n - 2] = A[(n - 1) + (n - 2) * lda];
+  } else if (n == 1) {
+    d[0] = A[0];
+  }
+}
+
+// V (n x kb): column c = v_{b+c}: zero above row b+c+1, one at b+c+1, stored tail below.
+__global__ void form_v_kernel(int64_t n, const double* A, int64_t lda, int64_t b, int kb,
+                              double* V) {
+  const int c = blockIdx.y;
+  const int64_t j = b + c;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x;
+    if (i <= j) x = 0.0;
+    else if (i == j + 1) x = 1.0;
+    else x = A[i + j * lda];
+    V[i + (int64_t)c * n] = x;
+  }
+}
+
+// T (kb x kb upper) of Q_b = H_b ... H_{b+kb-1} = I - V T V^T from G = V^T V.
+__global__ void form_t_kernel(int kb, const double* G, const double* tau, int64_t b, double* T) {
+  __shared__ double Ts[64][65];
+  __shared__ double g[64];
+  const int a = threadIdx.x;
+  for (int i = 0; i < kb; ++i) {
+    if (a < kb) g[a] = G[a + i * kb];
+    __syncthreads();
+    const double ti = tau[b + i];
+    if (a < i) {
+      double s = 0.0;
+      for (int c = a; c < i; ++c) s = fma(Ts[a][c], g[c], s);
+      Ts[a][i] = -ti * s;
+    } else if (a == i) {
+      Ts[a][i] = ti;
+    } else if (a < kb) {
+      Ts[a][i] = 0.0;
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < kb; ++i)
+    if (a < kb) T[a + i * kb] = Ts[a][i];
+}
+
+}  // namespace
+
+void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, double* e,
+                 double* tau, double* v, double* w, double* partial, int64_t partial_cap,
+                 const DevStatus* st) {
+  const int sms = num_sms();
+  for (int64_t j = 0; j + 2 < n; ++j) {
+    const int64_t len = n - j - 1;
+    house_col_kernel<<<1, HT, 0, s>>>(n, A, lda, j, v, d, e, tau, st);
+    const int64_t rb = (len + 255) / 256;
+    int64_t nchunk = (4 * sms + rb - 1) / rb;
+    if (nchunk < 1) nchunk = 1;
+    if (nchunk > len) nchunk = len;
+    while (nchunk * n > partial_cap) --nchunk;
+    const int64_t kc = (len + nchunk - 1) / nchunk;
+    nchunk = (len + kc - 1) / kc;
+    symv_partial_kernel<<<dim3((unsigned)rb, (unsigned)nchunk), 256, 0, s>>>(n, A, lda, j, v,
+                                                                             partial, kc);
+    w_kernel<<<1, HT, 0, s>>>(n, j, v, tau, partial, (int)nchunk, w);
+    dim3 g2((unsigned)((len + 255) / 256 < 8 ? (len + 255) / 256 : 8),
+            (unsigned)(len < 4096 ? len : 4096));
+    syr2_kernel<<<g2, 256, 0, s>>>(n, A, lda, j, v, w, tau);
+  }
+  tail_kernel<<<1, 1, 0, s>>>(n, A, lda, d, e);
+}
+
+void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const double* tau,
+                 double* Y, int64_t ldy, int64_t ncol, double* V, double* G, double* T,
+                 double* W, double* W2, const DevStatus* st) {
+  const int64_t nref = n - 2;
+  if (nref <= 0) return;
+  const int64_t nblk = (nref + NB - 1) / NB;
+  for (int64_t bi = nblk - 1; bi >= 0; --bi) {
+    const int64_t b = bi * NB;
+    const int kb = (int)((nref - b) < NB ? (nref - b) : NB);
+    form_v_kernel<<<dim3(32, kb), 256, 0, s>>>(n, A, lda, b, kb, V);
+    const int64_t r0 = b + 1, len = n - r0;
+    dgemm(s, T_, N_, kb, kb, len, 1.0, V + r0, n, V + r0, n, 0.0, G, kb, 0, st);
+    form_t_kernel<<<1, 64, 0, s>>>(kb, G, tau, b, T);
+    dgemm(s, T_, N_, kb, ncol, len, 1.0, V + r0, n, Y + r0, ldy, 0.0, W, kb, 0, st);
+    dgemm(s, N_, N_, kb, ncol, kb, 1.0, T, kb, W, kb, 0.0, W2, kb, 0, st);
+    dgemm(s, N_, N_, len, ncol, kb, -1.0, V + r0, n, W2, kb, 1.0, Y + r0, ldy, 0, st);
+  }
+}
+
+}  // namespace ec

@@ -1,0 +1,149 @@
+"""Modal form on the GPU against the FP64 oracle (Sec. 3.2, Sec. 3.3.2).
+
+The modal form is the same theta-scheme in the eigenvector basis, so its
+probe and snapshot outputs are compared with the oracle's plain (Cholesky)
+form at the FP64 bar (1e-10 relative, 2-norm per output); the eigenpairs are
+checked against the oracle's and against the invariants U^T R U = 1,
+U^T L U = diag(tau).
+"""
+import numpy as np
+import pytest
+
+from oracle import theta as orc
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def eddy():
+    from paper_2407_11993_gb300 import build, eddy as e
+    build.build()
+    return e
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make(eddy, p, form="modal"):
+    tm = eddy.ThetaMethod(form, p.theta, p.dt)
+    m = p.E.shape[0]
+    tm.setup(p.L, p.R, p.E if m else None, p.M if p.M.shape[1] else None,
+             p.MD if m else None, p.C)
+    return tm
+
+
+def run(tm, p, T=None, k0=0):
+    T = p.T if T is None else T
+    return tm.run(T, p.src[:, k0:k0 + T + 1] if p.M.shape[1] else None,
+                  p.iD[:, k0:k0 + T + 1] if p.E.shape[0] else None, p.snap_stride)
+
+
+def test_config1_coil_n512(eddy):
+    p = synth.config1()
+    ref = orc.run_problem(p, "plain")
+    probes, _ = run(make(eddy, p), p)
+    assert rel(probes, ref.probes) < TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 63, 64, 65, 200, 517])
+def test_ragged_sizes_with_electrode_and_coil(eddy, n):
+    electrodes = n >= 4
+    p = synth.small(n, T=40, seed=n, electrodes=electrodes, coil=True, snap_stride=7)
+    ref = orc.run_problem(p, "plain")
+    probes, snaps = run(make(eddy, p), p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+
+
+@pytest.mark.parametrize("n", [5, 130, 300])
+def test_eigenpairs_against_oracle(eddy, n):
+    p = synth.small(n, T=1, seed=3 * n, electrodes=False, coil=True)
+    tm = make(eddy, p)
+    tau, U = tm.modes()
+    md = orc.modal_setup(p.L, p.R)
+    assert np.all(np.diff(tau) <= 0) and tau.min() > 0
+    assert np.max(np.abs(tau - md.tau)) <= 1e-12 * md.tau.max()
+    eye = U.T @ p.R @ U
+    assert np.linalg.norm(eye - np.eye(n)) <= 1e-12 * n
+    lu = U.T @ p.L @ U
+    assert np.linalg.norm(lu - np.diag(tau)) <= 1e-12 * n * tau.max()
+    res = p.L @ U - (p.R @ U) * tau
+    assert np.linalg.norm(res) <= 1e-12 * n * np.linalg.norm(p.L) * np.linalg.norm(U)
+
+
+def test_two_electrode_rows(eddy):
+    p = synth.small(150, T=30, seed=4, electrodes=True, coil=True, snap_stride=5)
+    E2 = np.zeros((2, 150))
+    E2[0] = p.E[0]
+    face = p.geom.ijk[:, 0] == p.geom.grid[0] - 1
+    E2[1, face] = np.cos(p.geom.phi[face])
+    p.E = E2
+    p.MD = np.concatenate([p.MD, 0.5 * p.MD], axis=1)
+    p.iD = np.stack([p.iD[0], 0.3 * np.sin(np.arange(31) * 0.2)])
+    ref = orc.run_problem(p, "plain")
+    probes, snaps = run(make(eddy, p), p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+    assert np.allclose(p.E @ snaps, p.iD[:, 5::5], atol=1e-12)
+
+
+def test_initial_current(eddy):
+    p = synth.small(96, T=25, seed=8, electrodes=True, coil=False, snap_stride=1)
+    rng = np.random.default_rng(3)
+    red = orc.eliminate(p.L, p.R, p.E, p.M, p.MD, p.C)
+    I0 = red.K @ rng.standard_normal(95)          # consistent with i_D^0 = 0
+    ref = orc.run_problem(p, "plain", I0=I0)
+    tm = make(eddy, p)
+    tm.set_current(I0)
+    probes, snaps = run(tm, p)
+    assert rel(snaps, ref.snaps) < TOL
+
+
+def test_resume_is_bitwise(eddy):
+    p = synth.small(130, T=60, seed=9, electrodes=True, coil=True)
+    tm = make(eddy, p)
+    full, _ = run(tm, p)
+    x_full = tm.get_state()
+    tm2 = make(eddy, p)
+    a, _ = run(tm2, p, T=25)
+    st = tm2.get_state()
+    tm3 = make(eddy, p)
+    tm3.set_state(st)
+    b, _ = run(tm3, p, T=35, k0=25)
+    assert np.array_equal(np.concatenate([a, b], axis=1), full)
+    assert np.array_equal(tm3.get_state(), x_full)
+
+
+def test_set_step_reuses_modes(eddy):
+    """Changing dt only recomputes the per-mode coefficients (Sec. 5)."""
+    p = synth.small(120, T=30, seed=12, electrodes=True, coil=True, snap_stride=10)
+    tm = make(eddy, p)
+    q = synth.small(120, T=30, seed=12, electrodes=True, coil=True, snap_stride=10, dt=3e-6,
+                    theta=0.75)
+    tm.set_step(q.theta, q.dt)
+    probes, snaps = run(tm, q)
+    ref = orc.run_problem(q, "plain")
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+
+
+def test_modal_equals_plain_on_gpu(eddy):
+    p = synth.small(260, T=80, seed=14, electrodes=True, coil=True, snap_stride=20)
+    a, sa = run(make(eddy, p, "plain"), p)
+    b, sb = run(make(eddy, p, "modal"), p)
+    assert rel(b, a) < TOL and rel(sb, sa) < TOL
+
+
+def test_config2_electrodes_n8192_first_steps(eddy):
+    p = synth.config2(T=40, snap_stride=20)
+    ref = orc.run_problem(p, "plain")
+    tm = make(eddy, p)
+    probes, snaps = run(tm, p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+    t = tm.timings()
+    assert t["eig_ms"] > 0 and t["tridiag_ms"] > 0
