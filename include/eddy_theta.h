@@ -79,7 +79,19 @@ typedef struct ec_config {
   void* stream;           /* cudaStream_t to enqueue on; NULL = the legacy default stream */
   int device;             /* CUDA device ordinal */
   long long spin_limit;   /* polls before a kernel-side wait gives up (EC_ERR_TIMEOUT); 0 = default */
+  int profile;            /* nonzero: ec_run times its dominant kernels with CUDA events (see ec_timing) */
+  int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
 } ec_config;
+
+/* How the plain form applies its Cholesky factor C each step (Sec. 3.3.1).
+ *   EC_SOLVE_INVERSE       C^{-1} is formed once at setup (N^3/3 extra flops); each
+ *                          step computes y = C^{-1} b and x = C^{-T} y as triangular
+ *                          matrix-vector products (all tiles independent).
+ *   EC_SOLVE_SUBSTITUTION  forward then backward substitution with C itself, in a
+ *                          persistent kernel whose blocks wait on each other's
+ *                          published results (bounded waits).
+ * Both do N^2 multiply-adds per step. */
+enum { EC_SOLVE_INVERSE = 0, EC_SOLVE_SUBSTITUTION = 1 };
 
 /* Wall-clock phases of the last ec_setup / ec_run, in milliseconds, measured
  * with CUDA events on the context's stream.  Phases a form does not run are 0. */
@@ -94,6 +106,11 @@ typedef struct ec_timing {
   double setup_ms;        /* whole ec_setup */
   double run_ms;          /* whole last ec_run */
   int64_t run_steps;      /* steps of the last ec_run */
+  /* With cfg.profile set: summed device time and number of timed launches of the
+   * forward / backward solve kernels (plain form; a sample of steps) and of the
+   * modal scan kernel (modal form; every launch) during the last ec_run. */
+  double fwd_ms, bwd_ms, scan_ms;
+  int64_t fwd_launches, bwd_launches, scan_launches;
 } ec_timing;
 
 /* Create a context on cfg->device.  *out receives the handle. */
@@ -148,6 +165,10 @@ EC_API ec_status ec_sync(ec_ctx* ctx);
 EC_API int64_t ec_last_info(const ec_ctx* ctx);
 EC_API const char* ec_error_string(ec_status status);
 EC_API void ec_destroy(ec_ctx* ctx);
+
+/* Number of CUDA kernels the library has launched in this process, over all
+ * contexts (a monotonically increasing counter; take differences). */
+EC_API int64_t ec_launch_count(void);
 
 /* Self-test of the bounded kernel-side wait: launches one wait on a flag that
  * nothing sets, with at most spin_limit polls, and stores the status the kernel

@@ -1,14 +1,21 @@
 // C ABI of the theta-method library (include/eddy_theta.h): context, setup
 // and run orchestration for the plain and modal forms.
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ec_kernels.h"
 #include "ec_modal.h"
 
 using namespace ec;
+
+namespace ec {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace ec
 
 struct ec_ctx {
   ec_config cfg{};
@@ -24,6 +31,10 @@ struct ec_ctx {
   // plain
   double* dZ = nullptr;      // n0 x n0 Cholesky factor of L_i + theta dt R_i
   double* dDinv = nullptr;   // inverses of its 64 x 64 diagonal blocks
+  double* dW = nullptr;      // n0 x n0 inverse factor C^{-1} (EC_SOLVE_INVERSE)
+  double* dPart1 = nullptr;  // chunk partials of C^{-1} b
+  double* dPart2 = nullptr;  // chunk partials of C^{-T} y
+  double* dYsol = nullptr;   // C^{-1} b
   // elimination
   double* dE = nullptr;
   double* dV = nullptr;
@@ -73,6 +84,8 @@ struct ec_ctx {
 
 namespace {
 
+constexpr int TRMV_CHUNK = 16;   // 64 x 64 tiles per CTA in the inverse-factor products
+
 cudaError_t dev_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 8); }
 
 template <typename T>
@@ -104,6 +117,7 @@ ec_status grow(T** p, size_t& cap, size_t count) {
 
 void free_setup(ec_ctx* c) {
   dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
+  dfree(c->dW); dfree(c->dPart1); dfree(c->dPart2); dfree(c->dYsol);
   dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
   dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
   dfree(c->dY); dfree(c->dX); dfree(c->dSm); dfree(c->dZm); dfree(c->dGsrc); dfree(c->dDmat);
@@ -192,6 +206,9 @@ StepArgs step_args(ec_ctx* c, int64_t T, double* probes, double* snaps, int64_t 
   a.dots = c->dDots; a.partial = c->dPartial; a.counter = c->dCounter;
   a.probes = probes; a.snaps = snaps; a.snap_stride = stride;
   a.tickets = c->dTickets; a.epoch = c->dEpoch; a.st = c->st;
+  const bool inv = c->cfg.form == EC_FORM_PLAIN && c->cfg.plain_solver == EC_SOLVE_INVERSE;
+  a.dpart = inv ? c->dPart2 : nullptr;
+  a.npart = inv ? trmv_chunks(c->n0, TRMV_CHUNK) : 0;
   return a;
 }
 
@@ -220,6 +237,14 @@ ec_status plain_factor(ec_ctx* c) {
   copy_matrix(c->stream, n0, n0, c->dL + m + m * n, n, c->dZ, n0);
   add_lower(c->stream, n0, c->dZ, n0, c->dR + m + m * n, n, c->cfg.theta * c->cfg.dt);
   potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st);
+  if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
+    EC_TRY(alloc(&c->dW, (size_t)n0 * n0));
+    const int nc = trmv_chunks(n0, TRMV_CHUNK);
+    EC_TRY(alloc(&c->dPart1, (size_t)nc * n0));
+    EC_TRY(alloc(&c->dPart2, (size_t)nc * n0));
+    EC_TRY(alloc(&c->dYsol, (size_t)n0));
+    trtri_lower(c->stream, n0, c->dZ, n0, c->dDinv, c->dW, n0, c->st);
+  }
   c->tim.factor_ms = t.stop_ms();
   return collect(c);
 }
@@ -249,6 +274,8 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
   if (!out || !cfg) return EC_ERR_ARG;
   *out = nullptr;
   if (cfg->form != EC_FORM_PLAIN && cfg->form != EC_FORM_MODAL) return EC_ERR_ARG;
+  if (cfg->plain_solver != EC_SOLVE_INVERSE && cfg->plain_solver != EC_SOLVE_SUBSTITUTION)
+    return EC_ERR_ARG;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
@@ -478,21 +505,59 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
   }
   cudaMemsetAsync(c->dK, 0, sizeof(int64_t), c->stream);
   StepArgs a = step_args(c, T, outP, outS, nsnap > 0 ? stride : 0);
+  c->tim.fwd_ms = c->tim.bwd_ms = c->tim.scan_ms = 0.0;
+  c->tim.fwd_launches = c->tim.bwd_launches = c->tim.scan_launches = 0;
+  std::vector<cudaEvent_t> ev;
+  const bool prof = c->cfg.profile != 0;
   EventTimer t(c->stream);
   if (c->cfg.form == EC_FORM_PLAIN) {
     TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
+    const int64_t every = T > 512 ? (T + 511) / 512 : 1;
     for (int64_t k = 0; k < T; ++k) {
       plain_rhs(c->stream, a);
-      trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
-                c->trsv_grid, c->spin_limit, c->st);
+      cudaEvent_t* e3 = nullptr;
+      if (prof && k % every == 0) {
+        ev.resize(ev.size() + 3);
+        e3 = &ev[ev.size() - 3];
+        for (int q = 0; q < 3; ++q) cudaEventCreate(&e3[q]);
+      }
+      if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
+        trmv_pair(c->stream, c->n0, c->dW, c->n0, c->dWork, c->dPart1, c->dYsol, c->dPart2,
+                  TRMV_CHUNK, c->st, e3);
+      } else {
+        trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
+                  c->trsv_grid, c->spin_limit, c->st, e3);
+      }
       plain_update(c->stream, a, c->update_grid, 0);
       if (outS) plain_snapshot(c->stream, a);
     }
   } else {
-    EC_TRY(modal_run(c->stream, c->modal, a));
+    EC_TRY(modal_run(c->stream, c->modal, a, prof ? &ev : nullptr));
   }
   c->tim.run_ms = t.stop_ms();
   c->tim.run_steps = T;
+  if (!ev.empty()) {
+    cudaStreamSynchronize(c->stream);
+    if (c->cfg.form == EC_FORM_PLAIN) {
+      for (size_t q = 0; q + 2 < ev.size(); q += 3) {
+        float f = 0.f, b = 0.f;
+        cudaEventElapsedTime(&f, ev[q], ev[q + 1]);
+        cudaEventElapsedTime(&b, ev[q + 1], ev[q + 2]);
+        c->tim.fwd_ms += f;
+        c->tim.bwd_ms += b;
+        ++c->tim.fwd_launches;
+        ++c->tim.bwd_launches;
+      }
+    } else {
+      for (size_t q = 0; q + 1 < ev.size(); q += 2) {
+        float f = 0.f;
+        cudaEventElapsedTime(&f, ev[q], ev[q + 1]);
+        c->tim.scan_ms += f;
+        ++c->tim.scan_launches;
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
   EC_TRY(collect(c));
   if (outP && outP != probes) EC_TRY(copy_out(c, probes, outP, (size_t)T * c->P, mem));
   if (outS && outS != snaps) EC_TRY(copy_out(c, snaps, outS, (size_t)nsnap * n, mem));
@@ -547,6 +612,8 @@ ec_status ec_get_modes(ec_ctx* c, double* tau, double* U, int mem) {
   if (U) EC_TRY(copy_out(c, U, modal_U(c->modal), (size_t)c->n0 * c->n0, mem));
   return collect(c);
 }
+
+int64_t ec_launch_count(void) { return ec::g_launches.load(std::memory_order_relaxed); }
 
 ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {
   if (!code_out || spin_limit < 1) return EC_ERR_ARG;

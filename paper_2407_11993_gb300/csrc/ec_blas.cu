@@ -259,7 +259,7 @@ void axpy_matrix(cudaStream_t s, int64_t m, int64_t n, double alpha, const doubl
   if (m <= 0 || n <= 0) return;
   dim3 grid((unsigned)((m + 255) / 256 < 64 ? (m + 255) / 256 : 64),
             (unsigned)(n < 65535 ? n : 65535));
-  axpy_kernel<<<grid, 256, 0, s>>>(m, n, alpha, A, lda, B, ldb);
+  axpy_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(m, n, alpha, A, lda, B, ldb);
 }
 
 int num_sms() {
@@ -285,20 +285,20 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
     grid = dim3((unsigned)((M + GEMM_TILE - 1) / GEMM_TILE), (unsigned)((N + GEMM_TILE - 1) / GEMM_TILE), 1);
   }
   if (ta == N_ && tb == N_)
-    dgemm_kernel<0, 0><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+    dgemm_kernel<0, 0><<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
   else if (ta == N_ && tb == T_)
-    dgemm_kernel<0, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+    dgemm_kernel<0, 1><<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
   else if (ta == T_ && tb == N_)
-    dgemm_kernel<1, 0><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+    dgemm_kernel<1, 0><<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
   else
-    dgemm_kernel<1, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+    dgemm_kernel<1, 1><<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
 }
 
 void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,
                    const double* B, double* C, int64_t ld, const DevStatus* st) {
   if (groups <= 0) return;
   const unsigned t = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
-  dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, s>>>(n, bs, A, B, C, ld, st);
+  dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, A, B, C, ld, st);
 }
 
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {
@@ -312,7 +312,7 @@ void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevS
     const int kb = (int)((n - k) < NB ? (n - k) : NB);
     double* Akk = A + k + k * lda;
     double* Dk = Dinv + (k / NB) * NB * NB;
-    potf2_diag_kernel<<<1, 256, smem, s>>>(Akk, lda, kb, Dk, st, k);
+    potf2_diag_kernel<<<1, 256, smem, ::ec::counted(s)>>>(Akk, lda, kb, Dk, st, k);
     const int64_t rest = n - k - kb;
     if (rest > 0) {
       double* P = A + (k + kb) + k * lda;
@@ -370,13 +370,13 @@ void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* 
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
-  symmetrize_kernel<<<grid, blk, 0, s>>>(n, A, lda);
+  symmetrize_kernel<<<grid, blk, 0, ::ec::counted(s)>>>(n, A, lda);
 }
 
 void symmetrize_avg(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
-  symmetrize_avg_kernel<<<grid, blk, 0, s>>>(n, A, lda);
+  symmetrize_avg_kernel<<<grid, blk, 0, ::ec::counted(s)>>>(n, A, lda);
 }
 
 void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
@@ -384,7 +384,7 @@ void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* 
   if (n <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64),
             (unsigned)(n < 65535 ? n : 65535));
-  add_lower_kernel<<<grid, 256, 0, s>>>(n, A, lda, B, ldb, alpha);
+  add_lower_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(n, A, lda, B, ldb, alpha);
 }
 
 void copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t lda, double* B,
@@ -392,7 +392,7 @@ void copy_matrix(cudaStream_t s, int64_t m, int64_t n, const double* A, int64_t 
   if (m <= 0 || n <= 0) return;
   dim3 grid((unsigned)((m + 255) / 256 < 64 ? (m + 255) / 256 : 64),
             (unsigned)(n < 65535 ? n : 65535));
-  copy_kernel<<<grid, 256, 0, s>>>(m, n, A, lda, B, ldb);
+  copy_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(m, n, A, lda, B, ldb);
 }
 
 }  // namespace ec

@@ -337,18 +337,18 @@ ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, 
                    double* Q, double* Qtmp, double* W, DcWork* wk, DevStatus* st) {
   if (n <= 0) return EC_OK;
   cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * n, s);
-  leaf_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(
+  leaf_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n, d, e, lam, Q);
   for (int64_t bs = 2; bs / 2 < n; bs *= 2) {
     const int64_t half = bs / 2;
     const int64_t groups = (n - half + bs - 1) / bs;   // merges with a non-empty right half
     const unsigned chunks = (unsigned)((bs + 255) / 256);
-    deflate_kernel<<<(unsigned)groups, 256, 0, s>>>(n, bs, e, lam, Q, *wk);
-    secular_kernel<<<dim3((unsigned)groups, chunks), 256, 0, s>>>(bs, *wk);
-    zhat_kernel<<<dim3((unsigned)groups, chunks), 256, 0, s>>>(bs, *wk);
-    rank_kernel<<<dim3((unsigned)groups, chunks), 256, 0, s>>>(n, bs, *wk, lam);
-    qp_kernel<<<dim3((unsigned)groups, chunks), 256, 0, s>>>(n, bs, Q, Qtmp, *wk);
-    vec_kernel<<<dim3((unsigned)bs, (unsigned)groups), 256, 0, s>>>(n, bs, *wk, W);
+    deflate_kernel<<<(unsigned)groups, 256, 0, ::ec::counted(s)>>>(n, bs, e, lam, Q, *wk);
+    secular_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
+    zhat_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
+    rank_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, lam);
+    qp_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, Q, Qtmp, *wk);
+    vec_kernel<<<dim3((unsigned)bs, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, W);
     dgemm_grouped(s, n, bs, groups, Qtmp, W, Q, n, st);
   }
   return EC_OK;

@@ -194,13 +194,13 @@ __global__ void csr_fill_kernel(int64_t n, const double* A, int64_t lda, const l
 
 void house_qr(cudaStream_t s, int64_t n, int m, const double* E, double* V, double* T,
               double* RrinvT, DevStatus* st) {
-  house_kernel<<<1, HT, 0, s>>>(n, m, E, V, T, RrinvT, st);
+  house_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, m, E, V, T, RrinvT, st);
 }
 
 void sym_from_upper(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
-  sym_from_upper_kernel<<<grid, blk, 0, s>>>(n, A, lda);
+  sym_from_upper_kernel<<<grid, blk, 0, ::ec::counted(s)>>>(n, A, lda);
 }
 
 void two_sided_update(cudaStream_t s, int64_t n, int m, double* A, const double* V,
@@ -244,8 +244,8 @@ ec_status build_csr(cudaStream_t s, int64_t n, const double* A, Csr& out,
   }
   const int wpb = 8;
   const unsigned grid = (unsigned)((n + wpb - 1) / wpb);
-  csr_count_kernel<<<grid, 32 * wpb, 0, s>>>(n, A, n, cnt);
-  exclusive_scan_kernel<<<1, 1024, 0, s>>>(n, cnt, out.ptr);
+  csr_count_kernel<<<grid, 32 * wpb, 0, ::ec::counted(s)>>>(n, A, n, cnt);
+  exclusive_scan_kernel<<<1, 1024, 0, ::ec::counted(s)>>>(n, cnt, out.ptr);
   long long nnz = 0;
   cudaMemcpyAsync(&nnz, out.ptr + n, sizeof(long long), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -253,7 +253,7 @@ ec_status build_csr(cudaStream_t s, int64_t n, const double* A, Csr& out,
   out.nnz = nnz;
   if (alloc((void**)&out.col, sizeof(int) * (nnz > 0 ? nnz : 1)) != cudaSuccess) return EC_ERR_OOM;
   if (alloc((void**)&out.val, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess) return EC_ERR_OOM;
-  csr_fill_kernel<<<grid, 32 * wpb, 0, s>>>(n, A, n, out.ptr, out.col, out.val);
+  csr_fill_kernel<<<grid, 32 * wpb, 0, ::ec::counted(s)>>>(n, A, n, out.ptr, out.col, out.val);
   return EC_OK;
 }
 

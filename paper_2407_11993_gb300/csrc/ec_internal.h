@@ -71,15 +71,37 @@ struct TrsvSync {
   int* epoch;         // device epoch, bumped once per solve pair
 };
 // Lfac y = b then Lfac^T x = y, x and y of length n.  b and x may alias.
+// ev (optional, 3 events): recorded before the forward solve, between the two
+// solves and after the backward solve.
 void trsv_pair(cudaStream_t s, int64_t n, const double* Lfac, int64_t ldl, const double* Dinv,
                const double* b, double* y, double* x, const TrsvSync& sync, int grid,
-               long long spin_limit, DevStatus* st);
+               long long spin_limit, DevStatus* st, cudaEvent_t* ev = nullptr);
 void trsv_begin(cudaStream_t s, const TrsvSync& sync);   // resets tickets, bumps epoch
+
+// ---- inverse-factor solves (ec_trmv.cu) ----------------------------------
+// W = C^{-1} for the lower Cholesky factor C (n x n); W's diagonal 64 x 64 blocks
+// hold zeros above the diagonal, blocks above the block diagonal are not written.
+void trtri_lower(cudaStream_t s, int64_t n, const double* C, int64_t ldc, const double* Dinv,
+                 double* W, int64_t ldw, const DevStatus* st);
+int trmv_chunks(int64_t n, int chunk);
+// y = W b (part1: trmv_chunks x n partials, summed into y), then x = W^T y as
+// trmv_chunks x n partials in part2 (the consumer sums them in order).
+void trmv_pair(cudaStream_t s, int64_t n, const double* W, int64_t ldw, const double* b,
+               double* part1, double* y, double* part2, int chunk, const DevStatus* st,
+               cudaEvent_t* ev = nullptr);
 
 // Test hook: a wait on a flag nothing sets, bounded by spin_limit.
 void wait_timeout_probe(cudaStream_t s, int* flag, long long spin_limit, DevStatus* st);
 
 int num_sms();
+
+// Every kernel launch of the library passes its stream through counted(), which
+// increments the process-wide launch counter reported by ec_launch_count().
+void note_launch();
+inline cudaStream_t counted(cudaStream_t s) {
+  note_launch();
+  return s;
+}
 
 }  // namespace ec
 

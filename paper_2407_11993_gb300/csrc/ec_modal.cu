@@ -337,7 +337,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   {
     dim3 g((unsigned)((n0 + 255) / 256 < 16 ? (n0 + 255) / 256 : 16),
            (unsigned)(n0 < 65535 ? n0 : 65535));
-    reverse_kernel<<<g, 256, 0, s>>>(n0, lam, Q1, ms->tau, ms->U);
+    reverse_kernel<<<g, 256, 0, ::ec::counted(s)>>>(n0, lam, Q1, ms->tau, ms->U);
   }
   ormtr_lower(s, n0, a.Li, ld, th, ms->U, n0, n0, Vb, Gb, Tb, W1, W2, a.st);
   trsm_left_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, ms->U, n0, a.st);
@@ -357,7 +357,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
     cudaFree(Gm);
   }
   if (a.P > 0) dgemm(s, T_, N_, n0, a.P, n0, 1.0, ms->U, n0, a.CK, a.ldC, 0.0, ms->Gt, n0, 0, a.st);
-  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, s>>>(
+  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n0, ms->tau, ms->theta, ms->dt, ms->ac);
   tim->project_ms = t.ms();
   return EC_OK;
@@ -367,12 +367,13 @@ ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt
   ms->theta = theta;
   ms->dt = dt;
   const int64_t n0 = ms->n0;
-  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, s>>>(
+  coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n0, ms->tau, theta, dt, ms->ac);
   return EC_OK;
 }
 
-ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa) {
+ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
+                    std::vector<cudaEvent_t>* ev) {
   const int64_t n0 = ms->n0, T = sa.T;
   const int nblk = (int)((n0 + MT - 1) / MT);
   const int64_t nsnap = (sa.snap_stride > 0 && sa.snaps) ? T / sa.snap_stride : 0;
@@ -394,10 +395,17 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa) {
   for (int64_t k0 = 0; k0 < T; k0 += TCHUNK) {
     a.k0 = k0;
     a.kn = (T - k0) < TCHUNK ? (T - k0) : TCHUNK;
-    modal_scan_kernel<<<nblk, MT, smem, s>>>(a);
+    if (ev) {
+      ev->resize(ev->size() + 2);
+      cudaEventCreate(&(*ev)[ev->size() - 2]);
+      cudaEventCreate(&(*ev)[ev->size() - 1]);
+      cudaEventRecord((*ev)[ev->size() - 2], s);
+    }
+    modal_scan_kernel<<<nblk, MT, smem, ::ec::counted(s)>>>(a);
+    if (ev) cudaEventRecord(ev->back(), s);
     if (ms->P > 0 && sa.probes) {
       const int64_t tot = a.kn * ms->P;
-      probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a, nblk, sa.CPE, sa.probes);
+      probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ::ec::counted(s)>>>(a, nblk, sa.CPE, sa.probes);
     }
   }
   if (nsnap > 0) {
@@ -411,7 +419,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa) {
       one_sided_q(s, n, m, sa.snaps, nsnap, sa.V, sa.Tm, ms->small, ms->small + m * nsnap, sa.st);
       dim3 g((unsigned)((n + 255) / 256 < 16 ? (n + 255) / 256 : 16),
              (unsigned)(nsnap < 65535 ? nsnap : 65535));
-      snap_particular_kernel<<<g, 256, 0, s>>>(n, m, nsnap, sa.snap_stride, T, sa.PE, sa.iD,
+      snap_particular_kernel<<<g, 256, 0, ::ec::counted(s)>>>(n, m, nsnap, sa.snap_stride, T, sa.PE, sa.iD,
                                                sa.snaps);
     }
   }

@@ -2,6 +2,8 @@
 // per-mode theta-recurrence.
 #pragma once
 
+#include <vector>
+
 #include "ec_kernels.h"
 
 namespace ec {
@@ -29,7 +31,9 @@ ModalState* modal_create();
 void modal_free(ModalState* ms);
 ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, ec_timing* tim);
 ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt);
-ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& a);
+// ev (optional): receives an event pair around every scan launch.
+ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& a,
+                    std::vector<cudaEvent_t>* ev = nullptr);
 double* modal_state(ModalState* ms);
 const double* modal_tau(ModalState* ms);
 const double* modal_U(ModalState* ms);

@@ -108,8 +108,17 @@ __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode)
   const int64_t chunk = (n0 + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = (b0 + chunk < n0) ? b0 + chunk : n0;
-  if (mode == 0)
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
+  if (mode == 0) {
+    if (a.npart > 0) {
+      for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        double d = 0.0;
+        for (int q = 0; q < a.npart; ++q) d += a.dpart[q * n0 + i];
+        a.Ii[i] += d;
+      }
+    } else {
+      for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
+    }
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = 0; d < a.D; ++d) {
@@ -187,19 +196,19 @@ int rows_grid(int64_t n) {
 }  // namespace
 
 void plain_rhs(cudaStream_t s, const StepArgs& a) {
-  plain_rhs_kernel<<<rows_grid(a.n0), 256, 0, s>>>(a);
+  plain_rhs_kernel<<<rows_grid(a.n0), 256, 0, ::ec::counted(s)>>>(a);
 }
 
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode) {
-  plain_update_kernel<<<grid, 256, 0, s>>>(a, mode);
+  plain_update_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(a, mode);
 }
 
 void ri_apply(cudaStream_t s, const StepArgs& a, double* out) {
-  ri_apply_kernel<<<rows_grid(a.n0), 256, 0, s>>>(a, out);
+  ri_apply_kernel<<<rows_grid(a.n0), 256, 0, ::ec::counted(s)>>>(a, out);
 }
 
 void plain_snapshot(cudaStream_t s, const StepArgs& a) {
-  plain_snapshot_kernel<<<rows_grid(a.n), 256, 0, s>>>(a);
+  plain_snapshot_kernel<<<rows_grid(a.n), 256, 0, ::ec::counted(s)>>>(a);
 }
 
 }  // namespace ec

@@ -189,7 +189,7 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
   const int sms = num_sms();
   for (int64_t j = 0; j + 2 < n; ++j) {
     const int64_t len = n - j - 1;
-    house_col_kernel<<<1, HT, 0, s>>>(n, A, lda, j, v, d, e, tau, st);
+    house_col_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, A, lda, j, v, d, e, tau, st);
     const int64_t rb = (len + 255) / 256;
     int64_t nchunk = (4 * sms + rb - 1) / rb;
     if (nchunk < 1) nchunk = 1;
@@ -197,14 +197,14 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
     while (nchunk * n > partial_cap) --nchunk;
     const int64_t kc = (len + nchunk - 1) / nchunk;
     nchunk = (len + kc - 1) / kc;
-    symv_partial_kernel<<<dim3((unsigned)rb, (unsigned)nchunk), 256, 0, s>>>(n, A, lda, j, v,
+    symv_partial_kernel<<<dim3((unsigned)rb, (unsigned)nchunk), 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v,
                                                                              partial, kc);
-    w_kernel<<<1, HT, 0, s>>>(n, j, v, tau, partial, (int)nchunk, w);
+    w_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, j, v, tau, partial, (int)nchunk, w);
     dim3 g2((unsigned)((len + 255) / 256 < 8 ? (len + 255) / 256 : 8),
             (unsigned)(len < 4096 ? len : 4096));
-    syr2_kernel<<<g2, 256, 0, s>>>(n, A, lda, j, v, w, tau);
+    syr2_kernel<<<g2, 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v, w, tau);
   }
-  tail_kernel<<<1, 1, 0, s>>>(n, A, lda, d, e);
+  tail_kernel<<<1, 1, 0, ::ec::counted(s)>>>(n, A, lda, d, e);
 }
 
 void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const double* tau,
@@ -216,10 +216,10 @@ void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const 
   for (int64_t bi = nblk - 1; bi >= 0; --bi) {
     const int64_t b = bi * NB;
     const int kb = (int)((nref - b) < NB ? (nref - b) : NB);
-    form_v_kernel<<<dim3(32, kb), 256, 0, s>>>(n, A, lda, b, kb, V);
+    form_v_kernel<<<dim3(32, kb), 256, 0, ::ec::counted(s)>>>(n, A, lda, b, kb, V);
     const int64_t r0 = b + 1, len = n - r0;
     dgemm(s, T_, N_, kb, kb, len, 1.0, V + r0, n, V + r0, n, 0.0, G, kb, 0, st);
-    form_t_kernel<<<1, 64, 0, s>>>(kb, G, tau, b, T);
+    form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G, tau, b, T);
     dgemm(s, T_, N_, kb, ncol, len, 1.0, V + r0, n, Y + r0, ldy, 0.0, W, kb, 0, st);
     dgemm(s, N_, N_, kb, ncol, kb, 1.0, T, kb, W, kb, 0.0, W2, kb, 0, st);
     dgemm(s, N_, N_, len, ncol, kb, -1.0, V + r0, n, W2, kb, 1.0, Y + r0, ldy, 0, st);

@@ -236,20 +236,23 @@ __global__ void wait_probe_kernel(int* flag, long long limit, DevStatus* st) {
 }  // namespace
 
 void trsv_begin(cudaStream_t s, const TrsvSync& sync) {
-  trsv_begin_kernel<<<1, 1, 0, s>>>(sync.tickets, sync.epoch);
+  trsv_begin_kernel<<<1, 1, 0, ::ec::counted(s)>>>(sync.tickets, sync.epoch);
 }
 
 void trsv_pair(cudaStream_t s, int64_t n, const double* Lf, int64_t ldl, const double* Dinv,
                const double* b, double* y, double* x, const TrsvSync& sync, int grid,
-               long long limit, DevStatus* st) {
-  trsv_fwd_kernel<<<grid, 256, 0, s>>>(n, Lf, ldl, Dinv, b, y, sync.flags_fwd, sync.tickets,
-                                       sync.epoch, limit, st);
-  trsv_bwd_kernel<<<grid, 256, 0, s>>>(n, Lf, ldl, Dinv, y, x, sync.flags_bwd, sync.tickets + 1,
-                                       sync.epoch, limit, st);
+               long long limit, DevStatus* st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], s);
+  trsv_fwd_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(n, Lf, ldl, Dinv, b, y, sync.flags_fwd,
+                                                      sync.tickets, sync.epoch, limit, st);
+  if (ev) cudaEventRecord(ev[1], s);
+  trsv_bwd_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(n, Lf, ldl, Dinv, y, x, sync.flags_bwd,
+                                                      sync.tickets + 1, sync.epoch, limit, st);
+  if (ev) cudaEventRecord(ev[2], s);
 }
 
 void wait_timeout_probe(cudaStream_t s, int* flag, long long limit, DevStatus* st) {
-  wait_probe_kernel<<<1, 32, 0, s>>>(flag, limit, st);
+  wait_probe_kernel<<<1, 32, 0, ::ec::counted(s)>>>(flag, limit, st);
 }
 
 }  // namespace ec

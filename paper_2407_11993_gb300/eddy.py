@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 
 EC_FORM_PLAIN, EC_FORM_MODAL = 0, 1
 EC_MEM_HOST, EC_MEM_DEVICE = 0, 1
+EC_SOLVE_INVERSE, EC_SOLVE_SUBSTITUTION = 0, 1
 
 STATUS = {
     0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_SHAPE", 3: "EC_ERR_NOT_SPD", 4: "EC_ERR_RANK",
@@ -26,19 +27,23 @@ STATUS = {
 
 EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "ec_state_size",
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
-           "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout")
+           "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
+           "ec_launch_count")
 
 
 class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
-                ("device", c_int), ("spin_limit", c_longlong)]
+                ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
+                ("plain_solver", c_int)]
 
 
 class ec_timing(ctypes.Structure):
     _fields_ = [("elim_ms", c_double), ("factor_ms", c_double), ("reduce_ms", c_double),
                 ("tridiag_ms", c_double), ("eig_ms", c_double), ("backtransform_ms", c_double),
                 ("project_ms", c_double), ("setup_ms", c_double), ("run_ms", c_double),
-                ("run_steps", c_int64)]
+                ("run_steps", c_int64), ("fwd_ms", c_double), ("bwd_ms", c_double),
+                ("scan_ms", c_double), ("fwd_launches", c_int64), ("bwd_launches", c_int64),
+                ("scan_launches", c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "ec_error_string": (ctypes.c_char_p, [c_int]),
             "ec_destroy": (None, [P]),
             "ec_selftest_wait_timeout": (c_int, [c_longlong, POINTER(c_int)]),
+            "ec_launch_count": (c_int64, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -120,6 +126,11 @@ def check(code: int, where: str, ctx=None) -> None:
         raise EcError(code, where, info)
 
 
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().ec_launch_count())
+
+
 def selftest_wait_timeout(spin_limit: int) -> int:
     out = c_int(-1)
     check(lib().ec_selftest_wait_timeout(spin_limit, ctypes.byref(out)), "ec_selftest_wait_timeout")
@@ -136,9 +147,14 @@ class ThetaMethod:
     """
 
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
-                 device: int = 0, stream: int | None = None, spin_limit: int = 0):
+                 device: int = 0, stream: int | None = None, spin_limit: int = 0,
+                 profile: bool = False, solver: str = "inverse"):
+        if solver not in ("inverse", "substitution"):
+            raise ValueError("solver must be 'inverse' or 'substitution'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
-                        float(dt), c_void_p(stream or 0), int(device), int(spin_limit))
+                        float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
+                        int(bool(profile)),
+                        EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE)
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h

@@ -26,9 +26,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def run_gpu(eddy, p, form="plain", T=None, I0=None):
+SOLVERS = ["inverse", "substitution"]
+
+
+def run_gpu(eddy, p, form="plain", T=None, I0=None, solver="inverse"):
     T = p.T if T is None else T
-    tm = eddy.ThetaMethod(form, p.theta, p.dt)
+    tm = eddy.ThetaMethod(form, p.theta, p.dt, solver=solver)
     tm.setup(p.L, p.R, p.E if p.E.shape[0] else None, p.M if p.M.shape[1] else None,
              p.MD if p.E.shape[0] else None, p.C)
     if I0 is not None:
@@ -38,20 +41,22 @@ def run_gpu(eddy, p, form="plain", T=None, I0=None):
     return tm, probes, snaps
 
 
-def test_config1_coil_n512(eddy):
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_config1_coil_n512(eddy, solver):
     p = synth.config1()
     ref = orc.run_problem(p, "plain")
-    _, probes, _ = run_gpu(eddy, p)
+    _, probes, _ = run_gpu(eddy, p, solver=solver)
     assert probes.shape == ref.probes.shape
     assert rel(probes, ref.probes) < TOL
 
 
-@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 200, 517])
-def test_ragged_sizes_with_electrode_and_coil(eddy, n):
+@pytest.mark.parametrize("solver", SOLVERS)
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 200, 517, 1100])
+def test_ragged_sizes_with_electrode_and_coil(eddy, n, solver):
     electrodes = n >= 4
     p = synth.small(n, T=40, seed=n, electrodes=electrodes, coil=True, snap_stride=7)
     ref = orc.run_problem(p, "plain")
-    _, probes, snaps = run_gpu(eddy, p)
+    _, probes, snaps = run_gpu(eddy, p, solver=solver)
     assert rel(probes, ref.probes) < TOL
     assert rel(snaps, ref.snaps) < TOL
 
@@ -84,15 +89,16 @@ def test_initial_current_and_zero_source_decay(eddy):
     assert np.all(np.diff(W) <= 1e-12 * W[0])
 
 
-def test_resume_is_bitwise(eddy):
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_resume_is_bitwise(eddy, solver):
     p = synth.small(130, T=60, seed=9, electrodes=True, coil=True)
-    tm, full, _ = run_gpu(eddy, p)
+    tm, full, _ = run_gpu(eddy, p, solver=solver)
     state_full = tm.get_state()
-    tm2 = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm2 = eddy.ThetaMethod("plain", p.theta, p.dt, solver=solver)
     tm2.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
     a, _ = tm2.run(25, p.src[:, :26], p.iD[:, :26])
     st = tm2.get_state()
-    tm3 = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm3 = eddy.ThetaMethod("plain", p.theta, p.dt, solver=solver)
     tm3.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
     tm3.set_state(st)
     b, _ = tm3.run(35, p.src[:, 25:], p.iD[:, 25:])
@@ -115,10 +121,33 @@ def test_bounded_wait_times_out(eddy):
     assert eddy.selftest_wait_timeout(2000) == 7   # EC_ERR_TIMEOUT
 
 
-def test_config2_electrodes_n8192_first_steps(eddy):
-    """N = 8192 with the electrode step, 16 pickups: first 40 steps + snapshots."""
+@pytest.fixture(scope="module")
+def config2_ref():
     p = synth.config2(T=40, snap_stride=20)
-    ref = orc.run_problem(p, "plain")
-    _, probes, snaps = run_gpu(eddy, p)
+    return p, orc.run_problem(p, "plain")
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_config2_electrodes_n8192_first_steps(eddy, config2_ref, solver):
+    """N = 8192 with the electrode step, 16 pickups: first 40 steps + snapshots."""
+    p, ref = config2_ref
+    _, probes, snaps = run_gpu(eddy, p, solver=solver)
     assert rel(probes, ref.probes) < TOL
     assert rel(snaps, ref.snaps) < TOL
+
+
+def test_solvers_agree_and_set_step_refactors(eddy):
+    """Both solve paths give the same trajectory; set_step re-forms and re-factors Z."""
+    p = synth.small(300, T=30, seed=21, electrodes=True, coil=True, snap_stride=10)
+    q = synth.small(300, T=30, seed=21, electrodes=True, coil=True, snap_stride=10, dt=4e-6,
+                    theta=1.0)
+    ref = orc.run_problem(q, "plain")
+    outs = []
+    for solver in SOLVERS:
+        tm = eddy.ThetaMethod("plain", p.theta, p.dt, solver=solver)
+        tm.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
+        tm.set_step(q.theta, q.dt)
+        probes, snaps = tm.run(q.T, q.src, q.iD, q.snap_stride)
+        assert rel(probes, ref.probes) < TOL and rel(snaps, ref.snaps) < TOL
+        outs.append(probes)
+    assert rel(outs[0], outs[1]) < TOL
