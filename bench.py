@@ -302,13 +302,18 @@ def our_arm(args) -> None:
                 "peak_note": "FP64 peak derived from unit counts: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz "
                              f"(HBM peak {pk_kind})",
                 "avg_launch_ms": fwd_ms, "dominant_family": dominant}
-    traffic_path = os.path.join(ROOT, "profiles", "trmv_lower_traffic.json")
+    # DRAM traffic from the committed ncu summary of this kernel, scaled by N0^2
+    traffic_path = os.path.join(ROOT, "profiles", "trmv_lower_n8192.md")
     try:
+        tv = {}
         with open(traffic_path) as f:
-            tj = json.load(f)
-        if tj.get("n0") and tj.get("bytes_per_launch"):
-            roofline["traffic"] = tj["bytes_per_launch"] * (n0 * n0) / (tj["n0"] * tj["n0"])
-            roofline["traffic_note"] = tj.get("note", "")
+            for ln in f:
+                if ln.startswith("traffic_"):
+                    k, v = ln.split(":", 1)
+                    tv[k.strip()] = float(v)
+        if tv.get("traffic_bytes_per_launch") and tv.get("traffic_n0"):
+            roofline["traffic"] = tv["traffic_bytes_per_launch"] * (n0 * n0) / tv["traffic_n0"] ** 2
+            roofline["traffic_note"] = "ncu DRAM read+write of one launch (profiles/trmv_lower_n8192.md)"
     except (OSError, ValueError):
         pass
 

@@ -169,6 +169,29 @@ __device__ __forceinline__ double secular(const double* dnd, const double* znd, 
   return fma(rho, f0 + f1, 1.0);
 }
 
+// With the origin pole o removed: h(mu) = (d_o - d_o - mu) f(mu) = w_o - mu (1 + phi(mu)),
+// phi = rho sum_{j != o} z_j^2 / (dd_j - mu).  Returns f (for the bracket), h and h'.
+__device__ __forceinline__ void secular_h(const double* dnd, const double* znd, int k, int o,
+                                          double rho, double mu, double& f, double& h,
+                                          double& hp) {
+  const double dro = dnd[o];
+  double phi = 0.0, dphi = 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (j == o) continue;
+    const double r = 1.0 / ((dnd[j] - dro) - mu);
+    const double t = rho * znd[j] * znd[j] * r;
+    phi += t;
+    dphi = fma(t, r, dphi);
+  }
+  const double wo = rho * znd[o] * znd[o];
+  h = wo - mu * (1.0 + phi);
+  hp = -(1.0 + phi) - mu * dphi;
+  f = 1.0 + phi - wo / mu;
+}
+
+// Root i of the secular equation: origin at the nearer pole, then Newton steps on
+// h (smooth at the origin pole) kept inside the sign bracket of f, with bisection
+// whenever a step leaves the bracket.
 __global__ void __launch_bounds__(256) secular_kernel(int64_t bs, DcWork w) {
   const int64_t z = blockIdx.x;
   const int64_t s = z * bs;
@@ -190,15 +213,20 @@ __global__ void __launch_bounds__(256) secular_kernel(int64_t bs, DcWork w) {
     lo = 0.0;
     hi = rho;
   }
-  const double dro = dnd[o];
-  for (int it = 0; it < 2000; ++it) {
-    const double m = 0.5 * (lo + hi);
-    if (m == lo || m == hi) break;
-    if (secular(dnd, znd, k, rho, dro, m) > 0.0) hi = m;
-    else lo = m;
+  double mu = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    double f, h, hp;
+    secular_h(dnd, znd, k, o, rho, mu, f, h, hp);
+    if (f == 0.0) break;
+    if (f > 0.0) hi = mu; else lo = mu;
+    double nx = (hp != 0.0) ? mu - h / hp : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const bool done = fabs(nx - mu) <= 2.0 * EPS * fabs(nx) || nx == lo || nx == hi;
+    mu = nx;
+    if (done) break;
   }
   w.orig[s + i] = o;
-  w.mu[s + i] = 0.5 * (lo + hi);
+  w.mu[s + i] = mu;
 }
 
 __device__ __forceinline__ double root_minus_pole(const DcWork& w, int64_t s, int j, double di) {

@@ -193,7 +193,7 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
     const int64_t rb = (len + 255) / 256;
     int64_t nchunk = (4 * sms + rb - 1) / rb;
     if (nchunk < 1) nchunk = 1;
-    if (nchunk > len) nchunk = len;
+    if (nchunk > (len + 63) / 64) nchunk = (len + 63) / 64;
     while (nchunk * n > partial_cap) --nchunk;
     const int64_t kc = (len + nchunk - 1) / nchunk;
     nchunk = (len + kc - 1) / kc;
