@@ -158,6 +158,16 @@ EC_API ec_status ec_set_state(ec_ctx* ctx, const double* state, int mem);
  * column-major, U^T R_i U = 1) in the internal basis of ker E. */
 EC_API ec_status ec_get_modes(ec_ctx* ctx, double* tau, double* U, int mem);
 
+/* Plain form only: solve Z x = b, Z = L_i + theta dt R_i (the matrix of Eq. time_integration,
+ * Sec. 3.3.1), with the context's Cholesky factor and its configured solver.  b and x have
+ * length ec_state_size() and live in the internal basis of ker E; they may alias. */
+EC_API ec_status ec_solve_z(ec_ctx* ctx, const double* b, double* x, int mem);
+
+/* Plain form with EC_SOLVE_INVERSE only: copy out C^{-1}, the inverse of the lower
+ * Cholesky factor of Z (N_0 x N_0, column-major, zeros above the diagonal), so that
+ * Z^{-1} = C^{-T} C^{-1}. */
+EC_API ec_status ec_get_inverse_factor(ec_ctx* ctx, double* W, int mem);
+
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */
 EC_API ec_status ec_sync(ec_ctx* ctx);

@@ -613,6 +613,35 @@ ec_status ec_get_modes(ec_ctx* c, double* tau, double* U, int mem) {
   return collect(c);
 }
 
+ec_status ec_solve_z(ec_ctx* c, const double* b, double* x, int mem) {
+  if (!c || !b || !x) return EC_ERR_ARG;
+  if (!c->ready || c->cfg.form != EC_FORM_PLAIN) return EC_ERR_STATE;
+  if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
+  cudaSetDevice(c->cfg.device);
+  const int64_t n0 = c->n0;
+  EC_TRY(copy_in(c, c->dWork, b, (size_t)n0, mem));
+  if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
+    trmv_pair(c->stream, n0, c->dW, n0, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK,
+              c->st);
+    sum_partials(c->stream, n0, trmv_chunks(n0, TRMV_CHUNK), c->dPart2, c->dWork);
+  } else {
+    TrsvSync sy{c->dFlags, c->dFlags + (n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
+    trsv_begin(c->stream, sy);
+    trsv_pair(c->stream, n0, c->dZ, n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
+              c->trsv_grid, c->spin_limit, c->st);
+  }
+  EC_TRY(copy_out(c, x, c->dWork, (size_t)n0, mem));
+  return collect(c);
+}
+
+ec_status ec_get_inverse_factor(ec_ctx* c, double* W, int mem) {
+  if (!c || !W) return EC_ERR_ARG;
+  if (!c->ready || c->cfg.form != EC_FORM_PLAIN || c->cfg.plain_solver != EC_SOLVE_INVERSE)
+    return EC_ERR_STATE;
+  EC_TRY(copy_out(c, W, c->dW, (size_t)c->n0 * c->n0, mem));
+  return collect(c);
+}
+
 int64_t ec_launch_count(void) { return ec::g_launches.load(std::memory_order_relaxed); }
 
 ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {

@@ -90,6 +90,9 @@ void trmv_pair(cudaStream_t s, int64_t n, const double* W, int64_t ldw, const do
                double* part1, double* y, double* part2, int chunk, const DevStatus* st,
                cudaEvent_t* ev = nullptr);
 
+// out[i] = sum_q part[q * n + i], q = 0 .. nin-1 (fixed order)
+void sum_partials(cudaStream_t s, int64_t n, int nin, const double* part, double* out);
+
 // Test hook: a wait on a flag nothing sets, bounded by spin_limit.
 void wait_timeout_probe(cudaStream_t s, int* flag, long long spin_limit, DevStatus* st);
 

@@ -145,6 +145,11 @@ int trmv_chunks(int64_t n, int chunk) {
   return (int)((nblk + chunk - 1) / chunk);
 }
 
+void sum_partials(cudaStream_t s, int64_t n, int nin, const double* part, double* out) {
+  sum_partials_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0,
+                        ::ec::counted(s)>>>(n, nin, part, out);
+}
+
 void trmv_pair(cudaStream_t s, int64_t n, const double* W, int64_t ldw, const double* b,
                double* part1, double* y, double* part2, int chunk, const DevStatus* st,
                cudaEvent_t* ev) {

@@ -28,7 +28,7 @@ STATUS = {
 EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "ec_state_size",
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
-           "ec_launch_count")
+           "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor")
 
 
 class ec_config(ctypes.Structure):
@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
             "ec_destroy": (None, [P]),
             "ec_selftest_wait_timeout": (c_int, [c_longlong, POINTER(c_int)]),
             "ec_launch_count": (c_int64, []),
+            "ec_solve_z": (c_int, [P, P, P, c_int]),
+            "ec_get_inverse_factor": (c_int, [P, P, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -231,6 +233,33 @@ class ThetaMethod:
         check(lib().ec_get_modes(self._h, c_void_p(tau.ctypes.data), c_void_p(U.ctypes.data),
                                  EC_MEM_HOST), "ec_get_modes", self._h)
         return tau, U.T   # column-major in the ABI
+
+    def solve_z(self, b, mem: int = EC_MEM_HOST):
+        """x = Z^{-1} b in the internal basis (plain form)."""
+        if mem == EC_MEM_DEVICE:
+            import torch
+            x = torch.empty_like(b)
+            pb, k = _ptr(b, mem)
+            px = c_void_p(x.data_ptr())
+        else:
+            x = np.empty(self.state_size())
+            pb, k = _ptr(b, mem)
+            px = c_void_p(x.ctypes.data)
+        check(lib().ec_solve_z(self._h, pb, px, mem), "ec_solve_z", self._h)
+        return x
+
+    def inverse_factor(self, out=None, mem: int = EC_MEM_HOST):
+        """C^{-1} (N0 x N0, lower) of the plain form's Cholesky factor."""
+        n0 = self.state_size()
+        if mem == EC_MEM_DEVICE:
+            import torch
+            W = out if out is not None else torch.empty((n0, n0), dtype=torch.float64, device="cuda")
+            pw = c_void_p(W.data_ptr())
+        else:
+            W = np.empty((n0, n0)) if out is None else out
+            pw = c_void_p(W.ctypes.data)
+        check(lib().ec_get_inverse_factor(self._h, pw, mem), "ec_get_inverse_factor", self._h)
+        return W   # column-major buffer: as a row-major array this is (C^{-1})^T
 
     def timings(self) -> dict:
         t = ec_timing()

@@ -151,3 +151,28 @@ def test_solvers_agree_and_set_step_refactors(eddy):
         assert rel(probes, ref.probes) < TOL and rel(snaps, ref.snaps) < TOL
         outs.append(probes)
     assert rel(outs[0], outs[1]) < TOL
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+@pytest.mark.parametrize("n", [700, 1029])
+def test_solve_z_matches_dense_solve(eddy, solver, n):
+    """x = Z^{-1} b with Z = L + theta dt R (no electrodes: the internal basis is the identity)."""
+    p = synth.small(n, T=1, seed=31, electrodes=False, coil=True)
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt, solver=solver)
+    tm.setup(p.L, p.R, None, p.M, None, p.C)
+    b = np.random.default_rng(5).standard_normal(n)
+    x = tm.solve_z(b)
+    Z = p.L + p.dt * p.theta * p.R
+    x_ref = np.linalg.solve(Z, b)
+    assert rel(x, x_ref) < TOL
+
+
+def test_inverse_factor_export(eddy):
+    p = synth.small(300, T=1, seed=32, electrodes=False, coil=True)
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm.setup(p.L, p.R, None, p.M, None, p.C)
+    Wt = tm.inverse_factor()          # row-major view of the column-major C^{-1}
+    W = Wt.T
+    assert np.allclose(np.triu(W, 1), 0.0)
+    Z = p.L + p.dt * p.theta * p.R
+    assert rel(W.T @ W, np.linalg.inv(Z)) < 1e-10
