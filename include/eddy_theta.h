@@ -168,6 +168,33 @@ EC_API ec_status ec_solve_z(ec_ctx* ctx, const double* b, double* x, int mem);
  * Z^{-1} = C^{-T} C^{-1}. */
 EC_API ec_status ec_get_inverse_factor(ec_ctx* ctx, double* W, int mem);
 
+/* Allocation-free solve with an inverse Cholesky factor: x = Winv^T (Winv b), i.e.
+ * x = Z^{-1} b when Winv = C^{-1} and Z = C C^T (the same two triangular products
+ * the plain form runs every step; see ec_get_inverse_factor).  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device
+ * memory themselves -- e.g. a host application whose GPU memory is entirely owned
+ * by another allocator (a framework's caching pool or a fixed arena), or a
+ * real-time loop that cannot take the latency and implicit synchronisation of
+ * cudaMalloc -- and therefore cannot create a context.
+ *
+ *   n        system size, 1 <= n <= EC_NOALLOC_MAX_N (larger n: EC_ERR_SHAPE, nothing runs)
+ *   Winv     device pointer, n x n column-major with leading dimension ldw >= n; only
+ *            the lower triangle is read (the 64 x 64 diagonal blocks must hold zeros
+ *            above the diagonal, as ec_get_inverse_factor returns them)
+ *   b, x     device pointers of length n (b is read, x written; they may alias)
+ *   stream   cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Allocates nothing: no cudaMalloc or cudaFree is called.  Its scratch is a
+ * fixed-size device array inside the library (about 1.1 MB, held on every GPU
+ * that loads the library until the process exits).  The first call on a device
+ * looks up that array's device address with the device current; make that first
+ * call before any stream capture.  All calls share the array, so calls that may
+ * overlap on the GPU (different streams without ordering) race and corrupt each
+ * other's results.  The call is asynchronous: it returns after enqueueing, and
+ * reports only argument and launch errors. */
+#define EC_NOALLOC_MAX_N 8192
+EC_API ec_status ec_solve_inverse_noalloc(int64_t n, const double* Winv, int64_t ldw,
+                                          const double* b, double* x, void* stream);
+
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */
 EC_API ec_status ec_sync(ec_ctx* ctx);

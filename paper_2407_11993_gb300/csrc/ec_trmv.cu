@@ -13,6 +13,8 @@
 // partial sums are written out and summed in a fixed order by the consumer
 // (the next product, or the update kernel), so results are deterministic.
 
+#include <mutex>
+
 #include "ec_internal.h"
 
 namespace ec {
@@ -167,3 +169,74 @@ void trmv_pair(cudaStream_t s, int64_t n, const double* W, int64_t ldw, const do
 }
 
 }  // namespace ec
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the inverse-factor solve (ec_solve_inverse_noalloc).
+//
+// Its scratch (status block, chunk partial sums of both products and the
+// intermediate vector) lives in one file-scope device array sized for
+// n <= EC_NOALLOC_MAX_N.  Every GPU that loads this library holds the array
+// (about 1.1 MB) until the process exits.
+namespace ec {
+namespace {
+
+constexpr int NOALLOC_CHUNK = 16;
+constexpr int64_t NOALLOC_MAX_CHUNKS = ((EC_NOALLOC_MAX_N + NB - 1) / NB + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK;
+constexpr int64_t NOALLOC_HEAD = 32;   // doubles reserved for the status block (256 B)
+constexpr int64_t NOALLOC_DOUBLES =
+    NOALLOC_HEAD + 2 * NOALLOC_MAX_CHUNKS * EC_NOALLOC_MAX_N + EC_NOALLOC_MAX_N;
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device; looked up once per
+// device with that device current (host code cannot use the symbol itself).
+ec_status noalloc_scratch(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    cudaGetLastError();
+    return EC_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return EC_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return EC_OK;
+}
+
+}  // namespace
+}  // namespace ec
+
+extern "C" ec_status ec_solve_inverse_noalloc(int64_t n, const double* Winv, int64_t ldw,
+                                              const double* b, double* x, void* stream) {
+  using namespace ec;
+  if (!Winv || !b || !x || n < 1 || ldw < n) return EC_ERR_ARG;
+  if (n > EC_NOALLOC_MAX_N) return EC_ERR_SHAPE;
+  double* base = nullptr;
+  ec_status st = noalloc_scratch(&base);
+  if (st != EC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStatus* dst = reinterpret_cast<DevStatus*>(base);
+  const int nc = trmv_chunks(n, NOALLOC_CHUNK);
+  double* part1 = base + NOALLOC_HEAD;
+  double* y = part1 + (int64_t)nc * n;
+  double* part2 = y + n;
+  if (cudaMemsetAsync(dst, 0, sizeof(DevStatus), s) != cudaSuccess) {
+    cudaGetLastError();
+    return EC_ERR_CUDA;
+  }
+  trmv_pair(s, n, Winv, ldw, b, part1, y, part2, NOALLOC_CHUNK, dst);
+  sum_partials(s, n, nc, part2, x);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+

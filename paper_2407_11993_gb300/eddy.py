@@ -28,7 +28,8 @@ STATUS = {
 EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "ec_state_size",
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
-           "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor")
+           "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc")
+NOALLOC_MAX_N = 8192
 
 
 class ec_config(ctypes.Structure):
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "ec_launch_count": (c_int64, []),
             "ec_solve_z": (c_int, [P, P, P, c_int]),
             "ec_get_inverse_factor": (c_int, [P, P, c_int]),
+            "ec_solve_inverse_noalloc": (c_int, [c_int64, P, c_int64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -137,6 +139,21 @@ def selftest_wait_timeout(spin_limit: int) -> int:
     out = c_int(-1)
     check(lib().ec_selftest_wait_timeout(spin_limit, ctypes.byref(out)), "ec_selftest_wait_timeout")
     return out.value
+
+
+def solve_inverse_noalloc(Winv, b, x, stream=None, n: int | None = None) -> None:
+    """x = Winv^T (Winv b) on device tensors without any device allocation.
+
+    ``Winv`` is the column-major inverse Cholesky factor as returned by
+    ``ThetaMethod.inverse_factor(mem=EC_MEM_DEVICE)`` (an (n, n) tensor whose
+    memory is C^{-1} in column-major order).  ``stream`` is a raw cudaStream_t.
+    """
+    n = int(b.shape[0]) if n is None else int(n)
+    pw, k1 = _ptr(Winv, EC_MEM_DEVICE)
+    pb, k2 = _ptr(b, EC_MEM_DEVICE)
+    px, k3 = _ptr(x, EC_MEM_DEVICE)
+    check(lib().ec_solve_inverse_noalloc(n, pw, n, pb, px, c_void_p(stream or 0)),
+          "ec_solve_inverse_noalloc")
 
 
 class ThetaMethod:
