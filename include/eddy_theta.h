@@ -195,6 +195,22 @@ EC_API ec_status ec_get_inverse_factor(ec_ctx* ctx, double* W, int mem);
 EC_API ec_status ec_solve_inverse_noalloc(int64_t n, const double* Winv, int64_t ldw,
                                           const double* b, double* x, void* stream);
 
+/* Plain form, no electrodes (m = 0), EC_SOLVE_INVERSE: value and gradient of the probe
+ * misfit  J = sum_{k=1..T} || C I^k - v^k ||^2  of a T-step run from the current state,
+ * by the discrete adjoint of Eq. time_integration (Sec. 3.3.1):
+ *   Z lambda^k = (Z - dt R) lambda^{k+1} + 2 C^T (C I^k - v^k),  k = T..1, lambda^{T+1} = 0.
+ * The paper has no gradient; this serves inversion (e.g. resistivity from probe signals).
+ *   src        s x (T+1) coil currents, as for ec_run
+ *   v          T x p target probe signals (row k-1 = v^k)
+ *   ckpt_every states are checkpointed every ckpt_every steps and each segment is
+ *              recomputed once in the backward sweep (memory n x (T/ckpt_every + ckpt_every + 2))
+ *   J          1 value;  dJ_dRdiag: n values, dJ/dR_ee (R's diagonal entries);
+ *   dJ_dsrc    s x (T+1), dJ/ds^k_j.  Any output may be NULL.
+ * The state after the call is I^T of the forward run (as after ec_run). */
+EC_API ec_status ec_grad(ec_ctx* ctx, int64_t T, const double* src, const double* v,
+                         int64_t ckpt_every, double* J, double* dJ_dRdiag, double* dJ_dsrc,
+                         int mem);
+
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */
 EC_API ec_status ec_sync(ec_ctx* ctx);

@@ -642,6 +642,107 @@ ec_status ec_get_inverse_factor(ec_ctx* c, double* W, int mem) {
   return collect(c);
 }
 
+ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int64_t ckpt,
+                   double* J, double* dJ_dRdiag, double* dJ_dsrc, int mem) {
+  if (!c || T < 1 || !v || ckpt < 1) return EC_ERR_ARG;
+  if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
+  if (!c->ready || c->cfg.form != EC_FORM_PLAIN) return EC_ERR_STATE;
+  if (c->m != 0 || c->P < 1 || c->cfg.plain_solver != EC_SOLVE_INVERSE) return EC_ERR_UNSUPPORTED;
+  if (c->S > 0 && !src) return EC_ERR_ARG;
+  cudaSetDevice(c->cfg.device);
+  const int64_t n = c->n0;
+  const int S = c->S, P = c->P;
+  const double dt = c->cfg.dt, theta = c->cfg.theta;
+  if (ckpt > T) ckpt = T;
+  const int64_t nseg = (T + ckpt - 1) / ckpt;
+  double *probes = nullptr, *vd = nullptr, *ck = nullptr, *seg = nullptr, *mu = nullptr;
+  double *gR = nullptr, *lamA = nullptr, *lamB = nullptr, *rhs = nullptr, *fin = nullptr;
+  double *Jd = nullptr, *gs = nullptr, *part = nullptr;
+  const int grid = c->update_grid;
+  auto release = [&]() {
+    dfree(probes); dfree(vd); dfree(ck); dfree(seg); dfree(mu); dfree(gR); dfree(lamA);
+    dfree(lamB); dfree(rhs); dfree(fin); dfree(Jd); dfree(gs); dfree(part);
+  };
+  ec_status rc = EC_OK;
+  if ((rc = alloc(&probes, (size_t)T * P)) || (rc = alloc(&vd, (size_t)T * P)) ||
+      (rc = alloc(&ck, (size_t)n * (nseg + 1))) || (rc = alloc(&seg, (size_t)n * (ckpt + 1))) ||
+      (rc = alloc(&mu, (size_t)(S > 0 ? S : 1) * (T + 2))) || (rc = alloc(&gR, (size_t)n)) ||
+      (rc = alloc(&lamA, (size_t)n)) || (rc = alloc(&lamB, (size_t)n)) ||
+      (rc = alloc(&rhs, (size_t)n)) || (rc = alloc(&fin, (size_t)n)) || (rc = alloc(&Jd, 1)) ||
+      (rc = alloc(&gs, (size_t)(S > 0 ? S : 1) * (T + 1))) ||
+      (rc = alloc(&part, (size_t)grid * (S > 0 ? S : 1)))) {
+    release();
+    return rc;
+  }
+  cudaStream_t st = c->stream;
+  if ((rc = grow(&c->dSrc, c->srcCap, (size_t)(S > 0 ? S : 1) * (T + 1))) ||
+      (rc = grow(&c->dIDs, c->idsCap, (size_t)(T + 1))) ||
+      (rc = copy_in(c, c->dSrc, src, (size_t)S * (T + 1), mem)) ||
+      (rc = copy_in(c, vd, v, (size_t)T * P, mem))) {
+    release();
+    return rc;
+  }
+  cudaMemsetAsync(mu, 0, sizeof(double) * (S > 0 ? S : 1) * (T + 2), st);
+  cudaMemsetAsync(gR, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(lamA, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(lamB, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(rhs, 0, sizeof(double) * n, st);
+  const int nc = trmv_chunks(n, TRMV_CHUNK);
+  // forward pass with checkpoints every ckpt steps
+  cudaMemsetAsync(c->dK, 0, sizeof(int64_t), st);
+  copy_matrix(st, n, 1, c->dIi, n, ck, n);
+  StepArgs a = step_args(c, T, probes, nullptr, 0);
+  for (int64_t k = 0; k < T; ++k) {
+    plain_rhs(st, a);
+    trmv_pair(st, n, c->dW, n, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
+    plain_update(st, a, c->update_grid, 0);
+    if ((k + 1) % ckpt == 0) copy_matrix(st, n, 1, c->dIi, n, ck + ((k + 1) / ckpt) * n, n);
+  }
+  copy_matrix(st, n, 1, c->dIi, n, fin, n);
+  misfit(st, T * P, probes, vd, Jd);
+  // backward pass, segment by segment, recomputing the segment's states
+  StepArgs ar = step_args(c, T, nullptr, nullptr, 0);
+  double* lam_next = lamA;
+  double* lam = lamB;
+  for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+    const int64_t k0 = sg * ckpt, k1 = (k0 + ckpt < T) ? k0 + ckpt : T;
+    copy_matrix(st, n, 1, ck + sg * n, n, c->dIi, n);
+    copy_matrix(st, n, 1, ck + sg * n, n, seg, n);
+    plain_update(st, ar, c->update_grid, 1);
+    cudaMemcpyAsync(c->dK, &k0, sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);   // k0 lives on the host stack
+    for (int64_t k = k0; k < k1; ++k) {
+      plain_rhs(st, ar);
+      trmv_pair(st, n, c->dW, n, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
+      plain_update(st, ar, c->update_grid, 0);
+      copy_matrix(st, n, 1, c->dIi, n, seg + (k - k0 + 1) * n, n);
+    }
+    for (int64_t k = k1; k > k0; --k) {
+      adj_rhs(st, n, P, dt, c->csr, lam_next, rhs, probes + (k - 1) * P, vd + (k - 1) * P, c->dC);
+      trmv_pair(st, n, c->dW, n, rhs, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
+      sum_partials(st, n, nc, c->dPart2, lam);
+      adj_accum(st, n, S, dt, theta, lam, seg + (k - k0) * n, seg + (k - k0 - 1) * n, gR, c->dM,
+                part, c->dCounter, mu + k, T + 2, grid);
+      double* t = lam_next;
+      lam_next = lam;
+      lam = t;
+    }
+  }
+  (void)lam;
+  // dJ/ds^j = mu^{j+1} - mu^j (mu is S x (T+2), zero at both ends)
+  if (S > 0) dsrc(st, S, T, mu, gs);
+  // restore the end-of-forward state
+  copy_matrix(st, n, 1, fin, n, c->dIi, n);
+  plain_update(st, ar, c->update_grid, 1);
+  rc = collect(c);
+  if (rc == EC_OK && J) rc = copy_out(c, J, Jd, 1, mem);
+  if (rc == EC_OK && dJ_dRdiag) rc = copy_out(c, dJ_dRdiag, gR, (size_t)n, mem);
+  if (rc == EC_OK && dJ_dsrc && S > 0) rc = copy_out(c, dJ_dsrc, gs, (size_t)S * (T + 1), mem);
+  if (rc == EC_OK) rc = collect(c);
+  release();
+  return rc;
+}
+
 int64_t ec_launch_count(void) { return ec::g_launches.load(std::memory_order_relaxed); }
 
 ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {

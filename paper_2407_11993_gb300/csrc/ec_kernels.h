@@ -72,4 +72,13 @@ void plain_snapshot(cudaStream_t s, const StepArgs& a);
 // out = R_i I_i for the state in a.Ii (needs a.dots current for that state).
 void ri_apply(cudaStream_t s, const StepArgs& a, double* out);
 
+// ---- ec_adjoint.cu: misfit gradient of the plain form ---------------------
+void adj_rhs(cudaStream_t s, int64_t n, int P, double dt, const Csr& R, const double* lam_next,
+             double* rhs, const double* probes_row, const double* v_row, const double* Ct);
+void adj_accum(cudaStream_t s, int64_t n, int S, double dt, double theta, const double* lam,
+               const double* Ik, const double* Ikm1, double* gR, const double* M, double* partial,
+               unsigned* counter, double* mu_out, int64_t mu_stride, int grid);
+void misfit(cudaStream_t s, int64_t count, const double* probes, const double* v, double* J);
+void dsrc(cudaStream_t s, int S, int64_t T, const double* mu, double* out);
+
 }  // namespace ec

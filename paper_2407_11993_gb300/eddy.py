@@ -28,7 +28,8 @@ STATUS = {
 EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "ec_state_size",
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
-           "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc")
+           "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
+           "ec_grad")
 NOALLOC_MAX_N = 8192
 
 
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "ec_solve_z": (c_int, [P, P, P, c_int]),
             "ec_get_inverse_factor": (c_int, [P, P, c_int]),
             "ec_solve_inverse_noalloc": (c_int, [c_int64, P, c_int64, P, P, P]),
+            "ec_grad": (c_int, [P, c_int64, P, P, c_int64, P, P, P, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -277,6 +279,21 @@ class ThetaMethod:
             pw = c_void_p(W.ctypes.data)
         check(lib().ec_get_inverse_factor(self._h, pw, mem), "ec_get_inverse_factor", self._h)
         return W   # column-major buffer: as a row-major array this is (C^{-1})^T
+
+    def grad(self, T: int, src, v, ckpt_every: int = 250):
+        """(J, dJ/dR_diag (N,), dJ/dsrc (S, T+1)) of J = sum_k ||C I^k - v^k||^2 (host arrays).
+
+        ``v`` is (P, T) like the probe outputs of ``run``.
+        """
+        J = np.zeros(1)
+        gR = np.empty(self.n)
+        gs = np.empty((self.S, T + 1))
+        ps, k1 = _ptr(src if self.S else None, EC_MEM_HOST)
+        pv, k2 = _ptr(np.ascontiguousarray(np.asarray(v).T), EC_MEM_HOST)
+        check(lib().ec_grad(self._h, int(T), ps, pv, int(ckpt_every), c_void_p(J.ctypes.data),
+                            c_void_p(gR.ctypes.data), c_void_p(gs.ctypes.data) if self.S else None,
+                            EC_MEM_HOST), "ec_grad", self._h)
+        return float(J[0]), gR, gs
 
     def timings(self) -> dict:
         t = ec_timing()
