@@ -81,7 +81,22 @@ typedef struct ec_config {
   long long spin_limit;   /* polls before a kernel-side wait gives up (EC_ERR_TIMEOUT); 0 = default */
   int profile;            /* nonzero: ec_run times its dominant kernels with CUDA events (see ec_timing) */
   int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
+  int precision;          /* modal form: EC_PREC_FP64 (default) or EC_PREC_BF16, see below */
 } ec_config;
+
+/* Arithmetic of the modal form's dense contractions.  The Cholesky of R_i, the
+ * pencil reduction, the eigensolve and the per-mode recurrence are FP64 in every
+ * variant (tau and mode orthogonality need it).
+ *   EC_PREC_FP64  projections U^T [R_D | L_D | M_0], U^T (C K)^T and the snapshot
+ *                 reconstruction U X in FP64.
+ *   EC_PREC_BF16  the same three products with BF16 operands on the tensor cores
+ *                 (tcgen05), FP32 accumulation; each product carries BF16 rounding
+ *                 (2^-9 relative per entry), which cancellation in the modal sums
+ *                 can amplify (see ec_gemm_bf16 and the documented error tables).
+ *   EC_PREC_BF16X3  split BF16: each operand is stored as hi + lo BF16 parts and each
+ *                 product is hi*hi + hi*lo + lo*hi on the tensor cores, summed in
+ *                 FP64 (about 2^-16 relative per entry, three times the tensor work). */
+enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2 };
 
 /* How the plain form applies its Cholesky factor C each step (Sec. 3.3.1).
  *   EC_SOLVE_INVERSE       C^{-1} is formed once at setup (N^3/3 extra flops); each
@@ -210,6 +225,12 @@ EC_API ec_status ec_solve_inverse_noalloc(int64_t n, const double* Winv, int64_t
 EC_API ec_status ec_grad(ec_ctx* ctx, int64_t T, const double* src, const double* v,
                          int64_t ckpt_every, double* J, double* dJ_dRdiag, double* dJ_dsrc,
                          int mem);
+
+/* Dense product on the tensor cores: C = bf16(A) bf16(B) with FP32 accumulation (tcgen05,
+ * the kernel behind EC_PREC_BF16).  Device pointers, column-major FP64: A is M x K, B is
+ * K x N, C is M x N; inputs are rounded to BF16 into temporary buffers.  Synchronous. */
+EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, const double* B,
+                              double* C, void* stream);
 
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */

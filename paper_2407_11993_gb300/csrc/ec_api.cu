@@ -276,6 +276,9 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
   if (cfg->form != EC_FORM_PLAIN && cfg->form != EC_FORM_MODAL) return EC_ERR_ARG;
   if (cfg->plain_solver != EC_SOLVE_INVERSE && cfg->plain_solver != EC_SOLVE_SUBSTITUTION)
     return EC_ERR_ARG;
+  if (cfg->precision != EC_PREC_FP64 && cfg->precision != EC_PREC_BF16 &&
+      cfg->precision != EC_PREC_BF16X3)
+    return EC_ERR_ARG;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
@@ -451,6 +454,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     ma.Gsrc = c->dGsrc; ma.RD = c->dRD; ma.LD = c->dLD; ma.Msrc = c->dM + c->m; ma.ldM = n;
     ma.CK = c->dC + c->m; ma.ldC = n;
     ma.theta = c->cfg.theta; ma.dt = c->cfg.dt;
+    ma.precision = c->cfg.precision;
     ma.st = c->st;
     EC_TRY(modal_setup(c->stream, c->modal, ma, &c->tim));
     EC_TRY(collect(c));

@@ -27,6 +27,7 @@
 
 #include "ec_modal.h"
 #include "ec_sytrd.h"
+#include "ec_tc.h"
 
 namespace ec {
 
@@ -47,6 +48,14 @@ struct ModalState {
   size_t partialCap = 0;
   double* small = nullptr;    // m x nsnap scratch (x2)
   size_t smallCap = 0;
+  // reduced-precision copies (EC_PREC_BF16)
+  int precision = EC_PREC_FP64;
+  __nv_bfloat16* Ubf_rm = nullptr;   // U, K-major for U x           (n0 x ld)
+  __nv_bfloat16* Ubf_cm = nullptr;   // U^T, K-major for U^T y        (n0 x ld)
+  __nv_bfloat16* Ubf_rm_lo = nullptr;   // rounding remainders (EC_PREC_BF16X3)
+  __nv_bfloat16* Ubf_cm_lo = nullptr;
+  __nv_bfloat16* Ybf = nullptr;      // right operand (N x ld), hi and lo halves
+  size_t ybfCap = 0;
   // setup scratch
   double* DinvR = nullptr;
   const double* CR = nullptr;
@@ -245,6 +254,34 @@ __global__ void snap_particular_kernel(int64_t n, int m, int64_t nsnap, int64_t 
 
 }  // namespace
 
+#define MS_TRY(x)               \
+  do {                          \
+    ec_status _s = (x);         \
+    if (_s != EC_OK) return _s; \
+  } while (0)
+
+// C (n0 x N, column-major, ldc) = op(U) Y with Y n0 x N column-major (lds); op(U) = U^T
+// (trans_u = 1) or U (trans_u = 0); arithmetic per ms->precision.
+ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, const double* Y,
+                        int64_t lds, double* C, int64_t ldc, DevStatus* st) {
+  const int64_t n0 = ms->n0;
+  if (N <= 0) return EC_OK;
+  if (ms->precision == EC_PREC_FP64) {
+    dgemm(s, trans_u ? T_ : N_, N_, n0, N, n0, 1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
+    return EC_OK;
+  }
+  const int64_t ld = bf16_ld(n0);
+  const bool x3 = ms->precision == EC_PREC_BF16X3;
+  MS_TRY(grow_n(&ms->Ybf, ms->ybfCap, (size_t)(x3 ? 2 : 1) * N * ld));
+  __nv_bfloat16* yh = ms->Ybf;
+  __nv_bfloat16* yl = x3 ? ms->Ybf + (size_t)N * ld : nullptr;
+  to_bf16(s, N, n0, Y, lds, 1, yh, ld, yl);
+  const __nv_bfloat16* ah = trans_u ? ms->Ubf_cm : ms->Ubf_rm;
+  const __nv_bfloat16* al = trans_u ? ms->Ubf_cm_lo : ms->Ubf_rm_lo;
+  if (x3) return tc_gemm_bf16x3(s, n0, N, n0, 1.0, ah, al, ld, yh, yl, ld, C, ldc, st);
+  return tc_gemm_bf16(s, n0, N, n0, 1.0, ah, ld, yh, ld, 0.0, C, ldc, st);
+}
+
 ModalState* modal_create() { return new ModalState(); }
 
 void modal_free(ModalState* ms) {
@@ -253,6 +290,9 @@ void modal_free(ModalState* ms) {
                   ms->small, ms->DinvR};
   for (double* p : ps)
     if (p) cudaFree(p);
+  __nv_bfloat16* bs[] = {ms->Ubf_rm, ms->Ubf_cm, ms->Ubf_rm_lo, ms->Ubf_cm_lo, ms->Ybf};
+  for (__nv_bfloat16* p : bs)
+    if (p) cudaFree(p);
   delete ms;
 }
 
@@ -260,11 +300,6 @@ double* modal_state(ModalState* ms) { return ms->x; }
 const double* modal_tau(ModalState* ms) { return ms->tau; }
 const double* modal_U(ModalState* ms) { return ms->U; }
 
-#define MS_TRY(x)               \
-  do {                          \
-    ec_status _s = (x);         \
-    if (_s != EC_OK) return _s; \
-  } while (0)
 
 ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, ec_timing* tim) {
   const int64_t n0 = a.n0, ld = a.ld;
@@ -344,6 +379,19 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   tim->backtransform_ms = t.ms();
   cleanup();
   // a7: projections and per-mode coefficients
+  ms->precision = a.precision;
+  if (a.precision != EC_PREC_FP64) {
+    const int64_t ld = bf16_ld(n0);
+    const bool x3 = a.precision == EC_PREC_BF16X3;
+    MS_TRY(alloc_n(&ms->Ubf_rm, (size_t)n0 * ld));
+    MS_TRY(alloc_n(&ms->Ubf_cm, (size_t)n0 * ld));
+    if (x3) {
+      MS_TRY(alloc_n(&ms->Ubf_rm_lo, (size_t)n0 * ld));
+      MS_TRY(alloc_n(&ms->Ubf_cm_lo, (size_t)n0 * ld));
+    }
+    to_bf16(s, n0, n0, ms->U, n0, 0, ms->Ubf_rm, ld, x3 ? ms->Ubf_rm_lo : nullptr);
+    to_bf16(s, n0, n0, ms->U, n0, 1, ms->Ubf_cm, ld, x3 ? ms->Ubf_cm_lo : nullptr);
+  }
   if (ms->ncoef > 0) {
     double* Gm = nullptr;
     if (alloc_n(&Gm, (size_t)n0 * ms->ncoef)) return EC_ERR_OOM;
@@ -352,11 +400,12 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
       copy_matrix(s, n0, a.m, a.LD, n0, Gm + n0 * a.m, n0);
     }
     if (a.S > 0) copy_matrix(s, n0, a.S, a.Msrc, a.ldM, Gm + n0 * 2 * a.m, n0);
-    dgemm(s, T_, N_, n0, ms->ncoef, n0, 1.0, ms->U, n0, Gm, n0, 0.0, ms->B, n0, 0, a.st);
+    ec_status rc2 = modal_product(s, ms, 1, ms->ncoef, Gm, n0, ms->B, n0, a.st);
     cudaStreamSynchronize(s);
     cudaFree(Gm);
+    if (rc2 != EC_OK) return rc2;
   }
-  if (a.P > 0) dgemm(s, T_, N_, n0, a.P, n0, 1.0, ms->U, n0, a.CK, a.ldC, 0.0, ms->Gt, n0, 0, a.st);
+  if (a.P > 0) MS_TRY(modal_product(s, ms, 1, a.P, a.CK, a.ldC, ms->Gt, n0, a.st));
   coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n0, ms->tau, ms->theta, ms->dt, ms->ac);
   tim->project_ms = t.ms();
@@ -413,7 +462,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
     const int m = ms->m;
     // rows m.. of each snapshot: U x; rows 0..m-1: 0; then apply Q and add the particular field
     if (m > 0) cudaMemsetAsync(sa.snaps, 0, sizeof(double) * (size_t)n * nsnap, s);
-    dgemm(s, N_, N_, n0, nsnap, n0, 1.0, ms->U, n0, ms->Xsnap, n0, 0.0, sa.snaps + m, n, 0, sa.st);
+    MS_TRY(modal_product(s, ms, 0, nsnap, ms->Xsnap, n0, sa.snaps + m, n, sa.st));
     if (m > 0) {
       MS_TRY(grow_n(&ms->small, ms->smallCap, (size_t)2 * m * nsnap));
       one_sided_q(s, n, m, sa.snaps, nsnap, sa.V, sa.Tm, ms->small, ms->small + m * nsnap, sa.st);

@@ -24,6 +24,7 @@ struct ModalSetupArgs {
   const double* CK;    // n0 x P  ((C K)^T, ld ldC)
   int64_t ldC;
   double theta, dt;
+  int precision;       // EC_PREC_*
   DevStatus* st;
 };
 

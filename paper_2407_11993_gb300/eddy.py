@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 EC_FORM_PLAIN, EC_FORM_MODAL = 0, 1
 EC_MEM_HOST, EC_MEM_DEVICE = 0, 1
 EC_SOLVE_INVERSE, EC_SOLVE_SUBSTITUTION = 0, 1
+EC_PREC_FP64, EC_PREC_BF16, EC_PREC_BF16X3 = 0, 1, 2
+_PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3}
 
 STATUS = {
     0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_SHAPE", 3: "EC_ERR_NOT_SPD", 4: "EC_ERR_RANK",
@@ -29,14 +31,14 @@ EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
            "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
-           "ec_grad")
+           "ec_grad", "ec_gemm_bf16")
 NOALLOC_MAX_N = 8192
 
 
 class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
-                ("plain_solver", c_int)]
+                ("plain_solver", c_int), ("precision", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -91,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "ec_get_inverse_factor": (c_int, [P, P, c_int]),
             "ec_solve_inverse_noalloc": (c_int, [c_int64, P, c_int64, P, P, P]),
             "ec_grad": (c_int, [P, c_int64, P, P, c_int64, P, P, P, c_int]),
+            "ec_gemm_bf16": (c_int, [c_int64, c_int64, c_int64, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -132,6 +135,22 @@ def check(code: int, where: str, ctx=None) -> None:
         raise EcError(code, where, info)
 
 
+def gemm_bf16(A, B, C=None, stream=None):
+    """C = bf16(A) bf16(B), FP32 accumulation on the tensor cores (CUDA float64 tensors)."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    # column-major views: pass A^T / B^T row-major buffers
+    At = A.t().contiguous()
+    Bt = B.t().contiguous()
+    Ct = torch.empty((N, M), dtype=torch.float64, device=A.device) if C is None else C
+    check(lib().ec_gemm_bf16(M, N, K, c_void_p(At.data_ptr()), c_void_p(Bt.data_ptr()),
+                             c_void_p(Ct.data_ptr()), c_void_p(stream or 0)), "ec_gemm_bf16")
+    return Ct.t()
+
+
 def launch_count() -> int:
     """Kernels the library has launched in this process so far."""
     return int(lib().ec_launch_count())
@@ -169,13 +188,16 @@ class ThetaMethod:
 
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
-                 profile: bool = False, solver: str = "inverse"):
+                 profile: bool = False, solver: str = "inverse", precision: str = "fp64"):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
+        if precision not in _PREC:
+            raise ValueError("precision must be 'fp64', 'bf16' or 'bf16x3'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
-                        EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE)
+                        EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
+                        _PREC[precision])
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h
