@@ -46,6 +46,8 @@ struct ModalState {
   size_t xsnapCap = 0;
   double* partial = nullptr;
   size_t partialCap = 0;
+  double* chunkbuf = nullptr;    // xend, apow, xstart (3 x nchunk x n0)
+  size_t chunkCap = 0;
   double* small = nullptr;    // m x nsnap scratch (x2)
   size_t smallCap = 0;
   // reduced-precision copies (EC_PREC_BF16)
@@ -64,9 +66,10 @@ struct ModalState {
 
 namespace {
 
-constexpr int MT = 256;          // modes per CTA
-constexpr int TCHUNK = 4096;     // time steps per scan launch
-constexpr int TSUB = 32;         // steps buffered in shared memory per reduction
+constexpr int MT = 256;            // modes per CTA
+constexpr int TS = 16;             // steps per shared-memory block of the probe contraction
+constexpr int64_t SUPER = 32768;   // steps per launch group (bounds the partial-sum buffer)
+constexpr int64_t CH_MIN = 1024;   // shortest time chunk; runs up to this length are one chunk
 
 cudaError_t dalloc(void** p, size_t b) { return cudaMalloc(p, b ? b : 8); }
 
@@ -142,7 +145,10 @@ __device__ __forceinline__ double srcv(const double* a, int64_t T, int row, int6
 }
 
 struct ScanArgs {
-  int64_t n0, T, k0, kn;      // steps k0 .. k0+kn-1 of a run of T steps
+  int64_t n0, T;              // T: steps of the whole run (source arrays hold T+1 samples)
+  int64_t k0, kn;             // this launch group: steps k0 .. k0+kn-1
+  int64_t ch;                 // chunk length; chunk g covers [k0 + g ch, k0 + (g+1) ch)
+  int nchunk;
   int m, S, P, ncoef;
   double theta, dt;
   const double* ac;
@@ -150,79 +156,135 @@ struct ScanArgs {
   const double* Gt;
   const double* src;
   const double* iD;
-  double* x;
+  const double* x;            // state at k0
+  double* xout;               // state at k0 + kn
+  double* xend;               // nchunk x n0: chunk end state from a zero start (pass 1)
+  double* apow;               // nchunk x n0: a_n^(chunk length)
+  double* xstart;             // nchunk x n0: true chunk start states (carry pass)
   double* partial;            // nblk x kn x P
   double* Xsnap;              // n0 x nsnap
   int64_t stride;
 };
 
-__global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
+// Coefficient of projected source column c in beta^k (Sec. 3.3.2 with the Cholesky-form
+// right-hand side): [-dt i_D^k - theta dt d i_D | -d i_D | -d i_0].
+__device__ __forceinline__ double beta_coef(const ScanArgs& a, int c, int64_t k) {
+  const int m = a.m;
+  if (c < m) {
+    const double d0 = srcv(a.iD, a.T, c, k), d1 = srcv(a.iD, a.T, c, k + 1);
+    return -a.dt * d0 - a.theta * a.dt * (d1 - d0);
+  }
+  if (c < 2 * m) return -(srcv(a.iD, a.T, c - m, k + 1) - srcv(a.iD, a.T, c - m, k));
+  return -(srcv(a.src, a.T, c - 2 * m, k + 1) - srcv(a.src, a.T, c - 2 * m, k));
+}
+
+__device__ __forceinline__ void chunk_range(const ScanArgs& a, int g, int64_t& c0, int64_t& c1) {
+  c0 = a.k0 + (int64_t)g * a.ch;
+  c1 = c0 + a.ch;
+  if (c1 > a.k0 + a.kn) c1 = a.k0 + a.kn;
+}
+
+// Pass 1: every chunk from a zero start -> end state and a^len (no outputs).
+__global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
   extern __shared__ double smem[];
-  const int nc = a.ncoef;
-  const int ncs = nc > 0 ? nc : 1;
-  const int Ps = a.P > 0 ? a.P : 1;
-  double* coef = smem;                           // [TSUB][ncs]
-  double* red = smem + TSUB * ncs;               // [MT/32][TSUB][Ps]
+  const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
+  double* coef = smem;   // [TS][ncs]
+  const int g = blockIdx.y;
+  int64_t c0, c1;
+  chunk_range(a, g, c0, c1);
   const int64_t nmode = blockIdx.x * (int64_t)MT + threadIdx.x;
   const bool live = nmode < a.n0;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double an = 0.0, cn = 0.0, x = 0.0;
-  double b[2 * MAXM + 64];
-  double g[MAXD];
+  double an = 0.0, cn = 0.0, b[2 * MAXM + 64];
   if (live) {
     an = a.ac[nmode];
     cn = a.ac[a.n0 + nmode];
-    x = a.x[nmode];
     for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
-    for (int p = 0; p < a.P; ++p) g[p] = a.Gt[nmode + (int64_t)p * a.n0];
-  } else {
-    for (int c = 0; c < nc; ++c) b[c] = 0.0;
-    for (int p = 0; p < a.P; ++p) g[p] = 0.0;
   }
-  const int m = a.m;
-  for (int64_t t0 = 0; t0 < a.kn; t0 += TSUB) {
-    const int nt = (int)((a.kn - t0) < TSUB ? (a.kn - t0) : TSUB);
-    // per-step source coefficients of beta^k for this sub-chunk
-    for (int idx = threadIdx.x; idx < nt * nc; idx += MT) {
-      const int tt = idx / nc, c = idx % nc;
-      const int64_t k = a.k0 + t0 + tt;
-      double v;
-      if (c < m) {
-        const double d0 = srcv(a.iD, a.T, c, k), d1 = srcv(a.iD, a.T, c, k + 1);
-        v = -a.dt * d0 - a.theta * a.dt * (d1 - d0);
-      } else if (c < 2 * m) {
-        v = -(srcv(a.iD, a.T, c - m, k + 1) - srcv(a.iD, a.T, c - m, k));
-      } else {
-        v = -(srcv(a.src, a.T, c - 2 * m, k + 1) - srcv(a.src, a.T, c - 2 * m, k));
+  double x = 0.0, ap = 1.0;
+  for (int64_t t0 = c0; t0 < c1; t0 += TS) {
+    const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nt * nc; idx += MT)
+      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc);
+    __syncthreads();
+    if (live)
+      for (int tt = 0; tt < nt; ++tt) {
+        double beta = 0.0;
+        for (int c = 0; c < nc; ++c) beta = fma(b[c], coef[tt * ncs + c], beta);
+        x = fma(an, x, cn * beta);
+        ap *= an;
       }
-      coef[tt * ncs + c] = v;
+  }
+  if (live) {
+    a.xend[(int64_t)g * a.n0 + nmode] = x;
+    a.apow[(int64_t)g * a.n0 + nmode] = ap;
+  }
+}
+
+// Carry: true start state of every chunk (chunk 0 starts from the state itself).
+__global__ void modal_carry_kernel(ScanArgs a) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < a.n0;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    double xs = a.x[n];
+    for (int g = 0; g < a.nchunk; ++g) {
+      a.xstart[(int64_t)g * a.n0 + n] = xs;
+      xs = fma(a.apow[(int64_t)g * a.n0 + n], xs, a.xend[(int64_t)g * a.n0 + n]);
     }
+  }
+}
+
+// Pass 2: every chunk replayed from its true start with the outputs: snapshots and
+// per-CTA probe partials (G x over the CTA's modes, as a shared-memory block product
+// of TS steps at a time).
+__global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
+  extern __shared__ double smem[];
+  const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
+  const int P = a.P;
+  double* coef = smem;                  // [TS][ncs]
+  double* X = coef + TS * ncs;          // [MT][TS + 1]
+  double* Gs = X + MT * (TS + 1);       // [P][MT]
+  const int g = blockIdx.y;
+  int64_t c0, c1;
+  chunk_range(a, g, c0, c1);
+  const int tid = threadIdx.x;
+  const int64_t nmode = blockIdx.x * (int64_t)MT + tid;
+  const bool live = nmode < a.n0;
+  double an = 0.0, cn = 0.0, x = 0.0, b[2 * MAXM + 64];
+  if (live) {
+    an = a.ac[nmode];
+    cn = a.ac[a.n0 + nmode];
+    x = (g == 0) ? a.x[nmode] : a.xstart[(int64_t)g * a.n0 + nmode];
+    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
+  }
+  for (int p = 0; p < P; ++p) Gs[p * MT + tid] = live ? a.Gt[nmode + (int64_t)p * a.n0] : 0.0;
+  for (int64_t t0 = c0; t0 < c1; t0 += TS) {
+    const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
+    __syncthreads();
+    for (int idx = tid; idx < nt * nc; idx += MT)
+      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc);
     __syncthreads();
     for (int tt = 0; tt < nt; ++tt) {
       double beta = 0.0;
       for (int c = 0; c < nc; ++c) beta = fma(b[c], coef[tt * ncs + c], beta);
       x = fma(an, x, cn * beta);
-      const int64_t k1 = a.k0 + t0 + tt + 1;   // state index after this step
+      X[tid * (TS + 1) + tt] = live ? x : 0.0;
+      const int64_t k1 = t0 + tt + 1;   // state index after this step
       if (live && a.stride > 0 && a.Xsnap && k1 % a.stride == 0)
         a.Xsnap[nmode + (k1 / a.stride - 1) * a.n0] = x;
-      for (int p = 0; p < a.P; ++p) {
-        double v = g[p] * x;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[(w * TSUB + tt) * Ps + p] = v;
+    }
+    __syncthreads();
+    for (int o = tid; o < P * nt; o += MT) {
+      const int p = o / nt, tt = o % nt;
+      const double* gp = Gs + p * MT;
+      double s0 = 0.0, s1 = 0.0;
+      for (int n = 0; n < MT; n += 2) {
+        s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
+        s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
       }
+      a.partial[((int64_t)blockIdx.x * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nt * a.P; idx += MT) {
-      const int tt = idx / a.P, p = idx % a.P;
-      double v = 0.0;
-#pragma unroll
-      for (int ww = 0; ww < MT / 32; ++ww) v += red[(ww * TSUB + tt) * Ps + p];
-      a.partial[((int64_t)blockIdx.x * a.kn + t0 + tt) * a.P + p] = v;
-    }
-    __syncthreads();
   }
-  if (live) a.x[nmode] = x;
+  if (live && g == a.nchunk - 1) a.xout[nmode] = x;
 }
 
 __global__ void probe_reduce_kernel(ScanArgs a, int nblk, const double* CPE, double* probes) {
@@ -287,7 +349,7 @@ ModalState* modal_create() { return new ModalState(); }
 void modal_free(ModalState* ms) {
   if (!ms) return;
   double* ps[] = {ms->U, ms->tau, ms->ac, ms->B, ms->Gt, ms->x, ms->work, ms->Xsnap, ms->partial,
-                  ms->small, ms->DinvR};
+                  ms->small, ms->DinvR, ms->chunkbuf};
   for (double* p : ps)
     if (p) cudaFree(p);
   __nv_bfloat16* bs[] = {ms->Ubf_rm, ms->Ubf_cm, ms->Ubf_rm_lo, ms->Ubf_cm_lo, ms->Ybf};
@@ -427,34 +489,57 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   const int nblk = (int)((n0 + MT - 1) / MT);
   const int64_t nsnap = (sa.snap_stride > 0 && sa.snaps) ? T / sa.snap_stride : 0;
   if (nsnap > 0) MS_TRY(grow_n(&ms->Xsnap, ms->xsnapCap, (size_t)n0 * nsnap));
-  const int64_t kmax = T < TCHUNK ? T : TCHUNK;
-  MS_TRY(grow_n(&ms->partial, ms->partialCap, (size_t)nblk * kmax * (ms->P > 0 ? ms->P : 1)));
+  const int64_t kmax = T < SUPER ? T : SUPER;
+  const int P = ms->P > 0 ? ms->P : 1;
+  MS_TRY(grow_n(&ms->partial, ms->partialCap, (size_t)nblk * kmax * P));
+  // chunks: enough (mode tile, chunk) CTAs for ~4 per SM, never shorter than CH_MIN steps
+  const int64_t gtarget = ((int64_t)4 * num_sms() + nblk - 1) / nblk;
+  const int64_t maxchunks = (kmax + CH_MIN - 1) / CH_MIN;
+  const int64_t gcap = gtarget < maxchunks ? gtarget : maxchunks;
+  MS_TRY(grow_n(&ms->chunkbuf, ms->chunkCap, (size_t)3 * (gcap > 0 ? gcap : 1) * n0));
   ScanArgs a{};
   a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P; a.ncoef = ms->ncoef;
   a.theta = ms->theta; a.dt = ms->dt; a.ac = ms->ac; a.B = ms->B; a.Gt = ms->Gt;
-  a.src = sa.src; a.iD = sa.iD; a.x = ms->x; a.partial = ms->partial;
+  a.src = sa.src; a.iD = sa.iD; a.partial = ms->partial;
   a.Xsnap = nsnap > 0 ? ms->Xsnap : nullptr; a.stride = nsnap > 0 ? sa.snap_stride : 0;
-  const size_t smem = sizeof(double) * (size_t)(TSUB * (ms->ncoef > 0 ? ms->ncoef : 1) +
-                                                (MT / 32) * TSUB * (ms->P > 0 ? ms->P : 1));
+  const int ncs = ms->ncoef > 0 ? ms->ncoef : 1;
+  const size_t smem1 = sizeof(double) * (size_t)(TS * ncs);
+  const size_t smem2 = sizeof(double) * (size_t)(TS * ncs + MT * (TS + 1) + ms->P * MT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  for (int64_t k0 = 0; k0 < T; k0 += TCHUNK) {
+  for (int64_t k0 = 0; k0 < T; k0 += SUPER) {
     a.k0 = k0;
-    a.kn = (T - k0) < TCHUNK ? (T - k0) : TCHUNK;
+    a.kn = (T - k0) < SUPER ? (T - k0) : SUPER;
+    int64_t ch = (a.kn + gcap - 1) / (gcap > 0 ? gcap : 1);
+    if (ch < CH_MIN) ch = CH_MIN;
+    ch = (ch + TS - 1) / TS * TS;
+    a.ch = ch;
+    a.nchunk = (int)((a.kn + ch - 1) / ch);
+    a.x = ms->x;
+    a.xout = ms->work;
+    a.xend = ms->chunkbuf;
+    a.apow = ms->chunkbuf + (size_t)a.nchunk * n0;
+    a.xstart = ms->chunkbuf + (size_t)2 * a.nchunk * n0;
     if (ev) {
       ev->resize(ev->size() + 2);
       cudaEventCreate(&(*ev)[ev->size() - 2]);
       cudaEventCreate(&(*ev)[ev->size() - 1]);
       cudaEventRecord((*ev)[ev->size() - 2], s);
     }
-    modal_scan_kernel<<<nblk, MT, smem, ::ec::counted(s)>>>(a);
+    if (a.nchunk > 1) {
+      modal_chunk_end_kernel<<<dim3(nblk, a.nchunk), MT, smem1, ::ec::counted(s)>>>(a);
+      modal_carry_kernel<<<(unsigned)((n0 + 255) / 256), 256, 0, ::ec::counted(s)>>>(a);
+    }
+    modal_scan_kernel<<<dim3(nblk, a.nchunk), MT, smem2, ::ec::counted(s)>>>(a);
     if (ev) cudaEventRecord(ev->back(), s);
+    copy_matrix(s, n0, 1, ms->work, n0, ms->x, n0);
     if (ms->P > 0 && sa.probes) {
       const int64_t tot = a.kn * ms->P;
-      probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ::ec::counted(s)>>>(a, nblk, sa.CPE, sa.probes);
+      probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ::ec::counted(s)>>>(
+          a, nblk, sa.CPE, sa.probes);
     }
   }
   if (nsnap > 0) {

@@ -147,3 +147,17 @@ def test_config2_electrodes_n8192_first_steps(eddy):
     assert rel(snaps, ref.snaps) < TOL
     t = tm.timings()
     assert t["eig_ms"] > 0 and t["tridiag_ms"] > 0
+
+
+@pytest.mark.parametrize("n,T", [(200, 6000), (1030, 3100)])
+def test_long_run_uses_time_chunks(eddy, n, T):
+    """Runs longer than one time chunk: chunk end states from a zero start, carried
+    start states, chunks replayed in parallel -- same trajectory as the oracle."""
+    p = synth.small(n, T=T, seed=n + 1, electrodes=True, coil=True, snap_stride=500, dt=2e-7)
+    ref = orc.run_problem(p, "plain")
+    tm = make(eddy, p)
+    probes, snaps = run(tm, p)
+    assert rel(probes, ref.probes) < TOL
+    assert rel(snaps, ref.snaps) < TOL
+    if T % p.snap_stride == 0:       # the last snapshot is the final current
+        assert rel(snaps[:, -1], ref.I_final) < TOL
