@@ -82,7 +82,17 @@ typedef struct ec_config {
   int profile;            /* nonzero: ec_run times its dominant kernels with CUDA events (see ec_timing) */
   int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
   int precision;          /* modal form: EC_PREC_FP64 (default) or EC_PREC_BF16, see below */
+  int integrator;         /* modal form: EC_INTEG_THETA (default) or EC_INTEG_EXACT, see below */
 } ec_config;
+
+/* Per-mode time integrator of the modal form.
+ *   EC_INTEG_THETA  the theta-method of Sec. 3.3.2 (same scheme as the plain form).
+ *   EC_INTEG_EXACT  exact integration of each decoupled mode, tau x' + x = e(t), for
+ *                   sources linear between their samples (the analytical route Sec. 3.3
+ *                   points to): x^{k+1} = e^{-h} x^k + (1 - e^{-h}) e0 + (1 - (1 - e^{-h})/h) e1,
+ *                   h = dt / tau, e0 and e1 the forcing at the step start and its change
+ *                   over the step.  theta is ignored. */
+enum { EC_INTEG_THETA = 0, EC_INTEG_EXACT = 1 };
 
 /* Arithmetic of the modal form's dense contractions.  The Cholesky of R_i, the
  * pencil reduction, the eigensolve and the per-mode recurrence are FP64 in every

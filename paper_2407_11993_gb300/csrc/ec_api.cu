@@ -279,6 +279,8 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
   if (cfg->precision != EC_PREC_FP64 && cfg->precision != EC_PREC_BF16 &&
       cfg->precision != EC_PREC_BF16X3)
     return EC_ERR_ARG;
+  if (cfg->integrator != EC_INTEG_THETA && cfg->integrator != EC_INTEG_EXACT) return EC_ERR_ARG;
+  if (cfg->integrator == EC_INTEG_EXACT && cfg->form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
@@ -455,6 +457,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     ma.CK = c->dC + c->m; ma.ldC = n;
     ma.theta = c->cfg.theta; ma.dt = c->cfg.dt;
     ma.precision = c->cfg.precision;
+    ma.integ = c->cfg.integrator;
     ma.st = c->st;
     EC_TRY(modal_setup(c->stream, c->modal, ma, &c->tim));
     EC_TRY(collect(c));

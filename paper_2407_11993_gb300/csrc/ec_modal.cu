@@ -37,7 +37,8 @@ struct ModalState {
   double theta = 0.5, dt = 0.0;
   double* U = nullptr;
   double* tau = nullptr;
-  double* ac = nullptr;       // a_n (n0) then c_n (n0)
+  double* ac = nullptr;       // a_n, q0_n, q1_n (3 x n0)
+  int integ = EC_INTEG_THETA;
   double* B = nullptr;        // n0 x ncoef
   double* Gt = nullptr;       // n0 x P
   double* x = nullptr;        // n0
@@ -130,13 +131,38 @@ __global__ void reverse_kernel(int64_t n, const double* lam, const double* Q, do
   }
 }
 
-__global__ void coef_kernel(int64_t n0, const double* tau, double theta, double dt, double* ac) {
+// Per-mode step coefficients (a, q0, q1) of x^{k+1} = a x^k + q0 (B w0^k) + q1 (B w1^k).
+//   theta-method (Sec. 3.3.2):  a = (tau - (1-theta) dt)/(tau + theta dt), q0 = 1/(tau + theta dt), q1 = 0
+//   exact for piecewise-linear sources (h = dt/tau): a = e^{-h}, q0 = 1 - e^{-h},
+//   q1 = 1 - (1 - e^{-h})/h, summed from its Taylor series for h < 1 (it cancels to h/2).
+__global__ void coef_kernel(int64_t n0, const double* tau, double theta, double dt, int integ,
+                            double* ac) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n0;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double t = tau[i];
-    const double den = t + theta * dt;
-    ac[i] = (t - (1.0 - theta) * dt) / den;
-    ac[n0 + i] = 1.0 / den;
+    if (integ == EC_INTEG_EXACT) {
+      const double h = dt / t;
+      const double c0 = -expm1(-h);
+      double c1;
+      if (h < 1.0) {
+        double term = 0.5 * h, ser = term;
+        for (int j = 2; j <= 20; ++j) {
+          term = -term * h / (double)(j + 1);
+          ser += term;
+        }
+        c1 = ser;
+      } else {
+        c1 = 1.0 - c0 / h;
+      }
+      ac[i] = exp(-h);
+      ac[n0 + i] = c0;
+      ac[2 * n0 + i] = c1;
+    } else {
+      const double den = t + theta * dt;
+      ac[i] = (t - (1.0 - theta) * dt) / den;
+      ac[n0 + i] = 1.0 / den;
+      ac[2 * n0 + i] = 0.0;
+    }
   }
 }
 
@@ -150,8 +176,9 @@ struct ScanArgs {
   int64_t ch;                 // chunk length; chunk g covers [k0 + g ch, k0 + (g+1) ch)
   int nchunk;
   int m, S, P, ncoef;
+  int integ;                  // EC_INTEG_*
   double theta, dt;
-  const double* ac;
+  const double* ac;           // a, q0, q1 (3 x n0)
   const double* B;
   const double* Gt;
   const double* src;
@@ -166,10 +193,24 @@ struct ScanArgs {
   int64_t stride;
 };
 
-// Coefficient of projected source column c in beta^k (Sec. 3.3.2 with the Cholesky-form
-// right-hand side): [-dt i_D^k - theta dt d i_D | -d i_D | -d i_0].
-__device__ __forceinline__ double beta_coef(const ScanArgs& a, int c, int64_t k) {
+// Weights of projected source column c at step k.  which = 0: w0, which = 1: w1.
+//   theta-method, Cholesky-form right-hand side (Sec. 3.3.1 projected, Sec. 3.3.2):
+//     w0 = [-dt i_D^k - theta dt d i_D | -d i_D | -d i_0],  w1 = 0
+//   exact integration of sources linear between samples: the forcing over the step is
+//   e0 + e1 s with e0 = B w0, e1 = B w1,
+//     w0 = [-i_D^k | -d i_D / dt | -d i_0 / dt],  w1 = [-d i_D | 0 | 0]
+__device__ __forceinline__ double beta_coef(const ScanArgs& a, int c, int64_t k, int which) {
   const int m = a.m;
+  if (a.integ == EC_INTEG_EXACT) {
+    if (c < m) {
+      const double d0 = srcv(a.iD, a.T, c, k), d1 = srcv(a.iD, a.T, c, k + 1);
+      return which ? -(d1 - d0) : -d0;
+    }
+    if (which) return 0.0;
+    if (c < 2 * m) return -(srcv(a.iD, a.T, c - m, k + 1) - srcv(a.iD, a.T, c - m, k)) / a.dt;
+    return -(srcv(a.src, a.T, c - 2 * m, k + 1) - srcv(a.src, a.T, c - 2 * m, k)) / a.dt;
+  }
+  if (which) return 0.0;
   if (c < m) {
     const double d0 = srcv(a.iD, a.T, c, k), d1 = srcv(a.iD, a.T, c, k + 1);
     return -a.dt * d0 - a.theta * a.dt * (d1 - d0);
@@ -188,30 +229,36 @@ __device__ __forceinline__ void chunk_range(const ScanArgs& a, int g, int64_t& c
 __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
   extern __shared__ double smem[];
   const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
-  double* coef = smem;   // [TS][ncs]
+  double* coef = smem;   // [2][TS][ncs]
   const int g = blockIdx.y;
   int64_t c0, c1;
   chunk_range(a, g, c0, c1);
   const int64_t nmode = blockIdx.x * (int64_t)MT + threadIdx.x;
   const bool live = nmode < a.n0;
-  double an = 0.0, cn = 0.0, b[2 * MAXM + 64];
+  const bool two = a.integ == EC_INTEG_EXACT;
+  double an = 0.0, q0 = 0.0, q1 = 0.0, b[2 * MAXM + 64];
   if (live) {
     an = a.ac[nmode];
-    cn = a.ac[a.n0 + nmode];
+    q0 = a.ac[a.n0 + nmode];
+    q1 = a.ac[2 * a.n0 + nmode];
     for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
   }
   double x = 0.0, ap = 1.0;
   for (int64_t t0 = c0; t0 < c1; t0 += TS) {
     const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nt * nc; idx += MT)
-      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc);
+    for (int idx = threadIdx.x; idx < nt * nc; idx += MT) {
+      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 0);
+      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 1);
+    }
     __syncthreads();
     if (live)
       for (int tt = 0; tt < nt; ++tt) {
-        double beta = 0.0;
-        for (int c = 0; c < nc; ++c) beta = fma(b[c], coef[tt * ncs + c], beta);
-        x = fma(an, x, cn * beta);
+        double e0 = 0.0, e1 = 0.0;
+        for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
+        if (two)
+          for (int c = 0; c < nc; ++c) e1 = fma(b[c], coef[TS * ncs + tt * ncs + c], e1);
+        x = fma(an, x, fma(q0, e0, q1 * e1));
         ap *= an;
       }
   }
@@ -240,8 +287,8 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   extern __shared__ double smem[];
   const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
   const int P = a.P;
-  double* coef = smem;                  // [TS][ncs]
-  double* X = coef + TS * ncs;          // [MT][TS + 1]
+  double* coef = smem;                  // [2][TS][ncs]
+  double* X = coef + 2 * TS * ncs;      // [MT][TS + 1]
   double* Gs = X + MT * (TS + 1);       // [P][MT]
   const int g = blockIdx.y;
   int64_t c0, c1;
@@ -249,10 +296,12 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   const int tid = threadIdx.x;
   const int64_t nmode = blockIdx.x * (int64_t)MT + tid;
   const bool live = nmode < a.n0;
-  double an = 0.0, cn = 0.0, x = 0.0, b[2 * MAXM + 64];
+  const bool two = a.integ == EC_INTEG_EXACT;
+  double an = 0.0, q0 = 0.0, q1 = 0.0, x = 0.0, b[2 * MAXM + 64];
   if (live) {
     an = a.ac[nmode];
-    cn = a.ac[a.n0 + nmode];
+    q0 = a.ac[a.n0 + nmode];
+    q1 = a.ac[2 * a.n0 + nmode];
     x = (g == 0) ? a.x[nmode] : a.xstart[(int64_t)g * a.n0 + nmode];
     for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
   }
@@ -260,13 +309,17 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   for (int64_t t0 = c0; t0 < c1; t0 += TS) {
     const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
     __syncthreads();
-    for (int idx = tid; idx < nt * nc; idx += MT)
-      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc);
+    for (int idx = tid; idx < nt * nc; idx += MT) {
+      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 0);
+      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 1);
+    }
     __syncthreads();
     for (int tt = 0; tt < nt; ++tt) {
-      double beta = 0.0;
-      for (int c = 0; c < nc; ++c) beta = fma(b[c], coef[tt * ncs + c], beta);
-      x = fma(an, x, cn * beta);
+      double e0 = 0.0, e1 = 0.0;
+      for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
+      if (two)
+        for (int c = 0; c < nc; ++c) e1 = fma(b[c], coef[TS * ncs + tt * ncs + c], e1);
+      x = fma(an, x, fma(q0, e0, q1 * e1));
       X[tid * (TS + 1) + tt] = live ? x : 0.0;
       const int64_t k1 = t0 + tt + 1;   // state index after this step
       if (live && a.stride > 0 && a.Xsnap && k1 % a.stride == 0)
@@ -373,7 +426,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   MS_TRY(alloc_n(&ms->DinvR, (size_t)nblk * NB * NB));
   MS_TRY(alloc_n(&ms->U, nn));
   MS_TRY(alloc_n(&ms->tau, (size_t)n0));
-  MS_TRY(alloc_n(&ms->ac, (size_t)2 * n0));
+  MS_TRY(alloc_n(&ms->ac, (size_t)3 * n0));
   MS_TRY(alloc_n(&ms->B, (size_t)n0 * (ms->ncoef > 0 ? ms->ncoef : 1)));
   MS_TRY(alloc_n(&ms->Gt, (size_t)n0 * (a.P > 0 ? a.P : 1)));
   MS_TRY(alloc_n(&ms->x, (size_t)n0));
@@ -468,8 +521,9 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
     if (rc2 != EC_OK) return rc2;
   }
   if (a.P > 0) MS_TRY(modal_product(s, ms, 1, a.P, a.CK, a.ldC, ms->Gt, n0, a.st));
+  ms->integ = a.integ;
   coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
-      n0, ms->tau, ms->theta, ms->dt, ms->ac);
+      n0, ms->tau, ms->theta, ms->dt, ms->integ, ms->ac);
   tim->project_ms = t.ms();
   return EC_OK;
 }
@@ -479,7 +533,7 @@ ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt
   ms->dt = dt;
   const int64_t n0 = ms->n0;
   coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
-      n0, ms->tau, theta, dt, ms->ac);
+      n0, ms->tau, theta, dt, ms->integ, ms->ac);
   return EC_OK;
 }
 
@@ -500,11 +554,12 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   ScanArgs a{};
   a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P; a.ncoef = ms->ncoef;
   a.theta = ms->theta; a.dt = ms->dt; a.ac = ms->ac; a.B = ms->B; a.Gt = ms->Gt;
+  a.integ = ms->integ;
   a.src = sa.src; a.iD = sa.iD; a.partial = ms->partial;
   a.Xsnap = nsnap > 0 ? ms->Xsnap : nullptr; a.stride = nsnap > 0 ? sa.snap_stride : 0;
   const int ncs = ms->ncoef > 0 ? ms->ncoef : 1;
-  const size_t smem1 = sizeof(double) * (size_t)(TS * ncs);
-  const size_t smem2 = sizeof(double) * (size_t)(TS * ncs + MT * (TS + 1) + ms->P * MT);
+  const size_t smem1 = sizeof(double) * (size_t)(2 * TS * ncs);
+  const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + ms->P * MT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -25,6 +25,7 @@ struct ModalSetupArgs {
   int64_t ldC;
   double theta, dt;
   int precision;       // EC_PREC_*
+  int integ;           // EC_INTEG_*
   DevStatus* st;
 };
 

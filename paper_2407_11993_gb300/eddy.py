@@ -38,7 +38,7 @@ NOALLOC_MAX_N = 8192
 class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
-                ("plain_solver", c_int), ("precision", c_int)]
+                ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -188,16 +188,19 @@ class ThetaMethod:
 
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
-                 profile: bool = False, solver: str = "inverse", precision: str = "fp64"):
+                 profile: bool = False, solver: str = "inverse", precision: str = "fp64",
+                 integrator: str = "theta"):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
             raise ValueError("precision must be 'fp64', 'bf16' or 'bf16x3'")
+        if integrator not in ("theta", "exact"):
+            raise ValueError("integrator must be 'theta' or 'exact'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
-                        _PREC[precision])
+                        _PREC[precision], 1 if integrator == "exact" else 0)
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h
