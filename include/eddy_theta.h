@@ -242,6 +242,23 @@ EC_API ec_status ec_grad(ec_ctx* ctx, int64_t T, const double* src, const double
 EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, const double* B,
                               double* C, void* stream);
 
+/* Modal form only: selective integration (the decoupled modes can be advanced "in a
+ * selective manner", Sec. 2.3).  From now on only the n_keep modes of largest tau are
+ * integrated and reconstructed; the others are set to zero and stay there.  For a
+ * source-free run the result is the R_i-orthogonal projection of the full trajectory
+ * on the kept modes.  1 <= n_keep <= ec_state_size(); n_keep = ec_state_size()
+ * restores the full modal form. */
+EC_API ec_status ec_set_mode_count(ec_ctx* ctx, int64_t n_keep);
+
+/* Phasors of sampled signals at given frequencies (the Fourier post-processing of the
+ * time-domain responses, Sec. 4.6):  X_{j,p} = (2/T) sum_{k<T} y[k][p] exp(-i 2 pi f_j (t0 + k dt)).
+ *   y      T x p samples (row-major: row k = all p signals at t0 + k dt, as ec_run writes probes)
+ *   freqs  nf frequencies [Hz];  out  nf x p x 2 (real, imaginary), row-major.
+ * For a record spanning an integer number of periods of tone f, a signal
+ * Im(W exp(i 2 pi f t)) gives X = -i W.  Synchronous; uses the current device. */
+EC_API ec_status ec_phasors(int64_t T, int64_t p, const double* y, double t0, double dt,
+                            int64_t nf, const double* freqs, double* out, int mem);
+
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */
 EC_API ec_status ec_sync(ec_ctx* ctx);

@@ -750,6 +750,13 @@ ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int6
   return rc;
 }
 
+ec_status ec_set_mode_count(ec_ctx* c, int64_t n_keep) {
+  if (!c) return EC_ERR_ARG;
+  if (!c->ready || c->cfg.form != EC_FORM_MODAL) return EC_ERR_STATE;
+  EC_TRY(modal_set_mode_count(c->stream, c->modal, n_keep));
+  return collect(c);
+}
+
 int64_t ec_launch_count(void) { return ec::g_launches.load(std::memory_order_relaxed); }
 
 ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {

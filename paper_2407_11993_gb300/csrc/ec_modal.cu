@@ -39,6 +39,7 @@ struct ModalState {
   double* tau = nullptr;
   double* ac = nullptr;       // a_n, q0_n, q1_n (3 x n0)
   int integ = EC_INTEG_THETA;
+  int64_t nkeep = 0;          // modes integrated (the nkeep largest tau); the rest stay zero
   double* B = nullptr;        // n0 x ncoef
   double* Gt = nullptr;       // n0 x P
   double* x = nullptr;        // n0
@@ -172,6 +173,7 @@ __device__ __forceinline__ double srcv(const double* a, int64_t T, int row, int6
 
 struct ScanArgs {
   int64_t n0, T;              // T: steps of the whole run (source arrays hold T+1 samples)
+  int64_t nkeep;              // modes integrated: 0 .. nkeep-1
   int64_t k0, kn;             // this launch group: steps k0 .. k0+kn-1
   int64_t ch;                 // chunk length; chunk g covers [k0 + g ch, k0 + (g+1) ch)
   int nchunk;
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
   int64_t c0, c1;
   chunk_range(a, g, c0, c1);
   const int64_t nmode = blockIdx.x * (int64_t)MT + threadIdx.x;
-  const bool live = nmode < a.n0;
+  const bool live = nmode < a.nkeep;
   const bool two = a.integ == EC_INTEG_EXACT;
   double an = 0.0, q0 = 0.0, q1 = 0.0, b[2 * MAXM + 64];
   if (live) {
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
 
 // Carry: true start state of every chunk (chunk 0 starts from the state itself).
 __global__ void modal_carry_kernel(ScanArgs a) {
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < a.n0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < a.nkeep;
        n += (int64_t)gridDim.x * blockDim.x) {
     double xs = a.x[n];
     for (int g = 0; g < a.nchunk; ++g) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   chunk_range(a, g, c0, c1);
   const int tid = threadIdx.x;
   const int64_t nmode = blockIdx.x * (int64_t)MT + tid;
-  const bool live = nmode < a.n0;
+  const bool live = nmode < a.nkeep;
   const bool two = a.integ == EC_INTEG_EXACT;
   double an = 0.0, q0 = 0.0, q1 = 0.0, x = 0.0, b[2 * MAXM + 64];
   if (live) {
@@ -378,11 +380,12 @@ __global__ void snap_particular_kernel(int64_t n, int m, int64_t nsnap, int64_t 
 // C (n0 x N, column-major, ldc) = op(U) Y with Y n0 x N column-major (lds); op(U) = U^T
 // (trans_u = 1) or U (trans_u = 0); arithmetic per ms->precision.
 ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, const double* Y,
-                        int64_t lds, double* C, int64_t ldc, DevStatus* st) {
+                        int64_t lds, double* C, int64_t ldc, DevStatus* st, int64_t K = -1) {
   const int64_t n0 = ms->n0;
   if (N <= 0) return EC_OK;
+  if (K < 0) K = n0;
   if (ms->precision == EC_PREC_FP64) {
-    dgemm(s, trans_u ? T_ : N_, N_, n0, N, n0, 1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
+    dgemm(s, trans_u ? T_ : N_, N_, n0, N, K, 1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
     return EC_OK;
   }
   const int64_t ld = bf16_ld(n0);
@@ -390,11 +393,11 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
   MS_TRY(grow_n(&ms->Ybf, ms->ybfCap, (size_t)(x3 ? 2 : 1) * N * ld));
   __nv_bfloat16* yh = ms->Ybf;
   __nv_bfloat16* yl = x3 ? ms->Ybf + (size_t)N * ld : nullptr;
-  to_bf16(s, N, n0, Y, lds, 1, yh, ld, yl);
+  to_bf16(s, N, K, Y, lds, 1, yh, ld, yl);
   const __nv_bfloat16* ah = trans_u ? ms->Ubf_cm : ms->Ubf_rm;
   const __nv_bfloat16* al = trans_u ? ms->Ubf_cm_lo : ms->Ubf_rm_lo;
-  if (x3) return tc_gemm_bf16x3(s, n0, N, n0, 1.0, ah, al, ld, yh, yl, ld, C, ldc, st);
-  return tc_gemm_bf16(s, n0, N, n0, 1.0, ah, ld, yh, ld, 0.0, C, ldc, st);
+  if (x3) return tc_gemm_bf16x3(s, n0, N, K, 1.0, ah, al, ld, yh, yl, ld, C, ldc, st);
+  return tc_gemm_bf16(s, n0, N, K, 1.0, ah, ld, yh, ld, 0.0, C, ldc, st);
 }
 
 ModalState* modal_create() { return new ModalState(); }
@@ -412,6 +415,13 @@ void modal_free(ModalState* ms) {
 }
 
 double* modal_state(ModalState* ms) { return ms->x; }
+
+ec_status modal_set_mode_count(cudaStream_t s, ModalState* ms, int64_t nkeep) {
+  if (nkeep < 1 || nkeep > ms->n0) return EC_ERR_ARG;
+  ms->nkeep = nkeep;
+  if (nkeep < ms->n0) cudaMemsetAsync(ms->x + nkeep, 0, sizeof(double) * (ms->n0 - nkeep), s);
+  return EC_OK;
+}
 const double* modal_tau(ModalState* ms) { return ms->tau; }
 const double* modal_U(ModalState* ms) { return ms->U; }
 
@@ -522,6 +532,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   }
   if (a.P > 0) MS_TRY(modal_product(s, ms, 1, a.P, a.CK, a.ldC, ms->Gt, n0, a.st));
   ms->integ = a.integ;
+  ms->nkeep = n0;
   coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n0, ms->tau, ms->theta, ms->dt, ms->integ, ms->ac);
   tim->project_ms = t.ms();
@@ -540,7 +551,8 @@ ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt
 ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
                     std::vector<cudaEvent_t>* ev) {
   const int64_t n0 = ms->n0, T = sa.T;
-  const int nblk = (int)((n0 + MT - 1) / MT);
+  const int64_t nkeep = ms->nkeep;
+  const int nblk = (int)((nkeep + MT - 1) / MT);
   const int64_t nsnap = (sa.snap_stride > 0 && sa.snaps) ? T / sa.snap_stride : 0;
   if (nsnap > 0) MS_TRY(grow_n(&ms->Xsnap, ms->xsnapCap, (size_t)n0 * nsnap));
   const int64_t kmax = T < SUPER ? T : SUPER;
@@ -553,6 +565,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   MS_TRY(grow_n(&ms->chunkbuf, ms->chunkCap, (size_t)3 * (gcap > 0 ? gcap : 1) * n0));
   ScanArgs a{};
   a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P; a.ncoef = ms->ncoef;
+  a.nkeep = nkeep;
   a.theta = ms->theta; a.dt = ms->dt; a.ac = ms->ac; a.B = ms->B; a.Gt = ms->Gt;
   a.integ = ms->integ;
   a.src = sa.src; a.iD = sa.iD; a.partial = ms->partial;
@@ -590,7 +603,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
     }
     modal_scan_kernel<<<dim3(nblk, a.nchunk), MT, smem2, ::ec::counted(s)>>>(a);
     if (ev) cudaEventRecord(ev->back(), s);
-    copy_matrix(s, n0, 1, ms->work, n0, ms->x, n0);
+    copy_matrix(s, nkeep, 1, ms->work, n0, ms->x, n0);
     if (ms->P > 0 && sa.probes) {
       const int64_t tot = a.kn * ms->P;
       probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ::ec::counted(s)>>>(
@@ -602,7 +615,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
     const int m = ms->m;
     // rows m.. of each snapshot: U x; rows 0..m-1: 0; then apply Q and add the particular field
     if (m > 0) cudaMemsetAsync(sa.snaps, 0, sizeof(double) * (size_t)n * nsnap, s);
-    MS_TRY(modal_product(s, ms, 0, nsnap, ms->Xsnap, n0, sa.snaps + m, n, sa.st));
+    MS_TRY(modal_product(s, ms, 0, nsnap, ms->Xsnap, n0, sa.snaps + m, n, sa.st, nkeep));
     if (m > 0) {
       MS_TRY(grow_n(&ms->small, ms->smallCap, (size_t)2 * m * nsnap));
       one_sided_q(s, n, m, sa.snaps, nsnap, sa.V, sa.Tm, ms->small, ms->small + m * nsnap, sa.st);

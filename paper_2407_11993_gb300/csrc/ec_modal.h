@@ -37,6 +37,8 @@ ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt
 ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& a,
                     std::vector<cudaEvent_t>* ev = nullptr);
 double* modal_state(ModalState* ms);
+// Integrate only the nkeep modes of largest tau; the others are held at zero.
+ec_status modal_set_mode_count(cudaStream_t s, ModalState* ms, int64_t nkeep);
 const double* modal_tau(ModalState* ms);
 const double* modal_U(ModalState* ms);
 // x = U^T R_i I_i for an internal current I_i (device, length n0)

@@ -31,7 +31,7 @@ EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
            "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
-           "ec_grad", "ec_gemm_bf16")
+           "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors")
 NOALLOC_MAX_N = 8192
 
 
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
             "ec_solve_inverse_noalloc": (c_int, [c_int64, P, c_int64, P, P, P]),
             "ec_grad": (c_int, [P, c_int64, P, P, c_int64, P, P, P, c_int]),
             "ec_gemm_bf16": (c_int, [c_int64, c_int64, c_int64, P, P, P, P]),
+            "ec_set_mode_count": (c_int, [P, c_int64]),
+            "ec_phasors": (c_int, [c_int64, c_int64, P, c_double, c_double, c_int64, P, P, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -149,6 +151,17 @@ def gemm_bf16(A, B, C=None, stream=None):
     check(lib().ec_gemm_bf16(M, N, K, c_void_p(At.data_ptr()), c_void_p(Bt.data_ptr()),
                              c_void_p(Ct.data_ptr()), c_void_p(stream or 0)), "ec_gemm_bf16")
     return Ct.t()
+
+
+def phasors(probes, t0: float, dt: float, freqs):
+    """probes (P, T) host array -> (F, P) complex phasors computed on the GPU."""
+    y = np.ascontiguousarray(np.asarray(probes, np.float64).T)       # T x P
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    out = np.empty((f.size, y.shape[1], 2))
+    check(lib().ec_phasors(y.shape[0], y.shape[1], c_void_p(y.ctypes.data), float(t0), float(dt),
+                           f.size, c_void_p(f.ctypes.data), c_void_p(out.ctypes.data),
+                           EC_MEM_HOST), "ec_phasors")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def launch_count() -> int:
@@ -269,6 +282,10 @@ class ThetaMethod:
     def set_current(self, I) -> None:
         p, k = _ptr(I, EC_MEM_HOST)
         check(lib().ec_set_current(self._h, p, EC_MEM_HOST), "ec_set_current", self._h)
+
+    def set_mode_count(self, n_keep: int) -> None:
+        """Integrate only the n_keep slowest modes (modal form)."""
+        check(lib().ec_set_mode_count(self._h, int(n_keep)), "ec_set_mode_count", self._h)
 
     def modes(self):
         n0 = self.state_size()

@@ -256,3 +256,25 @@ def test_workload_matrices_are_spd():
     lap = p.R - np.diag(np.diag(p.R))
     assert np.allclose(lap.sum(axis=1) + (np.diag(p.R) - p.geom.rho * synth.G_FACTOR), 0.0,
                        atol=1e-18)
+
+
+def test_truncated_modes_error_is_the_dropped_modes_energy():
+    """Selective integration (Sec. 2.3: modes can be advanced 'in a selective manner'):
+    keeping the k slowest modes of a zero-source run gives the R_i-orthogonal projection
+    of the full trajectory, so ||I_full - I_k||_R^2 = sum over dropped modes of
+    (a_n^s x_n^0)^2 exactly (modes are R-orthonormal, Sec. 3.2)."""
+    p = synth.small(45, T=12, seed=31, electrodes=False, coil=False, snap_stride=1, dt=2e-4)
+    red = orc.eliminate(p.L, p.R, p.E, p.M, p.MD, p.C)
+    md = orc.modal_setup(red.Li, red.Ri)
+    I0 = np.random.default_rng(4).standard_normal(45)
+    full = orc.theta_modal(red, md, p.theta, p.dt, p.src, p.iD, 12, I0, 1)
+    k = 20
+    trunc = orc.theta_modal(red, orc.Modes(md.tau[:k], md.U[:, :k]), p.theta, p.dt, p.src, p.iD,
+                            12, I0, 1)
+    a, _ = orc.modal_coefficients(md.tau, p.theta, p.dt)
+    x0 = md.U.T @ (p.R @ I0)
+    for s in (1, 5, 12):
+        d = full.snaps[:, s - 1] - trunc.snaps[:, s - 1]
+        e2 = float(d @ p.R @ d)
+        expect = float(np.sum((a[k:] ** s * x0[k:]) ** 2))
+        assert abs(e2 - expect) <= 1e-10 * expect

@@ -170,6 +170,26 @@ def electrode_rows(g: Geometry) -> np.ndarray:
     return e
 
 
+# Tone frequencies [Hz] of the multi-sine excitation of the paper's NdT experiment
+# (Sec. 4.3): 30 tones from 1 Hz to 10 kHz, amplitude 4 A each.
+MULTISINE_HZ = (1.0, 50.0, 100.0, 150.0, 250.0, 300.0, 400.0, 600.0, 700.0, 800.0, 900.0,
+                1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 3500.0, 4000.0, 4500.0, 5000.0, 5500.0,
+                6000.0, 6500.0, 7000.0, 7500.0, 8000.0, 8500.0, 9000.0, 9500.0, 10000.0)
+MULTISINE_AMP = 4.0
+
+
+def multisine(T: int, dt: float, t0: float = 0.0, freqs=MULTISINE_HZ,
+              amp: float = MULTISINE_AMP) -> np.ndarray:
+    """i(t) = sum_k amp sin(2 pi f_k t + phi_k), phi_k = -pi k (k-1) / N_s (k = 1..N_s),
+    sampled at t_j = t0 + j dt, j = 0..T."""
+    t = t0 + np.arange(T + 1, dtype=np.float64) * dt
+    ns = len(freqs)
+    out = np.zeros(T + 1)
+    for k, f in enumerate(freqs, start=1):
+        out += amp * np.sin(2.0 * np.pi * f * t - np.pi * k * (k - 1) / ns)
+    return out
+
+
 def sine(T: int, dt: float, f_hz: float, amp: float = 1.0, phase: float = 0.0) -> np.ndarray:
     t = np.arange(T + 1, dtype=np.float64) * dt
     return amp * np.sin(2.0 * np.pi * f_hz * t + phase)
