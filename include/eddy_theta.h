@@ -83,7 +83,21 @@ typedef struct ec_config {
   int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
   int precision;          /* modal form: EC_PREC_FP64 (default) or EC_PREC_BF16, see below */
   int integrator;         /* modal form: EC_INTEG_THETA (default) or EC_INTEG_EXACT, see below */
+  int rhs_mode;           /* EC_RHS_SUM (default), EC_RHS_INDEPENDENT or EC_RHS_PAIRED, see below */
 } ec_config;
+
+/* How the s coil columns of M drive the system (batched right-hand sides).
+ *   EC_RHS_SUM          all coils act on one trajectory (their voltages add).
+ *   EC_RHS_INDEPENDENT  coil k drives its own trajectory k (s trajectories in one run;
+ *                       the plain form solves with s right-hand sides per step, the modal
+ *                       form runs s sets of mode recurrences).  ec_run writes probes as
+ *                       T x s x p (row (k-1) s + j = the p probes of trajectory j) and
+ *                       snapshots as nsnap x s x n.  Requires m = 0.
+ *   EC_RHS_PAIRED       as INDEPENDENT, but trajectory j is read by probe row j only
+ *                       (p = s, e.g. C = M^T: each coil's own pickup); probes are T x s.
+ * For the independent modes the state holds s trajectories (ec_state_size = s N_0) and
+ * ec_set_current starts every trajectory from the same current. */
+enum { EC_RHS_SUM = 0, EC_RHS_INDEPENDENT = 1, EC_RHS_PAIRED = 2 };
 
 /* Per-mode time integrator of the modal form.
  *   EC_INTEG_THETA  the theta-method of Sec. 3.3.2 (same scheme as the plain form).

@@ -35,6 +35,10 @@ struct ec_ctx {
   double* dPart1 = nullptr;  // chunk partials of C^{-1} b
   double* dPart2 = nullptr;  // chunk partials of C^{-T} y
   double* dYsol = nullptr;   // C^{-1} b
+  int ntraj = 1;             // trajectories (independent right-hand sides)
+  double* dRhsM = nullptr;   // n0 x ntraj work (independent right-hand sides)
+  double* dYM = nullptr;
+  double* dXM = nullptr;
   // elimination
   double* dE = nullptr;
   double* dV = nullptr;
@@ -118,6 +122,7 @@ ec_status grow(T** p, size_t& cap, size_t count) {
 void free_setup(ec_ctx* c) {
   dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
   dfree(c->dW); dfree(c->dPart1); dfree(c->dPart2); dfree(c->dYsol);
+  dfree(c->dRhsM); dfree(c->dYM); dfree(c->dXM);
   dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
   dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
   dfree(c->dY); dfree(c->dX); dfree(c->dSm); dfree(c->dZm); dfree(c->dGsrc); dfree(c->dDmat);
@@ -280,6 +285,12 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
       cfg->precision != EC_PREC_BF16X3)
     return EC_ERR_ARG;
   if (cfg->integrator != EC_INTEG_THETA && cfg->integrator != EC_INTEG_EXACT) return EC_ERR_ARG;
+  if (cfg->rhs_mode != EC_RHS_SUM && cfg->rhs_mode != EC_RHS_INDEPENDENT &&
+      cfg->rhs_mode != EC_RHS_PAIRED)
+    return EC_ERR_ARG;
+  if (cfg->rhs_mode != EC_RHS_SUM && cfg->form == EC_FORM_PLAIN &&
+      cfg->plain_solver != EC_SOLVE_INVERSE)
+    return EC_ERR_UNSUPPORTED;
   if (cfg->integrator == EC_INTEG_EXACT && cfg->form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
@@ -312,7 +323,10 @@ void ec_destroy(ec_ctx* c) {
 
 int64_t ec_last_info(const ec_ctx* c) { return c ? c->last_info : -1; }
 
-int64_t ec_state_size(const ec_ctx* c) { return (c && c->ready) ? c->n0 : 0; }
+int64_t ec_state_size(const ec_ctx* c) {
+  if (!c || !c->ready) return 0;
+  return c->cfg.form == EC_FORM_MODAL ? modal_state_size(c->modal) : c->n0 * c->ntraj;
+}
 
 ec_status ec_sync(ec_ctx* c) {
   if (!c) return EC_ERR_ARG;
@@ -332,7 +346,10 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   if ((m > 0 && !E) || (s > 0 && !M) || (p > 0 && !C)) return EC_ERR_ARG;
   if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
   if (m >= n) return EC_ERR_SHAPE;
-  if (m > MAXM || s > 64 || p + 2 * m > MAXD) return EC_ERR_UNSUPPORTED;
+  const bool indep = c->cfg.rhs_mode != EC_RHS_SUM;
+  if (m > MAXM || (!indep && s > 64) || p + 2 * m > MAXD) return EC_ERR_UNSUPPORTED;
+  if (indep && (m != 0 || s < 1 || s > 65535)) return EC_ERR_UNSUPPORTED;
+  if (c->cfg.rhs_mode == EC_RHS_PAIRED && p != s) return EC_ERR_SHAPE;
   cudaSetDevice(c->cfg.device);
   free_setup(c);
   cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
@@ -425,7 +442,13 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   if (c->update_grid > num_sms() * 2) c->update_grid = num_sms() * 2;
   if (c->update_grid < 1) c->update_grid = 1;
   c->trsv_grid = num_sms() * 2;
-  EC_TRY(alloc(&c->dIi, (size_t)n0));
+  c->ntraj = indep ? c->S : 1;
+  EC_TRY(alloc(&c->dIi, (size_t)n0 * c->ntraj));
+  if (indep && c->cfg.form == EC_FORM_PLAIN) {
+    EC_TRY(alloc(&c->dRhsM, (size_t)n0 * c->ntraj));
+    EC_TRY(alloc(&c->dYM, (size_t)n0 * c->ntraj));
+    EC_TRY(alloc(&c->dXM, (size_t)n0 * c->ntraj));
+  }
   EC_TRY(alloc(&c->dWork, (size_t)n0));
   EC_TRY(alloc(&c->dTmpN, (size_t)n));
   EC_TRY(alloc(&c->dDots, (size_t)MAXD));
@@ -436,7 +459,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   EC_TRY(alloc(&c->dFlags, (size_t)2 * nblk));
   EC_TRY(alloc(&c->dTickets, 2));
   EC_TRY(alloc(&c->dEpoch, 1));
-  cudaMemsetAsync(c->dIi, 0, sizeof(double) * n0, c->stream);
+  cudaMemsetAsync(c->dIi, 0, sizeof(double) * n0 * c->ntraj, c->stream);
   cudaMemsetAsync(c->dDots, 0, sizeof(double) * MAXD, c->stream);
   cudaMemsetAsync(c->dCounter, 0, sizeof(unsigned), c->stream);
   cudaMemsetAsync(c->dK, 0, sizeof(int64_t), c->stream);
@@ -458,6 +481,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     ma.theta = c->cfg.theta; ma.dt = c->cfg.dt;
     ma.precision = c->cfg.precision;
     ma.integ = c->cfg.integrator;
+    ma.rhs_mode = c->cfg.rhs_mode;
     ma.st = c->st;
     EC_TRY(modal_setup(c->stream, c->modal, ma, &c->tim));
     EC_TRY(collect(c));
@@ -490,6 +514,8 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
   if (T == 0) return EC_OK;
   const int64_t n = c->n;
   const int64_t nsnap = (stride > 0 && snaps) ? T / stride : 0;
+  const int64_t nt = c->ntraj;
+  const int64_t pout = (c->cfg.rhs_mode == EC_RHS_PAIRED) ? 1 : c->P;
   EC_TRY(grow(&c->dSrc, c->srcCap, (size_t)(c->S > 0 ? c->S : 1) * (T + 1)));
   EC_TRY(grow(&c->dIDs, c->idsCap, (size_t)(c->m > 0 ? c->m : 1) * (T + 1)));
   EC_TRY(copy_in(c, c->dSrc, src, (size_t)c->S * (T + 1), mem));
@@ -499,14 +525,14 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
   if (probes && c->P > 0) {
     if (mem == EC_MEM_DEVICE) outP = probes;
     else {
-      EC_TRY(grow(&c->dProbes, c->probesCap, (size_t)T * c->P));
+      EC_TRY(grow(&c->dProbes, c->probesCap, (size_t)T * nt * pout));
       outP = c->dProbes;
     }
   }
   if (nsnap > 0) {
     if (mem == EC_MEM_DEVICE) outS = snaps;
     else {
-      EC_TRY(grow(&c->dSnaps, c->snapsCap, (size_t)nsnap * n));
+      EC_TRY(grow(&c->dSnaps, c->snapsCap, (size_t)nsnap * nt * n));
       outS = c->dSnaps;
     }
   }
@@ -517,7 +543,36 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
   std::vector<cudaEvent_t> ev;
   const bool prof = c->cfg.profile != 0;
   EventTimer t(c->stream);
-  if (c->cfg.form == EC_FORM_PLAIN) {
+  if (c->cfg.form == EC_FORM_PLAIN && nt > 1 || (c->cfg.form == EC_FORM_PLAIN && c->cfg.rhs_mode != EC_RHS_SUM)) {
+    // independent right-hand sides: two GEMMs with the inverse factor per step
+    const int64_t n0 = c->n0;
+    const int S = (int)nt;
+    for (int64_t k = 0; k < T; ++k) {
+      plain_rhs_multi(c->stream, a, k, c->dIi, c->dRhsM);
+      cudaEvent_t* e3 = nullptr;
+      const int64_t every = T > 512 ? (T + 511) / 512 : 1;
+      if (prof && k % every == 0) {
+        ev.resize(ev.size() + 3);
+        e3 = &ev[ev.size() - 3];
+        for (int q = 0; q < 3; ++q) cudaEventCreate(&e3[q]);
+      }
+      if (e3) cudaEventRecord(e3[0], c->stream);
+      dgemm(c->stream, N_, N_, n0, S, n0, 1.0, c->dW, n0, c->dRhsM, n0, 0.0, c->dYM, n0, 0, c->st);
+      if (e3) cudaEventRecord(e3[1], c->stream);
+      dgemm(c->stream, T_, N_, n0, S, n0, 1.0, c->dW, n0, c->dYM, n0, 0.0, c->dXM, n0, 0, c->st);
+      if (e3) cudaEventRecord(e3[2], c->stream);
+      axpy_matrix(c->stream, n0, S, 1.0, c->dXM, n0, c->dIi, n0);
+      if (outP) {
+        if (c->cfg.rhs_mode == EC_RHS_PAIRED)
+          paired_probes(c->stream, n0, S, c->dC, n, c->dIi, outP + k * S);
+        else
+          dgemm(c->stream, T_, N_, c->P, S, n0, 1.0, c->dC, n, c->dIi, n0, 0.0,
+                outP + k * S * c->P, c->P, 0, c->st);
+      }
+      if (outS && (k + 1) % stride == 0)
+        copy_matrix(c->stream, n0, S, c->dIi, n0, outS + ((k + 1) / stride - 1) * S * n, n);
+    }
+  } else if (c->cfg.form == EC_FORM_PLAIN) {
     TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
     const int64_t every = T > 512 ? (T + 511) / 512 : 1;
     for (int64_t k = 0; k < T; ++k) {
@@ -566,8 +621,8 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
   EC_TRY(collect(c));
-  if (outP && outP != probes) EC_TRY(copy_out(c, probes, outP, (size_t)T * c->P, mem));
-  if (outS && outS != snaps) EC_TRY(copy_out(c, snaps, outS, (size_t)nsnap * n, mem));
+  if (outP && outP != probes) EC_TRY(copy_out(c, probes, outP, (size_t)T * nt * pout, mem));
+  if (outS && outS != snaps) EC_TRY(copy_out(c, snaps, outS, (size_t)nsnap * nt * n, mem));
   return collect(c);
 }
 
@@ -575,7 +630,7 @@ ec_status ec_get_state(ec_ctx* c, double* state, int mem) {
   if (!c || !state) return EC_ERR_ARG;
   if (!c->ready) return EC_ERR_STATE;
   const double* src = c->cfg.form == EC_FORM_PLAIN ? c->dIi : modal_state(c->modal);
-  EC_TRY(copy_out(c, state, src, (size_t)c->n0, mem));
+  EC_TRY(copy_out(c, state, src, (size_t)ec_state_size(c), mem));
   return collect(c);
 }
 
@@ -583,11 +638,13 @@ ec_status ec_set_state(ec_ctx* c, const double* state, int mem) {
   if (!c || !state) return EC_ERR_ARG;
   if (!c->ready) return EC_ERR_STATE;
   if (c->cfg.form == EC_FORM_PLAIN) {
-    EC_TRY(copy_in(c, c->dIi, state, (size_t)c->n0, mem));
-    StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
-    plain_update(c->stream, a, c->update_grid, 1);
+    EC_TRY(copy_in(c, c->dIi, state, (size_t)ec_state_size(c), mem));
+    if (c->ntraj == 1) {
+      StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
+      plain_update(c->stream, a, c->update_grid, 1);
+    }
   } else {
-    EC_TRY(copy_in(c, modal_state(c->modal), state, (size_t)c->n0, mem));
+    EC_TRY(copy_in(c, modal_state(c->modal), state, (size_t)ec_state_size(c), mem));
   }
   return collect(c);
 }
@@ -599,9 +656,10 @@ ec_status ec_set_current(ec_ctx* c, const double* I, int mem) {
   if (c->m > 0)
     one_sided_qt(c->stream, c->n, c->m, c->dTmpN, 1, c->dV, c->dT, c->dSm, c->dZm, c->st);
   if (c->cfg.form == EC_FORM_PLAIN) {
-    copy_matrix(c->stream, c->n0, 1, c->dTmpN + c->m, c->n, c->dIi, c->n0);
+    for (int64_t r = 0; r < c->ntraj; ++r)
+      copy_matrix(c->stream, c->n0, 1, c->dTmpN + c->m, c->n, c->dIi + r * c->n0, c->n0);
     StepArgs a = step_args(c, 0, nullptr, nullptr, 0);
-    plain_update(c->stream, a, c->update_grid, 1);
+    if (c->ntraj == 1) plain_update(c->stream, a, c->update_grid, 1);
   } else {
     copy_matrix(c->stream, c->n0, 1, c->dTmpN + c->m, c->n, c->dIi, c->n0);
     StepArgs a = step_args(c, 0, nullptr, nullptr, 0);

@@ -69,6 +69,11 @@ struct StepArgs {
 void plain_rhs(cudaStream_t s, const StepArgs& a);
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode);  // mode 0: += work; 1: dots only
 void plain_snapshot(cudaStream_t s, const StepArgs& a);
+// Independent right-hand sides (no electrodes): out (n0 x S) = -dt R I - M_0 diag(ds^k).
+void plain_rhs_multi(cudaStream_t s, const StepArgs& a, int64_t k, const double* I, double* out);
+// out[r] = C[:, r] . I[:, r]
+void paired_probes(cudaStream_t s, int64_t n0, int S, const double* C, int64_t ldc,
+                   const double* I, double* out);
 // out = R_i I_i for the state in a.Ii (needs a.dots current for that state).
 void ri_apply(cudaStream_t s, const StepArgs& a, double* out);
 

@@ -40,6 +40,8 @@ struct ModalState {
   double* ac = nullptr;       // a_n, q0_n, q1_n (3 x n0)
   int integ = EC_INTEG_THETA;
   int64_t nkeep = 0;          // modes integrated (the nkeep largest tau); the rest stay zero
+  int rhs_mode = EC_RHS_SUM;  // EC_RHS_*: independent trajectories for INDEPENDENT / PAIRED
+  int ntraj = 1;
   double* B = nullptr;        // n0 x ncoef
   double* Gt = nullptr;       // n0 x P
   double* x = nullptr;        // n0
@@ -190,9 +192,14 @@ struct ScanArgs {
   double* xend;               // nchunk x n0: chunk end state from a zero start (pass 1)
   double* apow;               // nchunk x n0: a_n^(chunk length)
   double* xstart;             // nchunk x n0: true chunk start states (carry pass)
-  double* partial;            // nblk x kn x P
-  double* Xsnap;              // n0 x nsnap
+  double* partial;            // ntraj x nblk x kn x Pout
+  double* Xsnap;              // n0 x (nsnap * ntraj), column j * ntraj + r
   int64_t stride;
+  // independent trajectories (blockIdx.z = trajectory r): coil r drives trajectory r
+  int ntraj;                  // 1 unless indep
+  int indep;                  // trajectory r uses projected column r and source row r only
+  int paired;                 // trajectory r is read by probe row r only
+  int Pout;                   // probes per trajectory (paired: 1)
 };
 
 // Weights of projected source column c at step k.  which = 0: w0, which = 1: w1.
@@ -221,6 +228,12 @@ __device__ __forceinline__ double beta_coef(const ScanArgs& a, int c, int64_t k,
   return -(srcv(a.src, a.T, c - 2 * m, k + 1) - srcv(a.src, a.T, c - 2 * m, k));
 }
 
+// Column c of trajectory r: the source weights of the column of B it uses.
+__device__ __forceinline__ int bcol(const ScanArgs& a, int c, int r) { return a.indep ? r : c; }
+__device__ __forceinline__ double coef_for(const ScanArgs& a, int c, int r, int64_t k, int which) {
+  return beta_coef(a, a.indep ? 2 * a.m + r : c, k, which);
+}
+
 __device__ __forceinline__ void chunk_range(const ScanArgs& a, int g, int64_t& c0, int64_t& c1) {
   c0 = a.k0 + (int64_t)g * a.ch;
   c1 = c0 + a.ch;
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
   extern __shared__ double smem[];
   const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
   double* coef = smem;   // [2][TS][ncs]
-  const int g = blockIdx.y;
+  const int g = blockIdx.y, r = blockIdx.z;
   int64_t c0, c1;
   chunk_range(a, g, c0, c1);
   const int64_t nmode = blockIdx.x * (int64_t)MT + threadIdx.x;
@@ -243,15 +256,15 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
     an = a.ac[nmode];
     q0 = a.ac[a.n0 + nmode];
     q1 = a.ac[2 * a.n0 + nmode];
-    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
+    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)bcol(a, c, r) * a.n0];
   }
   double x = 0.0, ap = 1.0;
   for (int64_t t0 = c0; t0 < c1; t0 += TS) {
     const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nt * nc; idx += MT) {
-      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 0);
-      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 1);
+      coef[(idx / nc) * ncs + idx % nc] = coef_for(a, idx % nc, r, t0 + idx / nc, 0);
+      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = coef_for(a, idx % nc, r, t0 + idx / nc, 1);
     }
     __syncthreads();
     if (live)
@@ -265,19 +278,21 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
       }
   }
   if (live) {
-    a.xend[(int64_t)g * a.n0 + nmode] = x;
-    a.apow[(int64_t)g * a.n0 + nmode] = ap;
+    a.xend[((int64_t)g * a.ntraj + r) * a.n0 + nmode] = x;
+    a.apow[((int64_t)g * a.ntraj + r) * a.n0 + nmode] = ap;
   }
 }
 
 // Carry: true start state of every chunk (chunk 0 starts from the state itself).
 __global__ void modal_carry_kernel(ScanArgs a) {
+  const int r = blockIdx.y;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < a.nkeep;
        n += (int64_t)gridDim.x * blockDim.x) {
-    double xs = a.x[n];
+    double xs = a.x[(int64_t)r * a.n0 + n];
     for (int g = 0; g < a.nchunk; ++g) {
-      a.xstart[(int64_t)g * a.n0 + n] = xs;
-      xs = fma(a.apow[(int64_t)g * a.n0 + n], xs, a.xend[(int64_t)g * a.n0 + n]);
+      const int64_t o = ((int64_t)g * a.ntraj + r) * a.n0 + n;
+      a.xstart[o] = xs;
+      xs = fma(a.apow[o], xs, a.xend[o]);
     }
   }
 }
@@ -288,11 +303,11 @@ __global__ void modal_carry_kernel(ScanArgs a) {
 __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   extern __shared__ double smem[];
   const int nc = a.ncoef, ncs = nc > 0 ? nc : 1;
-  const int P = a.P;
+  const int P = a.Pout;
   double* coef = smem;                  // [2][TS][ncs]
   double* X = coef + 2 * TS * ncs;      // [MT][TS + 1]
   double* Gs = X + MT * (TS + 1);       // [P][MT]
-  const int g = blockIdx.y;
+  const int g = blockIdx.y, r = blockIdx.z;
   int64_t c0, c1;
   chunk_range(a, g, c0, c1);
   const int tid = threadIdx.x;
@@ -304,16 +319,18 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
     an = a.ac[nmode];
     q0 = a.ac[a.n0 + nmode];
     q1 = a.ac[2 * a.n0 + nmode];
-    x = (g == 0) ? a.x[nmode] : a.xstart[(int64_t)g * a.n0 + nmode];
-    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)c * a.n0];
+    x = (g == 0) ? a.x[(int64_t)r * a.n0 + nmode]
+                 : a.xstart[((int64_t)g * a.ntraj + r) * a.n0 + nmode];
+    for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)bcol(a, c, r) * a.n0];
   }
-  for (int p = 0; p < P; ++p) Gs[p * MT + tid] = live ? a.Gt[nmode + (int64_t)p * a.n0] : 0.0;
+  for (int p = 0; p < P; ++p)
+    Gs[p * MT + tid] = live ? a.Gt[nmode + (int64_t)(a.paired ? r : p) * a.n0] : 0.0;
   for (int64_t t0 = c0; t0 < c1; t0 += TS) {
     const int nt = (int)((c1 - t0) < TS ? (c1 - t0) : TS);
     __syncthreads();
     for (int idx = tid; idx < nt * nc; idx += MT) {
-      coef[(idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 0);
-      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = beta_coef(a, idx % nc, t0 + idx / nc, 1);
+      coef[(idx / nc) * ncs + idx % nc] = coef_for(a, idx % nc, r, t0 + idx / nc, 0);
+      if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = coef_for(a, idx % nc, r, t0 + idx / nc, 1);
     }
     __syncthreads();
     for (int tt = 0; tt < nt; ++tt) {
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
       X[tid * (TS + 1) + tt] = live ? x : 0.0;
       const int64_t k1 = t0 + tt + 1;   // state index after this step
       if (live && a.stride > 0 && a.Xsnap && k1 % a.stride == 0)
-        a.Xsnap[nmode + (k1 / a.stride - 1) * a.n0] = x;
+        a.Xsnap[nmode + ((k1 / a.stride - 1) * a.ntraj + r) * a.n0] = x;
     }
     __syncthreads();
     for (int o = tid; o < P * nt; o += MT) {
@@ -336,22 +353,25 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
         s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
         s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
       }
-      a.partial[((int64_t)blockIdx.x * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
+      a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
     }
   }
-  if (live && g == a.nchunk - 1) a.xout[nmode] = x;
+  if (live && g == a.nchunk - 1) a.xout[(int64_t)r * a.n0 + nmode] = x;
 }
 
 __global__ void probe_reduce_kernel(ScanArgs a, int nblk, const double* CPE, double* probes) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= a.kn * a.P) return;
-  const int64_t tt = idx / a.P;
-  const int p = (int)(idx % a.P);
+  const int Po = a.Pout;
+  if (idx >= a.kn * a.ntraj * Po) return;
+  const int64_t tt = idx / ((int64_t)a.ntraj * Po);
+  const int r = (int)((idx / Po) % a.ntraj);
+  const int p = (int)(idx % Po);
   double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += a.partial[((int64_t)b * a.kn + tt) * a.P + p];
+  for (int b = 0; b < nblk; ++b) v += a.partial[(((int64_t)r * nblk + b) * a.kn + tt) * Po + p];
   const int64_t k1 = a.k0 + tt + 1;
-  for (int j = 0; j < a.m; ++j) v = fma(CPE[p + (int64_t)j * a.P], srcv(a.iD, a.T, j, k1), v);
-  probes[(a.k0 + tt) * a.P + p] = v;
+  if (!a.indep)
+    for (int j = 0; j < a.m; ++j) v = fma(CPE[p + (int64_t)j * a.P], srcv(a.iD, a.T, j, k1), v);
+  probes[((a.k0 + tt) * a.ntraj + r) * Po + p] = v;
 }
 
 // snaps (n x nsnap, ld n): add PE i_D at the snapshot times.
@@ -419,9 +439,13 @@ double* modal_state(ModalState* ms) { return ms->x; }
 ec_status modal_set_mode_count(cudaStream_t s, ModalState* ms, int64_t nkeep) {
   if (nkeep < 1 || nkeep > ms->n0) return EC_ERR_ARG;
   ms->nkeep = nkeep;
-  if (nkeep < ms->n0) cudaMemsetAsync(ms->x + nkeep, 0, sizeof(double) * (ms->n0 - nkeep), s);
+  if (nkeep < ms->n0)
+    for (int r = 0; r < ms->ntraj; ++r)
+      cudaMemsetAsync(ms->x + (int64_t)r * ms->n0 + nkeep, 0, sizeof(double) * (ms->n0 - nkeep), s);
   return EC_OK;
 }
+
+int64_t modal_state_size(const ModalState* ms) { return ms->n0 * ms->ntraj; }
 const double* modal_tau(ModalState* ms) { return ms->tau; }
 const double* modal_U(ModalState* ms) { return ms->U; }
 
@@ -430,6 +454,8 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   const int64_t n0 = a.n0, ld = a.ld;
   ms->n = a.n; ms->n0 = n0; ms->m = a.m; ms->S = a.S; ms->P = a.P;
   ms->ncoef = 2 * a.m + a.S;
+  ms->rhs_mode = a.rhs_mode;
+  ms->ntraj = (a.rhs_mode == EC_RHS_SUM) ? 1 : a.S;
   ms->theta = a.theta; ms->dt = a.dt;
   const size_t nn = (size_t)n0 * n0;
   const int64_t nblk = (n0 + NB - 1) / NB;
@@ -439,9 +465,9 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   MS_TRY(alloc_n(&ms->ac, (size_t)3 * n0));
   MS_TRY(alloc_n(&ms->B, (size_t)n0 * (ms->ncoef > 0 ? ms->ncoef : 1)));
   MS_TRY(alloc_n(&ms->Gt, (size_t)n0 * (a.P > 0 ? a.P : 1)));
-  MS_TRY(alloc_n(&ms->x, (size_t)n0));
-  MS_TRY(alloc_n(&ms->work, (size_t)n0));
-  cudaMemsetAsync(ms->x, 0, sizeof(double) * n0, s);
+  MS_TRY(alloc_n(&ms->x, (size_t)n0 * ms->ntraj));
+  MS_TRY(alloc_n(&ms->work, (size_t)n0 * ms->ntraj));
+  cudaMemsetAsync(ms->x, 0, sizeof(double) * n0 * ms->ntraj, s);
   ms->CR = a.Ri;
   ms->ldCR = ld;
 
@@ -552,27 +578,32 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
                     std::vector<cudaEvent_t>* ev) {
   const int64_t n0 = ms->n0, T = sa.T;
   const int64_t nkeep = ms->nkeep;
+  const int nt = ms->ntraj;
+  const bool indep = ms->rhs_mode != EC_RHS_SUM;
+  const int Pout = (ms->rhs_mode == EC_RHS_PAIRED) ? 1 : ms->P;
   const int nblk = (int)((nkeep + MT - 1) / MT);
   const int64_t nsnap = (sa.snap_stride > 0 && sa.snaps) ? T / sa.snap_stride : 0;
-  if (nsnap > 0) MS_TRY(grow_n(&ms->Xsnap, ms->xsnapCap, (size_t)n0 * nsnap));
+  if (nsnap > 0) MS_TRY(grow_n(&ms->Xsnap, ms->xsnapCap, (size_t)n0 * nsnap * nt));
   const int64_t kmax = T < SUPER ? T : SUPER;
-  const int P = ms->P > 0 ? ms->P : 1;
-  MS_TRY(grow_n(&ms->partial, ms->partialCap, (size_t)nblk * kmax * P));
-  // chunks: enough (mode tile, chunk) CTAs for ~4 per SM, never shorter than CH_MIN steps
-  const int64_t gtarget = ((int64_t)4 * num_sms() + nblk - 1) / nblk;
+  MS_TRY(grow_n(&ms->partial, ms->partialCap,
+                (size_t)nblk * kmax * (Pout > 0 ? Pout : 1) * nt));
+  // chunks: enough (mode tile, chunk, trajectory) CTAs for ~4 per SM, never shorter than CH_MIN
+  const int64_t gtarget = ((int64_t)4 * num_sms() + (int64_t)nblk * nt - 1) / ((int64_t)nblk * nt);
   const int64_t maxchunks = (kmax + CH_MIN - 1) / CH_MIN;
   const int64_t gcap = gtarget < maxchunks ? gtarget : maxchunks;
-  MS_TRY(grow_n(&ms->chunkbuf, ms->chunkCap, (size_t)3 * (gcap > 0 ? gcap : 1) * n0));
+  MS_TRY(grow_n(&ms->chunkbuf, ms->chunkCap, (size_t)3 * (gcap > 0 ? gcap : 1) * n0 * nt));
   ScanArgs a{};
-  a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P; a.ncoef = ms->ncoef;
+  a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P;
+  a.ncoef = indep ? 1 : ms->ncoef;
   a.nkeep = nkeep;
+  a.ntraj = nt; a.indep = indep; a.paired = ms->rhs_mode == EC_RHS_PAIRED; a.Pout = Pout;
   a.theta = ms->theta; a.dt = ms->dt; a.ac = ms->ac; a.B = ms->B; a.Gt = ms->Gt;
   a.integ = ms->integ;
   a.src = sa.src; a.iD = sa.iD; a.partial = ms->partial;
   a.Xsnap = nsnap > 0 ? ms->Xsnap : nullptr; a.stride = nsnap > 0 ? sa.snap_stride : 0;
-  const int ncs = ms->ncoef > 0 ? ms->ncoef : 1;
+  const int ncs = a.ncoef > 0 ? a.ncoef : 1;
   const size_t smem1 = sizeof(double) * (size_t)(2 * TS * ncs);
-  const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + ms->P * MT);
+  const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + Pout * MT);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -589,8 +620,8 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
     a.x = ms->x;
     a.xout = ms->work;
     a.xend = ms->chunkbuf;
-    a.apow = ms->chunkbuf + (size_t)a.nchunk * n0;
-    a.xstart = ms->chunkbuf + (size_t)2 * a.nchunk * n0;
+    a.apow = ms->chunkbuf + (size_t)a.nchunk * n0 * nt;
+    a.xstart = ms->chunkbuf + (size_t)2 * a.nchunk * n0 * nt;
     if (ev) {
       ev->resize(ev->size() + 2);
       cudaEventCreate(&(*ev)[ev->size() - 2]);
@@ -598,14 +629,14 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
       cudaEventRecord((*ev)[ev->size() - 2], s);
     }
     if (a.nchunk > 1) {
-      modal_chunk_end_kernel<<<dim3(nblk, a.nchunk), MT, smem1, ::ec::counted(s)>>>(a);
-      modal_carry_kernel<<<(unsigned)((n0 + 255) / 256), 256, 0, ::ec::counted(s)>>>(a);
+      modal_chunk_end_kernel<<<dim3(nblk, a.nchunk, nt), MT, smem1, ::ec::counted(s)>>>(a);
+      modal_carry_kernel<<<dim3((unsigned)((n0 + 255) / 256), nt), 256, 0, ::ec::counted(s)>>>(a);
     }
-    modal_scan_kernel<<<dim3(nblk, a.nchunk), MT, smem2, ::ec::counted(s)>>>(a);
+    modal_scan_kernel<<<dim3(nblk, a.nchunk, nt), MT, smem2, ::ec::counted(s)>>>(a);
     if (ev) cudaEventRecord(ev->back(), s);
-    copy_matrix(s, nkeep, 1, ms->work, n0, ms->x, n0);
-    if (ms->P > 0 && sa.probes) {
-      const int64_t tot = a.kn * ms->P;
+    copy_matrix(s, nkeep, nt, ms->work, n0, ms->x, n0);
+    if (Pout > 0 && sa.probes) {
+      const int64_t tot = a.kn * Pout * nt;
       probe_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, ::ec::counted(s)>>>(
           a, nblk, sa.CPE, sa.probes);
     }
@@ -615,7 +646,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
     const int m = ms->m;
     // rows m.. of each snapshot: U x; rows 0..m-1: 0; then apply Q and add the particular field
     if (m > 0) cudaMemsetAsync(sa.snaps, 0, sizeof(double) * (size_t)n * nsnap, s);
-    MS_TRY(modal_product(s, ms, 0, nsnap, ms->Xsnap, n0, sa.snaps + m, n, sa.st, nkeep));
+    MS_TRY(modal_product(s, ms, 0, nsnap * nt, ms->Xsnap, n0, sa.snaps + m, n, sa.st, nkeep));
     if (m > 0) {
       MS_TRY(grow_n(&ms->small, ms->smallCap, (size_t)2 * m * nsnap));
       one_sided_q(s, n, m, sa.snaps, nsnap, sa.V, sa.Tm, ms->small, ms->small + m * nsnap, sa.st);
@@ -629,9 +660,11 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
 }
 
 void modal_set_internal_current(cudaStream_t s, ModalState* ms, const double* RiIi) {
-  // x = U^T (R_i I_i): the caller passes R_i I_i.
+  // x = U^T (R_i I_i): the caller passes R_i I_i; every trajectory starts from it.
   dgemm(s, T_, N_, ms->n0, 1, ms->n0, 1.0, ms->U, ms->n0, RiIi, ms->n0, 0.0, ms->x, ms->n0, 0,
         nullptr);
+  for (int r = 1; r < ms->ntraj; ++r)
+    copy_matrix(s, ms->n0, 1, ms->x, ms->n0, ms->x + (int64_t)r * ms->n0, ms->n0);
 }
 
 }  // namespace ec

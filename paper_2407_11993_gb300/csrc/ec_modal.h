@@ -26,6 +26,7 @@ struct ModalSetupArgs {
   double theta, dt;
   int precision;       // EC_PREC_*
   int integ;           // EC_INTEG_*
+  int rhs_mode;        // EC_RHS_*
   DevStatus* st;
 };
 
@@ -37,6 +38,7 @@ ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt
 ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& a,
                     std::vector<cudaEvent_t>* ev = nullptr);
 double* modal_state(ModalState* ms);
+int64_t modal_state_size(const ModalState* ms);
 // Integrate only the nkeep modes of largest tau; the others are held at zero.
 ec_status modal_set_mode_count(cudaStream_t s, ModalState* ms, int64_t nkeep);
 const double* modal_tau(ModalState* ms);

@@ -195,6 +195,52 @@ int rows_grid(int64_t n) {
 
 }  // namespace
 
+namespace {
+
+// Independent trajectories, no electrodes: out[:, r] = -dt R I_r - M_0[:, r] (s_r^{k+1} - s_r^k).
+__global__ void __launch_bounds__(256) plain_rhs_multi_kernel(StepArgs a, int64_t k, const double* I,
+                                                              double* out) {
+  const int r = blockIdx.y;
+  const double ds = a.src[(int64_t)r * (a.T + 1) + k + 1] - a.src[(int64_t)r * (a.T + 1) + k];
+  const double* Ir = I + (int64_t)r * a.n0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (long long e = a.R.ptr[i]; e < a.R.ptr[i + 1]; ++e) v = fma(a.R.val[e], Ir[a.R.col[e]], v);
+    out[i + (int64_t)r * a.n0] = fma(-a.dt, v, -a.Gsrc[i + (int64_t)r * a.n0] * ds);
+  }
+}
+
+// probes[r] = C[:, r] . I[:, r]  (paired read-out), C column-major n0 x S (leading dim ldc)
+__global__ void __launch_bounds__(256) paired_probe_kernel(int64_t n0, const double* C, int64_t ldc,
+                                                           const double* I, double* out) {
+  const int r = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n0; i += blockDim.x)
+    acc = fma(C[i + (int64_t)r * ldc], I[i + (int64_t)r * n0], acc);
+  __shared__ double sh[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    out[r] = t;
+  }
+}
+
+}  // namespace
+
+void plain_rhs_multi(cudaStream_t s, const StepArgs& a, int64_t k, const double* I, double* out) {
+  plain_rhs_multi_kernel<<<dim3(rows_grid(a.n0), a.S), 256, 0, ::ec::counted(s)>>>(a, k, I, out);
+}
+
+void paired_probes(cudaStream_t s, int64_t n0, int S, const double* C, int64_t ldc,
+                   const double* I, double* out) {
+  paired_probe_kernel<<<S, 256, 0, ::ec::counted(s)>>>(n0, C, ldc, I, out);
+}
+
 void plain_rhs(cudaStream_t s, const StepArgs& a) {
   plain_rhs_kernel<<<rows_grid(a.n0), 256, 0, ::ec::counted(s)>>>(a);
 }

@@ -38,7 +38,8 @@ NOALLOC_MAX_N = 8192
 class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
-                ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int)]
+                ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int),
+                ("rhs_mode", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -202,18 +203,22 @@ class ThetaMethod:
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
-                 integrator: str = "theta"):
+                 integrator: str = "theta", rhs: str = "sum"):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
             raise ValueError("precision must be 'fp64', 'bf16' or 'bf16x3'")
         if integrator not in ("theta", "exact"):
             raise ValueError("integrator must be 'theta' or 'exact'")
+        if rhs not in ("sum", "independent", "paired"):
+            raise ValueError("rhs must be 'sum', 'independent' or 'paired'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
-                        _PREC[precision], 1 if integrator == "exact" else 0)
+                        _PREC[precision], 1 if integrator == "exact" else 0,
+                        {"sum": 0, "independent": 1, "paired": 2}[rhs])
+        self.rhs = rhs
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h
@@ -251,20 +256,28 @@ class ThetaMethod:
             probes_out=None, snaps_out=None):
         """Advance T steps; returns (probes (P, T), snaps (N, nsnap))."""
         nsnap = T // snap_stride if snap_stride else 0
+        nt = 1 if self.rhs == "sum" else self.S
+        pout = 1 if self.rhs == "paired" else self.P
+        pshape = (T, pout) if nt == 1 else (T, nt, pout)
+        sshape = (nsnap, self.n) if nt == 1 else (nsnap, nt, self.n)
         if mem == EC_MEM_DEVICE:
             import torch
             dev = torch.device("cuda")
-            probes = probes_out if probes_out is not None else torch.empty((T, self.P), dtype=torch.float64, device=dev)
-            snaps = snaps_out if snaps_out is not None else torch.empty((nsnap, self.n), dtype=torch.float64, device=dev)
+            probes = probes_out if probes_out is not None else torch.empty(pshape, dtype=torch.float64, device=dev)
+            snaps = snaps_out if snaps_out is not None else torch.empty(sshape, dtype=torch.float64, device=dev)
         else:
-            probes = np.empty((T, self.P)) if probes_out is None else probes_out
-            snaps = np.empty((nsnap, self.n)) if snaps_out is None else snaps_out
+            probes = np.empty(pshape) if probes_out is None else probes_out
+            snaps = np.empty(sshape) if snaps_out is None else snaps_out
         ps, k1 = _ptr(src if self.S else None, mem)
         pi, k2 = _ptr(iD if self.m else None, mem)
         pp = c_void_p(probes.data_ptr() if mem == EC_MEM_DEVICE else probes.ctypes.data) if self.P else None
         pn = c_void_p(snaps.data_ptr() if mem == EC_MEM_DEVICE else snaps.ctypes.data) if nsnap else None
         check(lib().ec_run(self._h, int(T), ps, pi, pp, int(snap_stride) if nsnap else 0, pn, mem),
               "ec_run", self._h)
+        if nt > 1:
+            # (T, nt, pout) -> (nt, pout, T); (nsnap, nt, n) -> (nt, n, nsnap)
+            return probes.transpose(1, 2, 0) if mem != EC_MEM_DEVICE else probes.permute(1, 2, 0), \
+                snaps.transpose(1, 2, 0) if mem != EC_MEM_DEVICE else snaps.permute(1, 2, 0)
         return probes.T, snaps.T
 
     def state_size(self) -> int:

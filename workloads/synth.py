@@ -272,3 +272,21 @@ def small(n: int, T: int, seed: int = 0, electrodes: bool = True, coil: bool = T
     iD = step_current(T)[None, :] if electrodes else np.zeros((0, T + 1))
     return Problem(f"n{n}_small", inductance(g), resistance(g), E, M, MD, C, src, iD,
                    theta, dt, T, snap_stride, g)
+
+
+def coil_scan(n: int, T: int, n_side: int = 16, seed: int = 0, dt: float = 1e-6,
+              f_hz: float = 1e4, probes: int = 0) -> Problem:
+    """Independent excitations: n_side x n_side coils at z = 5 mm over the plate (one
+    right-hand side each), every coil driven by sin(2 pi f t); probes: each coil's own
+    pickup (C = M^T) unless ``probes`` > 0 pickups on a grid are requested."""
+    g = geometry(n, seed)
+    M = mutual(g, pickup_grid(n_side, n_side))
+    if probes:
+        px = max(1, int(math.isqrt(probes)))
+        C = mutual(g, pickup_grid(px, max(1, probes // px), z_mm=4.0)).T.copy()
+    else:
+        C = M.T.copy()
+    S = M.shape[1]
+    src = np.repeat(sine(T, dt, f_hz)[None, :], S, axis=0)
+    return Problem(f"n{n}_coilscan{S}", inductance(g), resistance(g), np.zeros((0, n)), M,
+                   np.zeros((n, 0)), C, src, np.zeros((0, T + 1)), 0.5, dt, T, 0, g)
