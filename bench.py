@@ -284,8 +284,8 @@ def our_arm(args) -> None:
     fwd_ms = mean("fwd_ms", "plain") / max(1.0, mean("fwd_launches", "plain"))
     bwd_ms = mean("bwd_ms", "plain") / max(1.0, mean("bwd_launches", "plain"))
     fam = {
-        "plain forward solve (trmv_lower_kernel)": fwd_ms * T,
-        "plain backward solve (trmv_lower_t_kernel)": bwd_ms * T,
+        "plain forward solve (tile_trmv_kernel<false>)": fwd_ms * T,
+        "plain backward solve (tile_trmv_kernel<true>)": bwd_ms * T,
         "modal setup (FP64 eigensolver pipeline)": mean("setup_ms", "modal"),
     }
     dominant = max(fam, key=fam.get)
@@ -294,7 +294,7 @@ def our_arm(args) -> None:
     bytes_fwd = 8.0 * n0 * (n0 + 1) / 2.0
     achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
     pk, pk_kind = peaks()
-    roofline = {"kernel": "trmv_lower_kernel", "bound": "alu", "achieved": achieved,
+    roofline = {"kernel": "tile_trmv_kernel<false>", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": None, "algorithmic_bytes": bytes_fwd,
                 "achieved_gbs": bytes_fwd / (fwd_ms * 1e-3) / 1e9,
@@ -303,7 +303,7 @@ def our_arm(args) -> None:
                              f"(HBM peak {pk_kind})",
                 "avg_launch_ms": fwd_ms, "dominant_family": dominant}
     # DRAM traffic from the committed ncu summary of this kernel, scaled by N0^2
-    traffic_path = os.path.join(ROOT, "profiles", "trmv_lower_n8192.md")
+    traffic_path = os.path.join(ROOT, "profiles", "tile_trmv_n8192.md")
     try:
         tv = {}
         with open(traffic_path) as f:
@@ -313,7 +313,7 @@ def our_arm(args) -> None:
                     tv[k.strip()] = float(v)
         if tv.get("traffic_bytes_per_launch") and tv.get("traffic_n0"):
             roofline["traffic"] = tv["traffic_bytes_per_launch"] * (n0 * n0) / tv["traffic_n0"] ** 2
-            roofline["traffic_note"] = "ncu DRAM read+write of one launch (profiles/trmv_lower_n8192.md)"
+            roofline["traffic_note"] = "ncu DRAM read+write of one launch (profiles/tile_trmv_n8192.md)"
     except (OSError, ValueError):
         pass
 

@@ -84,6 +84,9 @@ typedef struct ec_config {
   int precision;          /* modal form: EC_PREC_FP64 (default) or EC_PREC_BF16, see below */
   int integrator;         /* modal form: EC_INTEG_THETA (default) or EC_INTEG_EXACT, see below */
   int rhs_mode;           /* EC_RHS_SUM (default), EC_RHS_INDEPENDENT or EC_RHS_PAIRED, see below */
+  int tile_variant;       /* plain form, EC_SOLVE_INVERSE: 0 (default) = ec_setup times every launch
+                             shape of the per-step products on the actual factor and keeps the
+                             fastest; 1 .. 3 = use that shape.  No shape changes a result bit. */
 } ec_config;
 
 /* How the s coil columns of M drive the system (batched right-hand sides).
@@ -150,6 +153,11 @@ typedef struct ec_timing {
    * modal scan kernel (modal form; every launch) during the last ec_run. */
   double fwd_ms, bwd_ms, scan_ms;
   int64_t fwd_launches, bwd_launches, scan_launches;
+  /* Plain form, EC_SOLVE_INVERSE: launch shape of the per-step products in use
+   * (1 .. 3) and, when ec_setup tuned it, the time of one product pair per shape
+   * (entries past the number of shapes are 0). */
+  int64_t tile_variant;
+  double tile_tune_ms[4];
 } ec_timing;
 
 /* Create a context on cfg->device.  *out receives the handle. */

@@ -9,6 +9,7 @@
 
 #include "ec_kernels.h"
 #include "ec_modal.h"
+#include "ec_tiles.h"
 
 using namespace ec;
 
@@ -31,10 +32,13 @@ struct ec_ctx {
   // plain
   double* dZ = nullptr;      // n0 x n0 Cholesky factor of L_i + theta dt R_i
   double* dDinv = nullptr;   // inverses of its 64 x 64 diagonal blocks
-  double* dW = nullptr;      // n0 x n0 inverse factor C^{-1} (EC_SOLVE_INVERSE)
-  double* dPart1 = nullptr;  // chunk partials of C^{-1} b
-  double* dPart2 = nullptr;  // chunk partials of C^{-T} y
-  double* dYsol = nullptr;   // C^{-1} b
+  double* dW = nullptr;      // n0 x n0 inverse factor C^{-1}, square column-major (kept
+                             // only for independent right-hand sides; freed otherwise)
+  TilePlan tiles;            // packed-tile layout of C^{-1} (EC_SOLVE_INVERSE)
+  double* dWp = nullptr;     // C^{-1} as packed lower 64 x 64 tiles
+  double* dPart1 = nullptr;  // unit partials of C^{-1} b
+  double* dPart2 = nullptr;  // unit partials of C^{-T} y
+  double* dYsol = nullptr;   // C^{-1} b (npad, zero tail)
   int ntraj = 1;             // trajectories (independent right-hand sides)
   double* dRhsM = nullptr;   // n0 x ntraj work (independent right-hand sides)
   double* dYM = nullptr;
@@ -88,8 +92,6 @@ struct ec_ctx {
 
 namespace {
 
-constexpr int TRMV_CHUNK = 16;   // 64 x 64 tiles per CTA in the inverse-factor products
-
 cudaError_t dev_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 8); }
 
 template <typename T>
@@ -121,7 +123,7 @@ ec_status grow(T** p, size_t& cap, size_t count) {
 
 void free_setup(ec_ctx* c) {
   dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
-  dfree(c->dW); dfree(c->dPart1); dfree(c->dPart2); dfree(c->dYsol);
+  dfree(c->dW); dfree(c->dWp); tile_plan_free(&c->tiles); dfree(c->dPart1); dfree(c->dPart2); dfree(c->dYsol);
   dfree(c->dRhsM); dfree(c->dYM); dfree(c->dXM);
   dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
   dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
@@ -211,9 +213,6 @@ StepArgs step_args(ec_ctx* c, int64_t T, double* probes, double* snaps, int64_t 
   a.dots = c->dDots; a.partial = c->dPartial; a.counter = c->dCounter;
   a.probes = probes; a.snaps = snaps; a.snap_stride = stride;
   a.tickets = c->dTickets; a.epoch = c->dEpoch; a.st = c->st;
-  const bool inv = c->cfg.form == EC_FORM_PLAIN && c->cfg.plain_solver == EC_SOLVE_INVERSE;
-  a.dpart = inv ? c->dPart2 : nullptr;
-  a.npart = inv ? trmv_chunks(c->n0, TRMV_CHUNK) : 0;
   return a;
 }
 
@@ -244,14 +243,26 @@ ec_status plain_factor(ec_ctx* c) {
   potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st);
   if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
     EC_TRY(alloc(&c->dW, (size_t)n0 * n0));
-    const int nc = trmv_chunks(n0, TRMV_CHUNK);
-    EC_TRY(alloc(&c->dPart1, (size_t)nc * n0));
-    EC_TRY(alloc(&c->dPart2, (size_t)nc * n0));
-    EC_TRY(alloc(&c->dYsol, (size_t)n0));
+    EC_TRY(tile_plan_create(n0, &c->tiles));
+    const size_t prow = (size_t)tile_partial_rows(c->tiles), npad = (size_t)c->tiles.npad;
+    EC_TRY(alloc(&c->dWp, tile_packed_doubles(c->tiles)));
+    EC_TRY(alloc(&c->dPart1, prow * npad));
+    EC_TRY(alloc(&c->dPart2, prow * npad));
+    EC_TRY(alloc(&c->dYsol, npad));
+    cudaMemsetAsync(c->dYsol, 0, sizeof(double) * npad, c->stream);
     trtri_lower(c->stream, n0, c->dZ, n0, c->dDinv, c->dW, n0, c->st);
+    tile_pack_lower(c->stream, c->tiles, c->dW, n0, c->dWp);
+    EC_TRY(tile_autotune(c->stream, &c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
+                         c->st, c->cfg.tile_variant));
+    c->tim.tile_variant = c->tiles.variant + 1;
+    for (int v = 0; v < TILE_VARIANTS && v < 4; ++v) c->tim.tile_tune_ms[v] = c->tiles.tune_ms[v];
   }
   c->tim.factor_ms = t.stop_ms();
-  return collect(c);
+  ec_status rc = collect(c);
+  // The per-step products read the packed tiles; the square inverse is kept only
+  // for the GEMMs of independent right-hand sides.
+  if (rc == EC_OK && c->dW && c->cfg.rhs_mode == EC_RHS_SUM) dfree(c->dW);
+  return rc;
 }
 
 }  // namespace
@@ -292,6 +303,7 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
       cfg->plain_solver != EC_SOLVE_INVERSE)
     return EC_ERR_UNSUPPORTED;
   if (cfg->integrator == EC_INTEG_EXACT && cfg->form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
+  if (cfg->tile_variant < 0 || cfg->tile_variant > TILE_VARIANTS) return EC_ERR_ARG;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
@@ -438,7 +450,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     copy_matrix(c->stream, n0, c->m, c->dWR + c->m, n, c->dDmat + n0 * (p + c->m), n0);
   }
   // state
-  c->update_grid = (int)((n0 + 1023) / 1024);
+  c->update_grid = (int)((n0 + 255) / 256);
   if (c->update_grid > num_sms() * 2) c->update_grid = num_sms() * 2;
   if (c->update_grid < 1) c->update_grid = 1;
   c->trsv_grid = num_sms() * 2;
@@ -449,7 +461,11 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     EC_TRY(alloc(&c->dYM, (size_t)n0 * c->ntraj));
     EC_TRY(alloc(&c->dXM, (size_t)n0 * c->ntraj));
   }
-  EC_TRY(alloc(&c->dWork, (size_t)n0));
+  // padded to whole 64-row tiles with a zero tail (the packed-tile products read
+  // their input vector in 64-entry segments)
+  const size_t nwork = (size_t)((n0 + NB - 1) / NB) * NB;
+  EC_TRY(alloc(&c->dWork, nwork));
+  cudaMemsetAsync(c->dWork, 0, sizeof(double) * nwork, c->stream);
   EC_TRY(alloc(&c->dTmpN, (size_t)n));
   EC_TRY(alloc(&c->dDots, (size_t)MAXD));
   EC_TRY(alloc(&c->dPartial, (size_t)c->update_grid * (c->D > 0 ? c->D : 1)));
@@ -584,8 +600,8 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
         for (int q = 0; q < 3; ++q) cudaEventCreate(&e3[q]);
       }
       if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
-        trmv_pair(c->stream, c->n0, c->dW, c->n0, c->dWork, c->dPart1, c->dYsol, c->dPart2,
-                  TRMV_CHUNK, c->st, e3);
+        tile_trmv_pair(c->stream, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
+                       c->dWork, c->st, e3);
       } else {
         trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
                   c->trsv_grid, c->spin_limit, c->st, e3);
@@ -686,9 +702,8 @@ ec_status ec_solve_z(ec_ctx* c, const double* b, double* x, int mem) {
   const int64_t n0 = c->n0;
   EC_TRY(copy_in(c, c->dWork, b, (size_t)n0, mem));
   if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
-    trmv_pair(c->stream, n0, c->dW, n0, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK,
-              c->st);
-    sum_partials(c->stream, n0, trmv_chunks(n0, TRMV_CHUNK), c->dPart2, c->dWork);
+    tile_trmv_pair(c->stream, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
+                   c->dWork, c->st);
   } else {
     TrsvSync sy{c->dFlags, c->dFlags + (n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
     trsv_begin(c->stream, sy);
@@ -703,8 +718,23 @@ ec_status ec_get_inverse_factor(ec_ctx* c, double* W, int mem) {
   if (!c || !W) return EC_ERR_ARG;
   if (!c->ready || c->cfg.form != EC_FORM_PLAIN || c->cfg.plain_solver != EC_SOLVE_INVERSE)
     return EC_ERR_STATE;
-  EC_TRY(copy_out(c, W, c->dW, (size_t)c->n0 * c->n0, mem));
-  return collect(c);
+  if (c->dW) {
+    EC_TRY(copy_out(c, W, c->dW, (size_t)c->n0 * c->n0, mem));
+    return collect(c);
+  }
+  // Square form from the packed tiles.
+  if (mem == EC_MEM_DEVICE) {
+    tile_unpack_lower(c->stream, c->tiles, c->dWp, W, c->n0);
+    return collect(c);
+  }
+  double* tmp = nullptr;
+  EC_TRY(alloc(&tmp, (size_t)c->n0 * c->n0));
+  tile_unpack_lower(c->stream, c->tiles, c->dWp, tmp, c->n0);
+  ec_status rc = copy_out(c, W, tmp, (size_t)c->n0 * c->n0, mem);
+  if (rc == EC_OK) rc = collect(c);
+  cudaStreamSynchronize(c->stream);
+  dfree(tmp);
+  return rc;
 }
 
 ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int64_t ckpt,
@@ -733,7 +763,7 @@ ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int6
       (rc = alloc(&ck, (size_t)n * (nseg + 1))) || (rc = alloc(&seg, (size_t)n * (ckpt + 1))) ||
       (rc = alloc(&mu, (size_t)(S > 0 ? S : 1) * (T + 2))) || (rc = alloc(&gR, (size_t)n)) ||
       (rc = alloc(&lamA, (size_t)n)) || (rc = alloc(&lamB, (size_t)n)) ||
-      (rc = alloc(&rhs, (size_t)n)) || (rc = alloc(&fin, (size_t)n)) || (rc = alloc(&Jd, 1)) ||
+      (rc = alloc(&rhs, (size_t)c->tiles.npad)) || (rc = alloc(&fin, (size_t)n)) || (rc = alloc(&Jd, 1)) ||
       (rc = alloc(&gs, (size_t)(S > 0 ? S : 1) * (T + 1))) ||
       (rc = alloc(&part, (size_t)grid * (S > 0 ? S : 1)))) {
     release();
@@ -751,15 +781,15 @@ ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int6
   cudaMemsetAsync(gR, 0, sizeof(double) * n, st);
   cudaMemsetAsync(lamA, 0, sizeof(double) * n, st);
   cudaMemsetAsync(lamB, 0, sizeof(double) * n, st);
-  cudaMemsetAsync(rhs, 0, sizeof(double) * n, st);
-  const int nc = trmv_chunks(n, TRMV_CHUNK);
+  cudaMemsetAsync(rhs, 0, sizeof(double) * c->tiles.npad, st);
   // forward pass with checkpoints every ckpt steps
   cudaMemsetAsync(c->dK, 0, sizeof(int64_t), st);
   copy_matrix(st, n, 1, c->dIi, n, ck, n);
   StepArgs a = step_args(c, T, probes, nullptr, 0);
   for (int64_t k = 0; k < T; ++k) {
     plain_rhs(st, a);
-    trmv_pair(st, n, c->dW, n, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
+    tile_trmv_pair(st, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2, c->dWork,
+                   c->st);
     plain_update(st, a, c->update_grid, 0);
     if ((k + 1) % ckpt == 0) copy_matrix(st, n, 1, c->dIi, n, ck + ((k + 1) / ckpt) * n, n);
   }
@@ -778,14 +808,14 @@ ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int6
     cudaStreamSynchronize(st);   // k0 lives on the host stack
     for (int64_t k = k0; k < k1; ++k) {
       plain_rhs(st, ar);
-      trmv_pair(st, n, c->dW, n, c->dWork, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
+      tile_trmv_pair(st, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2, c->dWork,
+                   c->st);
       plain_update(st, ar, c->update_grid, 0);
       copy_matrix(st, n, 1, c->dIi, n, seg + (k - k0 + 1) * n, n);
     }
     for (int64_t k = k1; k > k0; --k) {
       adj_rhs(st, n, P, dt, c->csr, lam_next, rhs, probes + (k - 1) * P, vd + (k - 1) * P, c->dC);
-      trmv_pair(st, n, c->dW, n, rhs, c->dPart1, c->dYsol, c->dPart2, TRMV_CHUNK, c->st);
-      sum_partials(st, n, nc, c->dPart2, lam);
+      tile_trmv_pair(st, c->tiles, c->dWp, rhs, c->dPart1, c->dYsol, c->dPart2, lam, c->st);
       adj_accum(st, n, S, dt, theta, lam, seg + (k - k0) * n, seg + (k - k0 - 1) * n, gR, c->dM,
                 part, c->dCounter, mu + k, T + 2, grid);
       double* t = lam_next;

@@ -55,8 +55,6 @@ struct StepArgs {
   double* work;                // n0 right-hand side / solution
   double* dots;                // D values for the current state
   double* partial;             // grid x D partial sums
-  const double* dpart;         // npart x n0 partial sums of the solve (inverse-factor path)
-  int npart;                   // 0: the solve result is in work
   unsigned* counter;           // last-block counter
   double* probes;              // T x P output (may be null)
   double* snaps;               // nsnap x n output (may be null)

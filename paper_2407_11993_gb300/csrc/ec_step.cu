@@ -101,41 +101,49 @@ __global__ void __launch_bounds__(256) ri_apply_kernel(StepArgs a, double* out) 
     out[i] = ri_row(a, i, alpha, beta);
 }
 
+// I_i += dI (mode 0), then the D dot products of the new state: per-CTA partials
+// (each warp reduces its rows with shuffles, one barrier for all D), summed by the
+// last CTA with one warp per dot product (lanes stride over the CTA partials).
 __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode) {
-  __shared__ double sh[33];
+  __shared__ double sh[8][MAXD];
   __shared__ bool last;
   const int64_t n0 = a.n0;
   const int64_t chunk = (n0 + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = (b0 + chunk < n0) ? b0 + chunk : n0;
   if (mode == 0) {
-    if (a.npart > 0) {
-      for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        double d = 0.0;
-        for (int q = 0; q < a.npart; ++q) d += a.dpart[q * n0 + i];
-        a.Ii[i] += d;
-      }
-    } else {
-      for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
-    }
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = 0; d < a.D; ++d) {
-    const double* col = a.Dmat + (int64_t)d * n0;
-    double s = 0.0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s = fma(col[i], a.Ii[i], s);
+  // Dot products in batches of 8 columns: the 8 loads of a row are issued before
+  // any of them is used, so the latency is paid once per batch, not per column.
+  for (int d0 = 0; d0 < a.D; d0 += 8) {
+    double s[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[w] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-      a.partial[(int64_t)blockIdx.x * a.D + d] = t;
+    for (int j = 0; j < 8; ++j) s[j] = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const double x = a.Ii[i];
+      double c[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) c[j] = (d0 + j < a.D) ? a.Dmat[i + (int64_t)(d0 + j) * n0] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s[j] = fma(c[j], x, s[j]);
     }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+      if (lane == 0 && d0 + j < a.D) sh[w][d0 + j] = s[j];
+    }
   }
+  __syncthreads();
+  for (int d = threadIdx.x; d < a.D; d += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q][d];
+    a.partial[(int64_t)blockIdx.x * a.D + d] = t;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(a.counter, 1u);
@@ -145,14 +153,18 @@ __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode)
   if (!last) return;
   __threadfence();
   const int64_t k = *a.kstep;   // this update produces state k + 1 (mode 0)
-  for (int d = threadIdx.x; d < a.D; d += blockDim.x) {
+  for (int d = w; d < a.D; d += (int)(blockDim.x >> 5)) {
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(a.partial + (int64_t)b * a.D + d);
-    a.dots[d] = t;
-    if (mode == 0 && d < a.P && a.probes != nullptr) {
-      double y = t;
-      for (int j = 0; j < a.m; ++j) y = fma(a.CPE[d + (int64_t)j * a.P], src_at(a.iD, a.T, j, k + 1), y);
-      a.probes[k * a.P + d] = y;
+    for (unsigned b = lane; b < gridDim.x; b += 32) t += __ldcg(a.partial + (int64_t)b * a.D + d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      a.dots[d] = t;
+      if (mode == 0 && d < a.P && a.probes != nullptr) {
+        double y = t;
+        for (int j = 0; j < a.m; ++j) y = fma(a.CPE[d + (int64_t)j * a.P], src_at(a.iD, a.T, j, k + 1), y);
+        a.probes[k * a.P + d] = y;
+      }
     }
   }
   __syncthreads();

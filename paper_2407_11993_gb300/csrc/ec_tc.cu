@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "ec_async.cuh"
 #include "ec_internal.h"
 #include "ec_tc.h"
 
@@ -35,43 +36,15 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;   // + alignment slack
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
+using dev::mbar_expect_tx;
+using dev::mbar_init;
+using dev::mbar_try_wait;
+using dev::smem_u32;
 
 // Bounded wait; false (and the status set) when the bound runs out.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, int where) {
-  long long it = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if (++it > WAIT_LIMIT) {
-      if (atomicCAS(&st->code, 0, (int)EC_ERR_TIMEOUT) == 0) st->where = where;
-      return false;
-    }
-    if (*(volatile int*)&st->code) return false;
-  }
-  return true;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st,
+                                          int where) {
+  return dev::mbar_wait(bar, parity, st, where, WAIT_LIMIT);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,

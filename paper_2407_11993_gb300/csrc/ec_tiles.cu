@@ -1,0 +1,442 @@
+// Inverse-factor products y = W b and x = W^T y on packed lower-triangular tiles.
+//
+// The plain form solves with the same factor every step (Sec. 3.3.1); with
+// W = C^{-1} both solves are triangular matrix-vector products.  On GB300 an SM
+// retires two FP64 FMAs per clock, so a 64 x 64 tile costs 2048 SM-cycles of
+// FP64 work and ~5 TB/s of HBM traffic keeps every FP64 pipe busy: the products
+// are FP64-bound, and the kernel's job is to keep the FP64 pipe fed.
+//
+// Design:
+//   * W lives as packed 64 x 64 tiles (lower triangle only: half the bytes of
+//     the square array), each tile 32 KB contiguous, XOR-swizzled inside so
+//     that both the row-wise and the column-wise product read shared memory
+//     without bank conflicts;
+//   * one CTA per SM, persistent: a producer lane streams tiles (and the 64
+//     matching vector entries) into a shared-memory ring with bulk asynchronous
+//     copies completing on mbarriers; eight consumer warps work on the tiles;
+//   * work is split into units (a run of `chunk` tiles of one tile row, or one
+//     tile column), ordered largest first and dealt round-robin to the CTAs, so
+//     every SM gets the same FP64 work to within one unit;
+//   * each warp owns 8 output rows (forward) or 8 output columns (transposed) of
+//     a unit; lanes split the other index, partial sums are reduced with
+//     shuffles and written per unit, then summed in a fixed order: results are
+//     bitwise deterministic and independent of the grid size.
+// Every mbarrier wait is bounded; a wait that runs out records EC_ERR_TIMEOUT.
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "ec_async.cuh"
+#include "ec_tiles.h"
+
+namespace ec {
+
+namespace {
+
+constexpr int TB = 64;
+constexpr int TILE_DBL = TB * TB;
+constexpr uint32_t TILE_BYTES = TILE_DBL * 8;
+constexpr uint32_t SEG_BYTES = TB * 8;
+constexpr long long WAIT_LIMIT = 1ll << 26;
+constexpr int CW = 8;   // consumer warps: 2 output halves x 4 quarters of the inner index
+constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
+
+struct Meta {
+  int I, J, c, flags;
+};
+
+template <int ST>
+struct Smem {
+  double W[ST][TILE_DBL];
+  double v[ST][TB];
+  uint64_t full[ST], empty[ST];
+  Meta meta[ST];
+};
+template <int ST>
+constexpr size_t smem_bytes() {
+  return sizeof(Smem<ST>) + 128;   // + alignment slack
+}
+
+struct TileArgs {
+  int64_t n, nblk, npad, nunits;
+  int chunk;
+  const double* Wp;
+  const double* x;     // input vector (npad, zero tail)
+  double* part;        // partial rows x npad
+  const int2* units;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ int64_t tile_index(int64_t I, int64_t J) { return I * (I + 1) / 2 + J; }
+
+// Warp-uniform bounded wait: every lane polls, the warp leaves together.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, DevStatus* st,
+                                          int where) {
+  const int lane = threadIdx.x & 31;
+  for (long long it = 0;; ++it) {
+    const bool ok = dev::mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if (it > WAIT_LIMIT) {
+      if (lane == 0 && atomicCAS(&st->code, 0, (int)EC_ERR_TIMEOUT) == 0) st->where = where;
+      return false;
+    }
+    if ((it & (dev::STATUS_POLL - 1)) == 0) {
+      int bad = 0;
+      if (lane == 0) bad = *(volatile int*)&st->code != 0;
+      if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+    }
+  }
+}
+
+// 8 consumer warps, ST ring stages, MINB CTAs per SM.  Every variant sums each
+// output entry in the same order, so all variants give bitwise identical results.
+template <bool TRANS, int ST, int MINB>
+__global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(TileArgs a) {
+  if (*(volatile const int*)&a.st->code) return;
+  extern __shared__ uint8_t smem_raw[];
+  Smem<ST>& sm = *reinterpret_cast<Smem<ST>*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      dev::mbar_init(&sm.full[s], 1);
+      dev::mbar_init(&sm.empty[s], CW);
+    }
+    dev::fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == CW) {
+    // ---- producer: one lane streams the tiles of this CTA's units ----------
+    if (lane != 0) return;
+    const uint64_t pol = dev::policy_evict_first();
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
+      const int2 un = a.units[u];
+      const int64_t K = un.x;                       // tile row (forward) / column (transposed)
+      int64_t t0, t1;
+      if (!TRANS) {
+        t0 = (int64_t)un.y * a.chunk;
+        t1 = min(t0 + a.chunk, K + 1);
+      } else {
+        t0 = K + (int64_t)un.y * a.chunk;
+        t1 = min(t0 + a.chunk, a.nblk);
+      }
+      for (int64_t t = t0; t < t1; ++t) {
+        const int s = (int)(it % ST);
+        const uint32_t ph = (uint32_t)((it / ST) & 1);
+        if (!dev::mbar_wait(&sm.empty[s], ph ^ 1u, a.st, 40, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        const int64_t I = TRANS ? t : K, J = TRANS ? K : t;
+        sm.meta[s] = Meta{(int)I, (int)J, un.y, (t == t0 ? F_FIRST : 0) | (t == t1 - 1 ? F_LAST : 0)};
+        dev::mbar_expect_tx(&sm.full[s], TILE_BYTES + SEG_BYTES);
+        dev::bulk_g2s_hint(sm.W[s], a.Wp + tile_index(I, J) * TILE_DBL, TILE_BYTES, &sm.full[s], pol);
+        dev::bulk_g2s(sm.v[s], a.x + (TRANS ? I : J) * TB, SEG_BYTES, &sm.full[s]);
+        ++it;
+      }
+    }
+    bool ended = false;
+    if (ok) {
+      const int s = (int)(it % ST);
+      const uint32_t ph = (uint32_t)((it / ST) & 1);
+      if (dev::mbar_wait(&sm.empty[s], ph ^ 1u, a.st, 41, WAIT_LIMIT)) {
+        sm.meta[s].flags = F_END;
+        dev::mbar_arrive(&sm.full[s]);
+        ended = true;
+      }
+    }
+    // Drain: every issued copy must land before the CTA's shared memory is released.
+    for (int64_t j = max((int64_t)0, it - ST + (ended ? 1 : 0)); j < it; ++j) {
+      const int s = (int)(j % ST);
+      const uint32_t ph = (uint32_t)((j / ST) & 1);
+      for (long long q = 0; q < WAIT_LIMIT && !dev::mbar_try_wait(&sm.full[s], ph); ++q) {
+      }
+    }
+    return;
+  }
+
+  // ---- consumers ------------------------------------------------------------
+  // Warp w = (h, q): lane l owns output row (forward) / column (transposed)
+  // h * 32 + l of the tile and sums over the 16 inner indices q * 16 .. q * 16 + 15
+  // with 4 independent accumulators.  Each (unit, q) writes its own partial row,
+  // so no sum crosses lanes or warps inside the kernel (on GB300 an FP64 add costs
+  // as much as an FMA: a shuffle reduction per unit would double the FP64 work).
+  const int h = warp & 1, q = warp >> 1;
+  const int o = h * 32 + lane;     // output index within the tile
+  double acc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+  for (int64_t it = 0;; ++it) {
+    const int s = (int)(it % ST);
+    const uint32_t ph = (uint32_t)((it / ST) & 1);
+    if (!warp_wait(&sm.full[s], ph, a.st, 42)) break;
+    const Meta m = sm.meta[s];
+    if (m.flags & F_END) break;
+    if (m.flags & F_FIRST) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+    }
+    const double* Wt = sm.W[s];
+    const double2* vv = reinterpret_cast<const double2*>(sm.v[s] + q * 16);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const double2 v = vv[k2];                // inner indices i0, i0 + 1 (broadcast)
+      const int i0 = q * 16 + 2 * k2, i1 = i0 + 1;
+      double w0, w1;
+      if (!TRANS) {                            // W[o, i]: column i, row o
+        w0 = Wt[i0 * TB + (o ^ i0)];
+        w1 = Wt[i1 * TB + (o ^ i1)];
+      } else {                                 // W[i, o]: column o, row i
+        w0 = Wt[o * TB + (i0 ^ o)];
+        w1 = Wt[o * TB + (i1 ^ o)];
+      }
+      acc[(2 * k2) & 3] = fma(w0, v.x, acc[(2 * k2) & 3]);
+      acc[(2 * k2 + 1) & 3] = fma(w1, v.y, acc[(2 * k2 + 1) & 3]);
+    }
+    __syncwarp();
+    if (lane == 0) dev::mbar_arrive(&sm.empty[s]);
+    if (m.flags & F_LAST) {
+      const double t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      const int64_t blk = TRANS ? m.J : m.I;
+      a.part[((int64_t)m.c * 4 + q) * a.npad + blk * TB + o] = t;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t tile_row_of(int64_t t) {
+  int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > t) --I;
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  return I;
+}
+
+__global__ void pack_kernel(int64_t n, int64_t ntiles, const double* W, int64_t ldw, double* Wp) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t I = tile_row_of(t), J = t - I * (I + 1) / 2;
+    for (int e = threadIdx.x; e < TILE_DBL; e += blockDim.x) {
+      const int c = e >> 6, r = (e & 63) ^ c;
+      const int64_t row = I * TB + r, col = J * TB + c;
+      const bool in = row < n && col < n && (I != J || r >= c);
+      Wp[t * TILE_DBL + e] = in ? W[row + col * ldw] : 0.0;
+    }
+  }
+}
+
+__global__ void unpack_kernel(int64_t n, int64_t ntiles, const double* Wp, double* W, int64_t ldw) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t I = tile_row_of(t), J = t - I * (I + 1) / 2;
+    for (int e = threadIdx.x; e < TILE_DBL; e += blockDim.x) {
+      const int c = e >> 6, r = (e & 63) ^ c;
+      const int64_t row = I * TB + r, col = J * TB + c;
+      if (row < n && col < n && (I != J || r >= c)) W[row + col * ldw] = Wp[t * TILE_DBL + e];
+    }
+  }
+}
+
+// out[i] = sum of the partial rows holding data for entry i.  A block covers 64
+// consecutive entries with SUM_G thread rows; thread row g sums partial rows
+// g, g + SUM_G, ... with two independent accumulators (so loads stay in flight),
+// then the thread rows are combined in a fixed order.  The partials were just
+// written and sit in L2; the kernel is latency-bound, hence the wide blocks.
+constexpr int SUM_G = 16;
+
+__global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(int64_t n, int64_t nblk,
+                                                            int64_t npad, int chunk, int trans,
+                                                            const double* part, double* out) {
+  __shared__ double red[SUM_G][TB];
+  const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int64_t i = (int64_t)blockIdx.x * TB + tx;
+  double s0 = 0.0, s1 = 0.0;
+  if (i < n) {
+    const int64_t nc = trans ? tile_valid_rows_t(i, nblk, chunk) : tile_valid_rows(i, chunk);
+    const double* p = part + i;
+    int64_t r = g;
+    for (; r + SUM_G < nc; r += 2 * SUM_G) {
+      s0 += p[r * npad];
+      s1 += p[(r + SUM_G) * npad];
+    }
+    if (r < nc) s0 += p[r * npad];
+  }
+  red[g][tx] = s0 + s1;
+  __syncthreads();
+#pragma unroll
+  for (int h = SUM_G / 2; h > 0; h >>= 1) {
+    if (g < h) red[g][tx] += red[g + h][tx];
+    __syncthreads();
+  }
+  if (g == 0 && i < n) out[i] = red[0][tx];
+}
+
+struct Variant {
+  void (*fwd)(TileArgs);
+  void (*bwd)(TileArgs);
+  int threads;
+  size_t smem;
+};
+
+// Launch shapes the autotuner chooses from: (ring stages, CTAs per SM).
+const Variant kVariants[TILE_VARIANTS] = {
+    {tile_trmv_kernel<false, 4, 1>, tile_trmv_kernel<true, 4, 1>, CW * 32 + 32, smem_bytes<4>()},
+    {tile_trmv_kernel<false, 3, 2>, tile_trmv_kernel<true, 3, 2>, CW * 32 + 32, smem_bytes<3>()},
+    {tile_trmv_kernel<false, 6, 1>, tile_trmv_kernel<true, 6, 1>, CW * 32 + 32, smem_bytes<6>()},
+};
+
+std::mutex g_attr_mu;
+bool g_attr_done[64] = {};
+
+void ensure_attributes() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (dev < 0 || dev >= 64 || g_attr_done[dev]) return;
+  for (const Variant& v : kVariants) {
+    cudaFuncSetAttribute(v.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    cudaFuncSetAttribute(v.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+  }
+  g_attr_done[dev] = true;
+}
+
+}  // namespace
+
+ec_status tile_plan_create(int64_t n, TilePlan* p) {
+  tile_plan_free(p);
+  p->n = n;
+  p->nblk = (n + TB - 1) / TB;
+  p->npad = p->nblk * TB;
+  p->ntiles = p->nblk * (p->nblk + 1) / 2;
+  const int64_t sms = num_sms();
+  int64_t chunk = p->ntiles / (sms * 16);
+  p->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, chunk));
+  std::vector<int2> fwd, bwd;
+  for (int64_t K = 0; K < p->nblk; ++K) {
+    const int64_t nf = K / p->chunk + 1;                          // tiles 0..K of row K
+    for (int64_t c = 0; c < nf; ++c) fwd.push_back(make_int2((int)K, (int)c));
+    const int64_t nbk = (p->nblk - 1 - K) / p->chunk + 1;         // tiles K..nblk-1 of column K
+    for (int64_t c = 0; c < nbk; ++c) bwd.push_back(make_int2((int)K, (int)c));
+  }
+  const int64_t nblk = p->nblk, ch = p->chunk;
+  auto size_f = [&](const int2& u) {
+    return std::min<int64_t>((int64_t)u.y * ch + ch, (int64_t)u.x + 1) - (int64_t)u.y * ch;
+  };
+  auto size_b = [&](const int2& u) {
+    const int64_t t0 = (int64_t)u.x + (int64_t)u.y * ch;
+    return std::min<int64_t>(t0 + ch, nblk) - t0;
+  };
+  auto order = [](auto size) {
+    return [size](const int2& a, const int2& b) {
+      const int64_t sa = size(a), sb = size(b);
+      if (sa != sb) return sa > sb;
+      if (a.x != b.x) return a.x < b.x;
+      return a.y < b.y;
+    };
+  };
+  std::stable_sort(fwd.begin(), fwd.end(), order(size_f));
+  std::stable_sort(bwd.begin(), bwd.end(), order(size_b));
+  p->nunits = (int64_t)fwd.size();
+  if (cudaMalloc((void**)&p->units_fwd, sizeof(int2) * fwd.size()) != cudaSuccess ||
+      cudaMalloc((void**)&p->units_bwd, sizeof(int2) * bwd.size()) != cudaSuccess) {
+    cudaGetLastError();
+    tile_plan_free(p);
+    return EC_ERR_OOM;
+  }
+  if (cudaMemcpy(p->units_fwd, fwd.data(), sizeof(int2) * fwd.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(p->units_bwd, bwd.data(), sizeof(int2) * bwd.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    tile_plan_free(p);
+    return EC_ERR_CUDA;
+  }
+  ensure_attributes();
+  for (int v = 0; v < TILE_VARIANTS; ++v) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kVariants[v].fwd, kVariants[v].threads,
+                                                  kVariants[v].smem);
+    if (per_sm < 1) per_sm = 1;
+    p->grids[v] = (int)std::min<int64_t>(sms * per_sm, p->nunits);
+  }
+  p->variant = 0;
+  return EC_OK;
+}
+
+void tile_plan_free(TilePlan* p) {
+  if (p->units_fwd) cudaFree(p->units_fwd);
+  if (p->units_bwd) cudaFree(p->units_bwd);
+  *p = TilePlan{};
+}
+
+void tile_pack_lower(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
+                     double* Wp) {
+  const int64_t g = std::min<int64_t>(p.ntiles, (int64_t)num_sms() * 16);
+  pack_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, W, ldw, Wp);
+}
+
+void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, double* W,
+                       int64_t ldw) {
+  cudaMemset2DAsync(W, sizeof(double) * ldw, 0, sizeof(double) * p.n, p.n, s);
+  const int64_t g = std::min<int64_t>(p.ntiles, (int64_t)num_sms() * 16);
+  unpack_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, Wp, W, ldw);
+}
+
+void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out) {
+  tile_sum_kernel<<<(unsigned)p.nblk, TB * SUM_G, 0, ::ec::counted(s)>>>(p.n, p.nblk, p.npad,
+                                                                        p.chunk, trans, part, out);
+}
+
+void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const double* b,
+                    double* part1, double* y, double* part2, double* x, DevStatus* st,
+                    cudaEvent_t* ev) {
+  ensure_attributes();
+  const Variant& v = kVariants[p.variant];
+  const int grid = p.grids[p.variant];
+  TileArgs a{p.n, p.nblk, p.npad, p.nunits, p.chunk, Wp, b, part1, p.units_fwd, st};
+  if (ev) cudaEventRecord(ev[0], s);
+  v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  if (ev) cudaEventRecord(ev[1], s);
+  tile_sum(s, p, 0, part1, y);
+  a.x = y;
+  a.part = part2;
+  a.units = p.units_bwd;
+  v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  if (ev) cudaEventRecord(ev[2], s);
+  tile_sum(s, p, 1, part2, x);
+}
+
+ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const double* b,
+                        double* part1, double* y, double* part2, DevStatus* st, int forced) {
+  if (forced >= 1 && forced <= TILE_VARIANTS) {
+    p->variant = forced - 1;
+    return EC_OK;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return EC_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return EC_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int best_v = 0;
+  for (int v = 0; v < TILE_VARIANTS; ++v) {
+    p->variant = v;
+    tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);   // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      break;
+    p->tune_ms[v] = ms / 3.f;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->variant = best_v;
+  return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+
+}  // namespace ec

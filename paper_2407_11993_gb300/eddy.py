@@ -39,7 +39,7 @@ class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
                 ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int),
-                ("rhs_mode", c_int)]
+                ("rhs_mode", c_int), ("tile_variant", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -48,10 +48,13 @@ class ec_timing(ctypes.Structure):
                 ("project_ms", c_double), ("setup_ms", c_double), ("run_ms", c_double),
                 ("run_steps", c_int64), ("fwd_ms", c_double), ("bwd_ms", c_double),
                 ("scan_ms", c_double), ("fwd_launches", c_int64), ("bwd_launches", c_int64),
-                ("scan_launches", c_int64)]
+                ("scan_launches", c_int64), ("tile_variant", c_int64),
+                ("tile_tune_ms", c_double * 4)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["tile_tune_ms"] = list(d["tile_tune_ms"])
+        return d
 
 
 class EcError(RuntimeError):
@@ -203,7 +206,7 @@ class ThetaMethod:
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
-                 integrator: str = "theta", rhs: str = "sum"):
+                 integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
@@ -212,12 +215,14 @@ class ThetaMethod:
             raise ValueError("integrator must be 'theta' or 'exact'")
         if rhs not in ("sum", "independent", "paired"):
             raise ValueError("rhs must be 'sum', 'independent' or 'paired'")
+        if not 0 <= int(tile_variant) <= 3:
+            raise ValueError("tile_variant must be 0 (autotune) or 1 .. 3")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
                         _PREC[precision], 1 if integrator == "exact" else 0,
-                        {"sum": 0, "independent": 1, "paired": 2}[rhs])
+                        {"sum": 0, "independent": 1, "paired": 2}[rhs], int(tile_variant))
         self.rhs = rhs
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
