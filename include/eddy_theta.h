@@ -191,6 +191,32 @@ EC_API ec_status ec_set_step(ec_ctx* ctx, double theta, double dt);
 EC_API ec_status ec_run(ec_ctx* ctx, int64_t T, const double* src, const double* iD,
                         double* probes, int64_t snap_stride, double* snaps, int mem);
 
+/* Batched instances (spec batching; no counterpart in the paper, which runs one
+ * problem).  Advances `count` independent plain-form problems of different sizes by T
+ * steps each, as if ec_run were called on each (same arguments per instance, one common
+ * snap_stride), in one pass per step:
+ *   - every instance's tile products go into one work list (all instances' units,
+ *     largest first) run by one persistent grid; right-hand sides, partial sums and
+ *     updates are one launch each over all instances;
+ *   - one step of all instances is captured once into a CUDA graph and replayed T times;
+ *   - the launch shape of the products is timed on the batch before the run.
+ * Each instance computes exactly what its own ec_run computes (bitwise): the instances
+ * keep their own factors, work decomposition and reduction order.
+ *   ctxs       count distinct contexts, 1 <= count <= EC_BATCH_MAX, all set up, all on
+ *              one device, all EC_FORM_PLAIN with EC_SOLVE_INVERSE and EC_RHS_SUM
+ *              (else EC_ERR_UNSUPPORTED)
+ *   src, iD    arrays of count pointers (entry i as ec_run's src / iD of instance i; the
+ *              array may be NULL when no instance needs it)
+ *   probes, snaps   arrays of count output pointers (entries may be NULL)
+ *   mem        memory space of every data pointer (the pointer arrays are host arrays)
+ * Blocking: returns after the outputs are written.  The run uses its own stream, after
+ * synchronising every instance's stream.  ec_timings(ctx) of each instance reports the
+ * batch's run time. */
+#define EC_BATCH_MAX 64
+EC_API ec_status ec_batch_run(ec_ctx* const* ctxs, int count, int64_t T, const double* const* src,
+                              const double* const* iD, double* const* probes, int64_t snap_stride,
+                              double* const* snaps, int mem);
+
 /* Set the state from a physical current I (length n): I_i = K^T I (the particular
  * part is rebuilt from i_D at the next step). */
 EC_API ec_status ec_set_current(ec_ctx* ctx, const double* I, int mem);

@@ -1,6 +1,7 @@
 // C ABI of the theta-method library (include/eddy_theta.h): context, setup
 // and run orchestration for the plain and modal forms.
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -210,7 +211,7 @@ StepArgs step_args(ec_ctx* c, int64_t T, double* probes, double* snaps, int64_t 
   a.src = c->dSrc; a.iD = c->dIDs; a.T = T; a.kstep = c->dK;
   a.V = c->dV; a.WR = c->dWR; a.Tm = c->dT; a.VtWR = c->dVtWR; a.PE = c->dPE; a.CPE = c->dCPE;
   a.R = c->csr; a.Gsrc = c->dGsrc; a.Dmat = c->dDmat; a.Ii = c->dIi; a.work = c->dWork;
-  a.dots = c->dDots; a.partial = c->dPartial; a.counter = c->dCounter;
+  a.dots = c->dDots; a.partial = c->dPartial; a.counter = c->dCounter; a.ugrid = c->update_grid;
   a.probes = probes; a.snaps = snaps; a.snap_stride = stride;
   a.tickets = c->dTickets; a.epoch = c->dEpoch; a.st = c->st;
   return a;
@@ -640,6 +641,149 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
   if (outP && outP != probes) EC_TRY(copy_out(c, probes, outP, (size_t)T * nt * pout, mem));
   if (outS && outS != snaps) EC_TRY(copy_out(c, snaps, outS, (size_t)nsnap * nt * n, mem));
   return collect(c);
+}
+
+ec_status ec_batch_run(ec_ctx* const* ctxs, int count, int64_t T, const double* const* src,
+                       const double* const* iD, double* const* probes, int64_t stride,
+                       double* const* snaps, int mem) {
+  if (!ctxs || count < 1 || count > EC_BATCH_MAX || T < 0 || stride < 0) return EC_ERR_ARG;
+  if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    const ec_ctx* c = ctxs[i];
+    if (!c) return EC_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return EC_ERR_ARG;
+    if (!c->ready) return EC_ERR_STATE;
+    if (c->cfg.form != EC_FORM_PLAIN || c->cfg.plain_solver != EC_SOLVE_INVERSE ||
+        c->cfg.rhs_mode != EC_RHS_SUM)
+      return EC_ERR_UNSUPPORTED;
+    if (c->cfg.device != ctxs[0]->cfg.device) return EC_ERR_ARG;
+    if ((c->S > 0 && (!src || !src[i])) || (c->m > 0 && (!iD || !iD[i]))) return EC_ERR_ARG;
+  }
+  if (T == 0) return EC_OK;
+  cudaSetDevice(ctxs[0]->cfg.device);
+  // Earlier work of every instance completes before the batch starts.
+  for (int i = 0; i < count; ++i)
+    if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return EC_ERR_CUDA;
+
+  std::vector<StepArgs> args(count);
+  std::vector<TileInst> inst(count);
+  std::vector<double*> outP(count, nullptr), outS(count, nullptr);
+  int64_t max_n0 = 0, max_n = 0;
+  int max_ugrid = 1;
+  bool any_snaps = false;
+  for (int i = 0; i < count; ++i) {
+    ec_ctx* c = ctxs[i];
+    const int64_t nsnap = (stride > 0 && snaps && snaps[i]) ? T / stride : 0;
+    EC_TRY(grow(&c->dSrc, c->srcCap, (size_t)(c->S > 0 ? c->S : 1) * (T + 1)));
+    EC_TRY(grow(&c->dIDs, c->idsCap, (size_t)(c->m > 0 ? c->m : 1) * (T + 1)));
+    EC_TRY(copy_in(c, c->dSrc, c->S > 0 ? src[i] : nullptr, (size_t)c->S * (T + 1), mem));
+    EC_TRY(copy_in(c, c->dIDs, c->m > 0 ? iD[i] : nullptr, (size_t)c->m * (T + 1), mem));
+    if (probes && probes[i] && c->P > 0) {
+      if (mem == EC_MEM_DEVICE) outP[i] = probes[i];
+      else {
+        EC_TRY(grow(&c->dProbes, c->probesCap, (size_t)T * c->P));
+        outP[i] = c->dProbes;
+      }
+    }
+    if (nsnap > 0) {
+      if (mem == EC_MEM_DEVICE) outS[i] = snaps[i];
+      else {
+        EC_TRY(grow(&c->dSnaps, c->snapsCap, (size_t)nsnap * c->n));
+        outS[i] = c->dSnaps;
+      }
+      any_snaps = true;
+    }
+    cudaMemsetAsync(c->dK, 0, sizeof(int64_t), c->stream);
+    args[i] = step_args(c, T, outP[i], outS[i], nsnap > 0 ? stride : 0);
+    inst[i] = TileInst{&c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2, c->dWork};
+    max_n0 = std::max(max_n0, c->n0);
+    max_n = std::max(max_n, c->n);
+    max_ugrid = std::max(max_ugrid, c->update_grid);
+  }
+  for (int i = 0; i < count; ++i)
+    if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return EC_ERR_CUDA;
+
+  cudaStream_t st = nullptr;
+  StepArgs* dA = nullptr;
+  DevStatus* bst = nullptr;
+  TileBatch B;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ec_status rc = EC_OK;
+  auto release = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    tile_batch_free(&B);
+    dfree(dA);
+    dfree(bst);
+    if (st) cudaStreamDestroy(st);
+  };
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return EC_ERR_CUDA;
+  if ((rc = alloc(&dA, (size_t)count)) || (rc = alloc(&bst, 1))) {
+    release();
+    return rc;
+  }
+  if (cudaMemcpy(dA, args.data(), sizeof(StepArgs) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(bst, 0, sizeof(DevStatus)) != cudaSuccess) {
+    release();
+    return EC_ERR_CUDA;
+  }
+  // One work list over every instance's tile units; launch shape tuned on the batch.
+  if ((rc = tile_batch_create(inst.data(), count, &B)) ||
+      (rc = tile_batch_autotune(st, &B, inst.data(), bst))) {
+    release();
+    return rc;
+  }
+  // One step of all instances, captured once and replayed T times.
+  const int64_t launches0 = ec::g_launches.load(std::memory_order_relaxed);
+  tile_prepare_launches();
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    release();
+    return EC_ERR_CUDA;
+  }
+  plain_rhs_batch(st, dA, count, max_n0);
+  tile_batch_pair(st, B, inst.data(), bst);
+  plain_update_batch(st, dA, count, max_ugrid);
+  if (any_snaps) plain_snapshot_batch(st, dA, count, max_n);
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  const int64_t per_step = ec::g_launches.load(std::memory_order_relaxed) - launches0;
+  if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return EC_ERR_CUDA;
+  }
+  EventTimer t(st);
+  for (int64_t k = 0; k < T; ++k)
+    if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+      rc = EC_ERR_CUDA;
+      break;
+    }
+  const double ms = t.stop_ms();
+  // the capture counted one step's launches; the replays ran T steps
+  ec::g_launches.fetch_add(per_step * (T - 1), std::memory_order_relaxed);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = EC_ERR_CUDA;
+  DevStatus h{};
+  if (rc == EC_OK && cudaMemcpy(&h, bst, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = EC_ERR_CUDA;
+  if (rc == EC_OK && h.code != 0) {
+    ctxs[0]->last_info = h.info;
+    rc = (ec_status)h.code;
+  }
+  for (int i = 0; i < count && rc == EC_OK; ++i) {
+    ec_ctx* c = ctxs[i];
+    c->tim.run_ms = ms;
+    c->tim.run_steps = T;
+    rc = collect(c);
+    const int64_t nsnap = outS[i] ? T / stride : 0;
+    if (rc == EC_OK && outP[i] && outP[i] != probes[i])
+      rc = copy_out(c, probes[i], outP[i], (size_t)T * c->P, mem);
+    if (rc == EC_OK && outS[i] && outS[i] != snaps[i])
+      rc = copy_out(c, snaps[i], outS[i], (size_t)nsnap * c->n, mem);
+    if (rc == EC_OK) rc = collect(c);
+  }
+  release();
+  return rc;
 }
 
 ec_status ec_get_state(ec_ctx* c, double* state, int mem) {

@@ -54,7 +54,8 @@ struct StepArgs {
   double* Ii;                  // n0 state (plain)
   double* work;                // n0 right-hand side / solution
   double* dots;                // D values for the current state
-  double* partial;             // grid x D partial sums
+  double* partial;             // ugrid x D partial sums
+  int ugrid;                   // CTAs of this instance's update (batched launches)
   unsigned* counter;           // last-block counter
   double* probes;              // T x P output (may be null)
   double* snaps;               // nsnap x n output (may be null)
@@ -67,6 +68,12 @@ struct StepArgs {
 void plain_rhs(cudaStream_t s, const StepArgs& a);
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode);  // mode 0: += work; 1: dots only
 void plain_snapshot(cudaStream_t s, const StepArgs& a);
+// Batched forms over `count` instances (dA: device array of their StepArgs): one
+// launch each, blockIdx.y = instance; each instance computes exactly what its own
+// launch computes (the update uses the instance's own ugrid).
+void plain_rhs_batch(cudaStream_t s, const StepArgs* dA, int count, int64_t max_n0);
+void plain_update_batch(cudaStream_t s, const StepArgs* dA, int count, int max_grid);
+void plain_snapshot_batch(cudaStream_t s, const StepArgs* dA, int count, int64_t max_n);
 // Independent right-hand sides (no electrodes): out (n0 x S) = -dt R I - M_0 diag(ds^k).
 void plain_rhs_multi(cudaStream_t s, const StepArgs& a, int64_t k, const double* I, double* out);
 // out[r] = C[:, r] . I[:, r]

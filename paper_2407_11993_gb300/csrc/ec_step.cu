@@ -63,10 +63,12 @@ __device__ __forceinline__ double ri_row(const StepArgs& a, int64_t i, const dou
   return s;
 }
 
-__global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
+// Body of the right-hand-side kernel for CTA bx of gx (batched launches pass the
+// instance's arguments and the CTA index within the instance).
+__device__ __forceinline__ void plain_rhs_body(const StepArgs& a, unsigned bx, unsigned gx) {
   __shared__ double alpha[MAXM], beta[MAXM], coef[2 * MAXM + 64];
   const int64_t k = *a.kstep;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) {
     a.tickets[0] = 0u;
     a.tickets[1] = 0u;
     *a.epoch = *a.epoch + 1;
@@ -84,12 +86,20 @@ __global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
       coef[2 * m + l] = -(src_at(a.src, a.T, l, k + 1) - src_at(a.src, a.T, l, k));
   }
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
+       i += (int64_t)gx * blockDim.x) {
     double b = -a.dt * ri_row(a, i, alpha, beta);
     for (int c = 0; c < ncoef; ++c) b = fma(coef[c], a.Gsrc[i + (int64_t)c * a.n0], b);
     a.work[i] = b;
   }
+}
+
+__global__ void __launch_bounds__(256) plain_rhs_kernel(StepArgs a) {
+  plain_rhs_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) plain_rhs_batch_kernel(const StepArgs* A) {
+  plain_rhs_body(A[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) ri_apply_kernel(StepArgs a, double* out) {
@@ -104,12 +114,13 @@ __global__ void __launch_bounds__(256) ri_apply_kernel(StepArgs a, double* out) 
 // I_i += dI (mode 0), then the D dot products of the new state: per-CTA partials
 // (each warp reduces its rows with shuffles, one barrier for all D), summed by the
 // last CTA with one warp per dot product (lanes stride over the CTA partials).
-__global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode) {
+__device__ __forceinline__ void plain_update_body(const StepArgs& a, int mode, unsigned bx,
+                                                  unsigned nb) {
   __shared__ double sh[8][MAXD];
   __shared__ bool last;
   const int64_t n0 = a.n0;
-  const int64_t chunk = (n0 + gridDim.x - 1) / gridDim.x;
-  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t chunk = (n0 + nb - 1) / nb;
+  const int64_t b0 = bx * chunk;
   const int64_t b1 = (b0 + chunk < n0) ? b0 + chunk : n0;
   if (mode == 0) {
     for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) a.Ii[i] += a.work[i];
@@ -141,13 +152,13 @@ __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode)
   for (int d = threadIdx.x; d < a.D; d += blockDim.x) {
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q][d];
-    a.partial[(int64_t)blockIdx.x * a.D + d] = t;
+    a.partial[(int64_t)bx * a.D + d] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(a.counter, 1u);
-    last = (prev == gridDim.x - 1);
+    last = (prev == nb - 1);
   }
   __syncthreads();
   if (!last) return;
@@ -155,7 +166,7 @@ __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode)
   const int64_t k = *a.kstep;   // this update produces state k + 1 (mode 0)
   for (int d = w; d < a.D; d += (int)(blockDim.x >> 5)) {
     double t = 0.0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) t += __ldcg(a.partial + (int64_t)b * a.D + d);
+    for (unsigned b = lane; b < nb; b += 32) t += __ldcg(a.partial + (int64_t)b * a.D + d);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) {
@@ -174,7 +185,19 @@ __global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode)
   }
 }
 
-__global__ void plain_snapshot_kernel(StepArgs a) {
+__global__ void __launch_bounds__(256) plain_update_kernel(StepArgs a, int mode) {
+  plain_update_body(a, mode, blockIdx.x, gridDim.x);
+}
+
+// blockIdx.y = instance; CTAs past the instance's own update grid leave at once,
+// so every instance reduces exactly as its own launch does.
+__global__ void __launch_bounds__(256) plain_update_batch_kernel(const StepArgs* A) {
+  const StepArgs& a = A[blockIdx.y];
+  if (blockIdx.x >= (unsigned)a.ugrid) return;
+  plain_update_body(a, 0, blockIdx.x, (unsigned)a.ugrid);
+}
+
+__device__ __forceinline__ void plain_snapshot_body(const StepArgs& a, unsigned bx, unsigned gx) {
   const int64_t k = *a.kstep;
   if (a.snap_stride <= 0 || a.snaps == nullptr || k == 0 || k % a.snap_stride != 0) return;
   const int64_t j = k / a.snap_stride - 1;
@@ -189,13 +212,19 @@ __global__ void plain_snapshot_kernel(StepArgs a) {
     }
   }
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gx * blockDim.x) {
     double v = (i >= m) ? a.Ii[i - m] : 0.0;
     for (int c = 0; c < m; ++c)
       v = fma(-a.V[i + (int64_t)c * a.n], Tp[c], fma(a.PE[i + (int64_t)c * a.n], iDk[c], v));
     a.snaps[j * a.n + i] = v;
   }
+}
+
+__global__ void plain_snapshot_kernel(StepArgs a) { plain_snapshot_body(a, blockIdx.x, gridDim.x); }
+
+__global__ void plain_snapshot_batch_kernel(const StepArgs* A) {
+  plain_snapshot_body(A[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 int rows_grid(int64_t n) {
@@ -267,6 +296,18 @@ void ri_apply(cudaStream_t s, const StepArgs& a, double* out) {
 
 void plain_snapshot(cudaStream_t s, const StepArgs& a) {
   plain_snapshot_kernel<<<rows_grid(a.n), 256, 0, ::ec::counted(s)>>>(a);
+}
+
+void plain_rhs_batch(cudaStream_t s, const StepArgs* dA, int count, int64_t max_n0) {
+  plain_rhs_batch_kernel<<<dim3(rows_grid(max_n0), count), 256, 0, ::ec::counted(s)>>>(dA);
+}
+
+void plain_update_batch(cudaStream_t s, const StepArgs* dA, int count, int max_grid) {
+  plain_update_batch_kernel<<<dim3(max_grid, count), 256, 0, ::ec::counted(s)>>>(dA);
+}
+
+void plain_snapshot_batch(cudaStream_t s, const StepArgs* dA, int count, int64_t max_n) {
+  plain_snapshot_batch_kernel<<<dim3(rows_grid(max_n), count), 256, 0, ::ec::counted(s)>>>(dA);
 }
 
 }  // namespace ec

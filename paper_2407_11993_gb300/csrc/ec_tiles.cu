@@ -42,8 +42,11 @@ constexpr long long WAIT_LIMIT = 1ll << 26;
 constexpr int CW = 8;   // consumer warps: 2 output halves x 4 quarters of the inner index
 constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
 
+// What the consumers need of a stage: where the unit's partial rows go.
 struct Meta {
-  int I, J, c, flags;
+  double* out;       // partial row 4c of the unit, offset to the unit's 64 outputs
+  int64_t npad;      // stride between partial rows
+  int flags;
 };
 
 template <int ST>
@@ -58,13 +61,20 @@ constexpr size_t smem_bytes() {
   return sizeof(Smem<ST>) + 128;   // + alignment slack
 }
 
-struct TileArgs {
-  int64_t n, nblk, npad, nunits;
-  int chunk;
-  const double* Wp;
+// One instance of the products (NI of them per launch, passed by value).
+struct TileDesc {
+  const double* Wp;    // packed tiles
   const double* x;     // input vector (npad, zero tail)
   double* part;        // partial rows x npad
-  const int2* units;
+  int64_t nblk, npad;
+  int chunk;
+};
+
+template <int NI>
+struct TileArgs {
+  TileDesc d[NI];
+  const int4* units;   // (instance, tile row / column, unit index within it, 0)
+  int64_t nunits;
   DevStatus* st;
 };
 
@@ -91,8 +101,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, DevSta
 
 // 8 consumer warps, ST ring stages, MINB CTAs per SM.  Every variant sums each
 // output entry in the same order, so all variants give bitwise identical results.
-template <bool TRANS, int ST, int MINB>
-__global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(TileArgs a) {
+template <bool TRANS, int ST, int MINB, int NI>
+__global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __grid_constant__ TileArgs<NI> a) {
   if (*(volatile const int*)&a.st->code) return;
   extern __shared__ uint8_t smem_raw[];
   Smem<ST>& sm = *reinterpret_cast<Smem<ST>*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -113,16 +123,18 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(TileArgs 
     int64_t it = 0;
     bool ok = true;
     for (int64_t u = blockIdx.x; u < a.nunits && ok; u += gridDim.x) {
-      const int2 un = a.units[u];
-      const int64_t K = un.x;                       // tile row (forward) / column (transposed)
+      const int4 un = a.units[u];
+      const TileDesc& d = a.d[NI == 1 ? 0 : un.x];
+      const int64_t K = un.y;                       // tile row (forward) / column (transposed)
       int64_t t0, t1;
       if (!TRANS) {
-        t0 = (int64_t)un.y * a.chunk;
-        t1 = min(t0 + a.chunk, K + 1);
+        t0 = (int64_t)un.z * d.chunk;
+        t1 = min(t0 + d.chunk, K + 1);
       } else {
-        t0 = K + (int64_t)un.y * a.chunk;
-        t1 = min(t0 + a.chunk, a.nblk);
+        t0 = K + (int64_t)un.z * d.chunk;
+        t1 = min(t0 + d.chunk, d.nblk);
       }
+      double* out = d.part + (int64_t)un.z * 4 * d.npad + K * TB;
       for (int64_t t = t0; t < t1; ++t) {
         const int s = (int)(it % ST);
         const uint32_t ph = (uint32_t)((it / ST) & 1);
@@ -131,10 +143,10 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(TileArgs 
           break;
         }
         const int64_t I = TRANS ? t : K, J = TRANS ? K : t;
-        sm.meta[s] = Meta{(int)I, (int)J, un.y, (t == t0 ? F_FIRST : 0) | (t == t1 - 1 ? F_LAST : 0)};
+        sm.meta[s] = Meta{out, d.npad, (t == t0 ? F_FIRST : 0) | (t == t1 - 1 ? F_LAST : 0)};
         dev::mbar_expect_tx(&sm.full[s], TILE_BYTES + SEG_BYTES);
-        dev::bulk_g2s_hint(sm.W[s], a.Wp + tile_index(I, J) * TILE_DBL, TILE_BYTES, &sm.full[s], pol);
-        dev::bulk_g2s(sm.v[s], a.x + (TRANS ? I : J) * TB, SEG_BYTES, &sm.full[s]);
+        dev::bulk_g2s_hint(sm.W[s], d.Wp + tile_index(I, J) * TILE_DBL, TILE_BYTES, &sm.full[s], pol);
+        dev::bulk_g2s(sm.v[s], d.x + t * TB, SEG_BYTES, &sm.full[s]);
         ++it;
       }
     }
@@ -199,9 +211,7 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(TileArgs 
     __syncwarp();
     if (lane == 0) dev::mbar_arrive(&sm.empty[s]);
     if (m.flags & F_LAST) {
-      const double t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-      const int64_t blk = TRANS ? m.J : m.I;
-      a.part[((int64_t)m.c * 4 + q) * a.npad + blk * TB + o] = t;
+      m.out[q * m.npad + o] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
   }
 }
@@ -241,24 +251,39 @@ __global__ void unpack_kernel(int64_t n, int64_t ntiles, const double* Wp, doubl
 // g, g + SUM_G, ... with two independent accumulators (so loads stay in flight),
 // then the thread rows are combined in a fixed order.  The partials were just
 // written and sit in L2; the kernel is latency-bound, hence the wide blocks.
+// blockIdx.y selects the instance of a batched launch.
 constexpr int SUM_G = 16;
 
-__global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(int64_t n, int64_t nblk,
-                                                            int64_t npad, int chunk, int trans,
-                                                            const double* part, double* out) {
+struct SumDesc {
+  const double* part;
+  double* out;
+  int64_t n, nblk, npad;
+  int chunk;
+};
+
+template <int NI>
+struct SumArgs {
+  SumDesc d[NI];
+  int trans;
+};
+
+template <int NI>
+__global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(const __grid_constant__ SumArgs<NI> a) {
   __shared__ double red[SUM_G][TB];
+  const SumDesc& d = a.d[NI == 1 ? 0 : blockIdx.y];
+  if ((int64_t)blockIdx.x >= d.nblk) return;
   const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
   const int64_t i = (int64_t)blockIdx.x * TB + tx;
   double s0 = 0.0, s1 = 0.0;
-  if (i < n) {
-    const int64_t nc = trans ? tile_valid_rows_t(i, nblk, chunk) : tile_valid_rows(i, chunk);
-    const double* p = part + i;
+  if (i < d.n) {
+    const int64_t nc = a.trans ? tile_valid_rows_t(i, d.nblk, d.chunk) : tile_valid_rows(i, d.chunk);
+    const double* p = d.part + i;
     int64_t r = g;
     for (; r + SUM_G < nc; r += 2 * SUM_G) {
-      s0 += p[r * npad];
-      s1 += p[(r + SUM_G) * npad];
+      s0 += p[r * d.npad];
+      s1 += p[(r + SUM_G) * d.npad];
     }
-    if (r < nc) s0 += p[r * npad];
+    if (r < nc) s0 += p[r * d.npad];
   }
   red[g][tx] = s0 + s1;
   __syncthreads();
@@ -267,36 +292,105 @@ __global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(int64_t n, int64_t
     if (g < h) red[g][tx] += red[g + h][tx];
     __syncthreads();
   }
-  if (g == 0 && i < n) out[i] = red[0][tx];
+  if (g == 0 && i < d.n) d.out[i] = red[0][tx];
 }
 
+template <int NI>
 struct Variant {
-  void (*fwd)(TileArgs);
-  void (*bwd)(TileArgs);
+  void (*fwd)(TileArgs<NI>);
+  void (*bwd)(TileArgs<NI>);
   int threads;
   size_t smem;
 };
 
 // Launch shapes the autotuner chooses from: (ring stages, CTAs per SM).
-const Variant kVariants[TILE_VARIANTS] = {
-    {tile_trmv_kernel<false, 4, 1>, tile_trmv_kernel<true, 4, 1>, CW * 32 + 32, smem_bytes<4>()},
-    {tile_trmv_kernel<false, 3, 2>, tile_trmv_kernel<true, 3, 2>, CW * 32 + 32, smem_bytes<3>()},
-    {tile_trmv_kernel<false, 6, 1>, tile_trmv_kernel<true, 6, 1>, CW * 32 + 32, smem_bytes<6>()},
-};
+template <int NI>
+const Variant<NI>* variants() {
+  static const Variant<NI> v[TILE_VARIANTS] = {
+      {tile_trmv_kernel<false, 4, 1, NI>, tile_trmv_kernel<true, 4, 1, NI>, CW * 32 + 32, smem_bytes<4>()},
+      {tile_trmv_kernel<false, 3, 2, NI>, tile_trmv_kernel<true, 3, 2, NI>, CW * 32 + 32, smem_bytes<3>()},
+      {tile_trmv_kernel<false, 6, 1, NI>, tile_trmv_kernel<true, 6, 1, NI>, CW * 32 + 32, smem_bytes<6>()},
+  };
+  return v;
+}
 
 std::mutex g_attr_mu;
 bool g_attr_done[64] = {};
 
-void ensure_attributes() {
+template <int NI>
+void set_attributes() {
+  for (int i = 0; i < TILE_VARIANTS; ++i) {
+    const Variant<NI>& v = variants<NI>()[i];
+    cudaFuncSetAttribute(v.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    cudaFuncSetAttribute(v.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+  }
+}
+
+}  // namespace
+
+void tile_prepare_launches() {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (dev < 0 || dev >= 64 || g_attr_done[dev]) return;
-  for (const Variant& v : kVariants) {
-    cudaFuncSetAttribute(v.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
-    cudaFuncSetAttribute(v.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
-  }
+  set_attributes<1>();
+  set_attributes<TILE_BATCH_MAX>();
   g_attr_done[dev] = true;
+}
+
+namespace {
+
+// Units of one instance: forward (row K, run c) and transposed (column K, run c).
+void instance_units(int inst, int64_t nblk, int64_t chunk, std::vector<int4>& fwd,
+                    std::vector<int4>& bwd) {
+  for (int64_t K = 0; K < nblk; ++K) {
+    for (int64_t c = 0; c < K / chunk + 1; ++c) fwd.push_back(make_int4(inst, (int)K, (int)c, 0));
+    for (int64_t c = 0; c < (nblk - 1 - K) / chunk + 1; ++c)
+      bwd.push_back(make_int4(inst, (int)K, (int)c, 0));
+  }
+}
+
+// Largest unit first (ties: instance, row, run), so round-robin dealing balances.
+void order_units(std::vector<int4>& u, const std::vector<int64_t>& nblk,
+                 const std::vector<int64_t>& chunk, bool trans) {
+  auto size = [&](const int4& x) {
+    const int64_t ch = chunk[x.x];
+    if (!trans) return std::min<int64_t>((int64_t)x.z * ch + ch, (int64_t)x.y + 1) - (int64_t)x.z * ch;
+    const int64_t t0 = (int64_t)x.y + (int64_t)x.z * ch;
+    return std::min<int64_t>(t0 + ch, nblk[x.x]) - t0;
+  };
+  std::stable_sort(u.begin(), u.end(), [&](const int4& a, const int4& b) {
+    const int64_t sa = size(a), sb = size(b);
+    if (sa != sb) return sa > sb;
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+}
+
+ec_status upload_units(const std::vector<int4>& fwd, const std::vector<int4>& bwd, int4** dfwd,
+                       int4** dbwd) {
+  if (cudaMalloc((void**)dfwd, sizeof(int4) * fwd.size()) != cudaSuccess ||
+      cudaMalloc((void**)dbwd, sizeof(int4) * bwd.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return EC_ERR_OOM;
+  }
+  if (cudaMemcpy(*dfwd, fwd.data(), sizeof(int4) * fwd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(*dbwd, bwd.data(), sizeof(int4) * bwd.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return EC_ERR_CUDA;
+  return EC_OK;
+}
+
+template <int NI>
+void grids_for(int64_t nunits, int* grids) {
+  const int64_t sms = num_sms();
+  for (int v = 0; v < TILE_VARIANTS; ++v) {
+    int per_sm = 0;
+    const Variant<NI>& var = variants<NI>()[v];
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, var.fwd, var.threads, var.smem);
+    if (per_sm < 1) per_sm = 1;
+    grids[v] = (int)std::max<int64_t>(1, std::min<int64_t>(sms * per_sm, nunits));
+  }
 }
 
 }  // namespace
@@ -308,55 +402,19 @@ ec_status tile_plan_create(int64_t n, TilePlan* p) {
   p->npad = p->nblk * TB;
   p->ntiles = p->nblk * (p->nblk + 1) / 2;
   const int64_t sms = num_sms();
-  int64_t chunk = p->ntiles / (sms * 16);
-  p->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, chunk));
-  std::vector<int2> fwd, bwd;
-  for (int64_t K = 0; K < p->nblk; ++K) {
-    const int64_t nf = K / p->chunk + 1;                          // tiles 0..K of row K
-    for (int64_t c = 0; c < nf; ++c) fwd.push_back(make_int2((int)K, (int)c));
-    const int64_t nbk = (p->nblk - 1 - K) / p->chunk + 1;         // tiles K..nblk-1 of column K
-    for (int64_t c = 0; c < nbk; ++c) bwd.push_back(make_int2((int)K, (int)c));
-  }
-  const int64_t nblk = p->nblk, ch = p->chunk;
-  auto size_f = [&](const int2& u) {
-    return std::min<int64_t>((int64_t)u.y * ch + ch, (int64_t)u.x + 1) - (int64_t)u.y * ch;
-  };
-  auto size_b = [&](const int2& u) {
-    const int64_t t0 = (int64_t)u.x + (int64_t)u.y * ch;
-    return std::min<int64_t>(t0 + ch, nblk) - t0;
-  };
-  auto order = [](auto size) {
-    return [size](const int2& a, const int2& b) {
-      const int64_t sa = size(a), sb = size(b);
-      if (sa != sb) return sa > sb;
-      if (a.x != b.x) return a.x < b.x;
-      return a.y < b.y;
-    };
-  };
-  std::stable_sort(fwd.begin(), fwd.end(), order(size_f));
-  std::stable_sort(bwd.begin(), bwd.end(), order(size_b));
+  p->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(64, p->ntiles / (sms * 16)));
+  std::vector<int4> fwd, bwd;
+  instance_units(0, p->nblk, p->chunk, fwd, bwd);
+  order_units(fwd, {p->nblk}, {(int64_t)p->chunk}, false);
+  order_units(bwd, {p->nblk}, {(int64_t)p->chunk}, true);
   p->nunits = (int64_t)fwd.size();
-  if (cudaMalloc((void**)&p->units_fwd, sizeof(int2) * fwd.size()) != cudaSuccess ||
-      cudaMalloc((void**)&p->units_bwd, sizeof(int2) * bwd.size()) != cudaSuccess) {
-    cudaGetLastError();
+  ec_status rc = upload_units(fwd, bwd, &p->units_fwd, &p->units_bwd);
+  if (rc != EC_OK) {
     tile_plan_free(p);
-    return EC_ERR_OOM;
+    return rc;
   }
-  if (cudaMemcpy(p->units_fwd, fwd.data(), sizeof(int2) * fwd.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(p->units_bwd, bwd.data(), sizeof(int2) * bwd.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
-    tile_plan_free(p);
-    return EC_ERR_CUDA;
-  }
-  ensure_attributes();
-  for (int v = 0; v < TILE_VARIANTS; ++v) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kVariants[v].fwd, kVariants[v].threads,
-                                                  kVariants[v].smem);
-    if (per_sm < 1) per_sm = 1;
-    p->grids[v] = (int)std::min<int64_t>(sms * per_sm, p->nunits);
-  }
+  tile_prepare_launches();
+  grids_for<1>(p->nunits, p->grids);
   p->variant = 0;
   return EC_OK;
 }
@@ -381,35 +439,40 @@ void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, doub
 }
 
 void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out) {
-  tile_sum_kernel<<<(unsigned)p.nblk, TB * SUM_G, 0, ::ec::counted(s)>>>(p.n, p.nblk, p.npad,
-                                                                        p.chunk, trans, part, out);
+  SumArgs<1> a{};
+  a.d[0] = SumDesc{part, out, p.n, p.nblk, p.npad, p.chunk};
+  a.trans = trans;
+  tile_sum_kernel<1><<<(unsigned)p.nblk, TB * SUM_G, 0, ::ec::counted(s)>>>(a);
 }
 
 void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const double* b,
                     double* part1, double* y, double* part2, double* x, DevStatus* st,
                     cudaEvent_t* ev) {
-  ensure_attributes();
-  const Variant& v = kVariants[p.variant];
+  tile_prepare_launches();
+  const Variant<1>& v = variants<1>()[p.variant];
   const int grid = p.grids[p.variant];
-  TileArgs a{p.n, p.nblk, p.npad, p.nunits, p.chunk, Wp, b, part1, p.units_fwd, st};
+  TileArgs<1> a{};
+  a.d[0] = TileDesc{Wp, b, part1, p.nblk, p.npad, p.chunk};
+  a.units = p.units_fwd;
+  a.nunits = p.nunits;
+  a.st = st;
   if (ev) cudaEventRecord(ev[0], s);
   v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[1], s);
   tile_sum(s, p, 0, part1, y);
-  a.x = y;
-  a.part = part2;
+  a.d[0] = TileDesc{Wp, y, part2, p.nblk, p.npad, p.chunk};
   a.units = p.units_bwd;
   v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[2], s);
   tile_sum(s, p, 1, part2, x);
 }
 
-ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const double* b,
-                        double* part1, double* y, double* part2, DevStatus* st, int forced) {
-  if (forced >= 1 && forced <= TILE_VARIANTS) {
-    p->variant = forced - 1;
-    return EC_OK;
-  }
+namespace {
+
+// Times every launch shape (one warm-up and three timed runs of `run` each) and
+// returns the fastest; `run(v)` enqueues one product pair with shape v.
+template <typename F>
+ec_status autotune_shapes(cudaStream_t s, F run, int* best_out, float* tune_ms) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return EC_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -419,15 +482,14 @@ ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const dou
   float best = 1e30f;
   int best_v = 0;
   for (int v = 0; v < TILE_VARIANTS; ++v) {
-    p->variant = v;
-    tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);   // warm-up
+    run(v);
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 3; ++r) tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);
+    for (int r = 0; r < 3; ++r) run(v);
     cudaEventRecord(e1, s);
     float ms = 0.f;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
       break;
-    p->tune_ms[v] = ms / 3.f;
+    tune_ms[v] = ms / 3.f;
     if (ms < best) {
       best = ms;
       best_v = v;
@@ -435,8 +497,106 @@ ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const dou
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  p->variant = best_v;
+  *best_out = best_v;
   return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+
+}  // namespace
+
+ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const double* b,
+                        double* part1, double* y, double* part2, DevStatus* st, int forced) {
+  if (forced >= 1 && forced <= TILE_VARIANTS) {
+    p->variant = forced - 1;
+    return EC_OK;
+  }
+  int best = 0;
+  ec_status rc = autotune_shapes(
+      s,
+      [&](int v) {
+        p->variant = v;
+        tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);
+      },
+      &best, p->tune_ms);
+  p->variant = best;
+  return rc;
+}
+
+// ---- batches of instances ---------------------------------------------------
+
+ec_status tile_batch_create(const TileInst* inst, int count, TileBatch* B) {
+  tile_batch_free(B);
+  if (count < 1 || count > TILE_BATCH_MAX) return EC_ERR_ARG;
+  std::vector<int4> fwd, bwd;
+  std::vector<int64_t> nblk(count), chunk(count);
+  for (int i = 0; i < count; ++i) {
+    nblk[i] = inst[i].plan->nblk;
+    chunk[i] = inst[i].plan->chunk;
+    instance_units(i, nblk[i], chunk[i], fwd, bwd);
+    B->max_nblk = std::max(B->max_nblk, nblk[i]);
+  }
+  order_units(fwd, nblk, chunk, false);
+  order_units(bwd, nblk, chunk, true);
+  B->count = count;
+  B->nunits_fwd = (int64_t)fwd.size();
+  B->nunits_bwd = (int64_t)bwd.size();
+  ec_status rc = upload_units(fwd, bwd, &B->units_fwd, &B->units_bwd);
+  if (rc != EC_OK) {
+    tile_batch_free(B);
+    return rc;
+  }
+  tile_prepare_launches();
+  grids_for<TILE_BATCH_MAX>(std::min(B->nunits_fwd, B->nunits_bwd), B->grids);
+  B->variant = 0;
+  return EC_OK;
+}
+
+void tile_batch_free(TileBatch* B) {
+  if (B->units_fwd) cudaFree(B->units_fwd);
+  if (B->units_bwd) cudaFree(B->units_bwd);
+  *B = TileBatch{};
+}
+
+void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, DevStatus* st) {
+  const Variant<TILE_BATCH_MAX>& v = variants<TILE_BATCH_MAX>()[B.variant];
+  const int grid = B.grids[B.variant];
+  TileArgs<TILE_BATCH_MAX> a{};
+  SumArgs<TILE_BATCH_MAX> sa{};
+  for (int i = 0; i < B.count; ++i) {
+    const TilePlan& p = *inst[i].plan;
+    a.d[i] = TileDesc{inst[i].Wp, inst[i].b, inst[i].part1, p.nblk, p.npad, p.chunk};
+    sa.d[i] = SumDesc{inst[i].part1, inst[i].y, p.n, p.nblk, p.npad, p.chunk};
+  }
+  a.units = B.units_fwd;
+  a.nunits = B.nunits_fwd;
+  a.st = st;
+  v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  sa.trans = 0;
+  tile_sum_kernel<TILE_BATCH_MAX><<<dim3((unsigned)B.max_nblk, (unsigned)B.count), TB * SUM_G, 0,
+                                    ::ec::counted(s)>>>(sa);
+  for (int i = 0; i < B.count; ++i) {
+    const TilePlan& p = *inst[i].plan;
+    a.d[i] = TileDesc{inst[i].Wp, inst[i].y, inst[i].part2, p.nblk, p.npad, p.chunk};
+    sa.d[i] = SumDesc{inst[i].part2, inst[i].x, p.n, p.nblk, p.npad, p.chunk};
+  }
+  a.units = B.units_bwd;
+  a.nunits = B.nunits_bwd;
+  v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  sa.trans = 1;
+  tile_sum_kernel<TILE_BATCH_MAX><<<dim3((unsigned)B.max_nblk, (unsigned)B.count), TB * SUM_G, 0,
+                                    ::ec::counted(s)>>>(sa);
+}
+
+ec_status tile_batch_autotune(cudaStream_t s, TileBatch* B, const TileInst* inst, DevStatus* st) {
+  int best = 0;
+  ec_status rc = autotune_shapes(
+      s,
+      [&](int v) {
+        B->variant = v;
+        tile_batch_pair(s, *B, inst, st);
+      },
+      &best, B->tune_ms);
+  B->variant = best;
+  return rc;
 }
 
 }  // namespace ec

@@ -24,8 +24,8 @@ struct TilePlan {
   int variant = 0;              // launch shape in use (index into the variant table)
   int grids[TILE_VARIANTS] = {};   // CTAs per launch of each shape
   float tune_ms[TILE_VARIANTS] = {};   // autotuner: time of one product pair per shape
-  int2* units_fwd = nullptr;    // device, nunits entries (I, c), largest first
-  int2* units_bwd = nullptr;    // device, nunits entries (J, c)
+  int4* units_fwd = nullptr;    // device, nunits entries (0, I, c, 0), largest first
+  int4* units_bwd = nullptr;    // device, nunits entries (0, J, c, 0)
 };
 
 ec_status tile_plan_create(int64_t n, TilePlan* p);
@@ -60,6 +60,44 @@ ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const dou
 // out[i] = sum over the partial rows unit products wrote for row i, in row order
 // (trans = 0: partials of W b; trans = 1: partials of W^T y).
 void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out);
+
+// ---- batches: the products of up to TILE_BATCH_MAX instances in one launch ----
+// Every instance keeps its own plan (tiles, unit decomposition, partial rows), so
+// a batched product computes bit for bit what the instance's own launch computes;
+// the batch merges all instances' units into one largest-first list dealt to one
+// persistent grid.
+constexpr int TILE_BATCH_MAX = 64;
+
+struct TileInst {
+  const TilePlan* plan;
+  const double* Wp;
+  const double* b;     // input (npad, zero tail)
+  double* part1;
+  double* y;           // W b (npad, zero tail)
+  double* part2;
+  double* x;           // W^T y
+};
+
+struct TileBatch {
+  int count = 0;
+  int64_t max_nblk = 0, nunits_fwd = 0, nunits_bwd = 0;
+  int4* units_fwd = nullptr;    // device, (instance, K, c, 0), largest first
+  int4* units_bwd = nullptr;
+  int variant = 0;
+  int grids[TILE_VARIANTS] = {};
+  float tune_ms[TILE_VARIANTS] = {};
+};
+
+ec_status tile_batch_create(const TileInst* inst, int count, TileBatch* B);
+void tile_batch_free(TileBatch* B);
+// x_i = W_i^T (W_i b_i) for every instance: 4 launches in all.
+void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, DevStatus* st);
+// Chooses B->variant by timing every launch shape on the batch (synchronises s).
+ec_status tile_batch_autotune(cudaStream_t s, TileBatch* B, const TileInst* inst, DevStatus* st);
+
+// Sets the shared-memory attributes of every product kernel on the current device
+// (idempotent; call once before capturing launches into a graph).
+void tile_prepare_launches();
 
 // Number of partial rows holding data for output i of the forward / transposed
 // product (they are the first rows of the partial array).

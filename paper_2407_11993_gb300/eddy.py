@@ -31,7 +31,7 @@ EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
            "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
-           "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors")
+           "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors", "ec_batch_run")
 NOALLOC_MAX_N = 8192
 
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
             "ec_gemm_bf16": (c_int, [c_int64, c_int64, c_int64, P, P, P, P]),
             "ec_set_mode_count": (c_int, [P, c_int64]),
             "ec_phasors": (c_int, [c_int64, c_int64, P, c_double, c_double, c_int64, P, P, c_int]),
+            "ec_batch_run": (c_int, [P, c_int, c_int64, P, P, P, c_int64, P, c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -362,3 +363,38 @@ class ThetaMethod:
 
     def sync(self) -> None:
         check(lib().ec_sync(self._h), "ec_sync", self._h)
+
+
+EC_BATCH_MAX = 64
+
+
+def batch_run(models, T: int, srcs=None, iDs=None, snap_stride: int = 0):
+    """ec_batch_run on host arrays: advance every plain-form ThetaMethod in ``models``
+    by T steps in one batched, graph-captured pass.
+
+    ``srcs[i]`` / ``iDs[i]`` are model i's src / iD as for ``run`` (None where the model
+    has no coils / electrodes).  Returns a list of (probes (P, T), snaps (N, nsnap)).
+    """
+    count = len(models)
+    if not 1 <= count <= EC_BATCH_MAX:
+        raise ValueError(f"batch of 1 .. {EC_BATCH_MAX} models")
+    keep = []
+    nsnap = T // snap_stride if snap_stride else 0
+    Handles = c_void_p * count
+    Ptrs = c_void_p * count
+    hs = Handles(*[m._h for m in models])
+    ps, pi, pp, pn = Ptrs(), Ptrs(), Ptrs(), Ptrs()
+    outs = []
+    for i, m in enumerate(models):
+        s = srcs[i] if (srcs is not None and m.S) else None
+        d = iDs[i] if (iDs is not None and m.m) else None
+        a, k = _ptr(s, EC_MEM_HOST); keep.append(k); ps[i] = a
+        a, k = _ptr(d, EC_MEM_HOST); keep.append(k); pi[i] = a
+        probes = np.empty((T, m.P))
+        snaps = np.empty((nsnap, m.n))
+        pp[i] = c_void_p(probes.ctypes.data) if m.P else None
+        pn[i] = c_void_p(snaps.ctypes.data) if nsnap else None
+        outs.append((probes, snaps))
+    check(lib().ec_batch_run(hs, count, int(T), ps, pi, pp, int(snap_stride) if nsnap else 0, pn,
+                             EC_MEM_HOST), "ec_batch_run", models[0]._h)
+    return [(p.T, s.T) for p, s in outs]
