@@ -2,6 +2,7 @@
 
     python -m paper_2407_11993_gb300.profile_cases --form plain --n 8192 --T 5
     python -m paper_2407_11993_gb300.profile_cases --form modal --n 4096 --T 100
+    python -m paper_2407_11993_gb300.profile_cases --batch 64 --nmin 1024 --nmax 12288 --T 200
 
 Builds a seeded synthetic problem (plate grid, one electrode row, one coil,
 16 pickups), runs setup and T steps through the C ABI on cuda:0 and prints the
@@ -20,6 +21,54 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def batch_case(args) -> dict:
+    """Uneven plain-form instances (N uniform in [nmin, nmax], seeds 0..batch-1, one coil,
+    4 pickups): total setup, T steps of all instances through ec_batch_run, and the same T
+    steps run instance by instance through ec_run for comparison."""
+    import time
+
+    import numpy as np
+
+    from paper_2407_11993_gb300 import eddy
+    from workloads import synth
+
+    rng = np.random.default_rng(12345)
+    sizes = [int(x) for x in rng.integers(args.nmin, args.nmax + 1, size=args.batch)]
+    models, srcs = [], []
+    t_setup = 0.0
+    for i, n in enumerate(sizes):
+        p = synth.small(n, T=args.T, seed=i, electrodes=False, coil=True, probes=4, dt=1e-6)
+        tm = eddy.ThetaMethod("plain", p.theta, p.dt)
+        t0 = time.perf_counter()
+        tm.setup(p.L, p.R, None, p.M, None, p.C)
+        t_setup += time.perf_counter() - t0
+        models.append(tm)
+        srcs.append(p.src)
+        del p
+    state0 = [m.get_state() for m in models]
+    eddy.batch_run(models, 3, srcs, None)                  # warm-up (graph, autotune paths)
+    for m, s0 in zip(models, state0):
+        m.set_state(s0)
+    t0 = time.perf_counter()
+    outs = eddy.batch_run(models, args.T, srcs, None)
+    t_batch = time.perf_counter() - t0
+    batch_ms = models[0].timings()["run_ms"]
+    for m, s0 in zip(models, state0):
+        m.set_state(s0)
+    t0 = time.perf_counter()
+    single = [m.run(args.T, s, None, 0)[0] for m, s in zip(models, srcs)]
+    t_single = time.perf_counter() - t0
+    same = all(np.array_equal(a[0], b) for a, b in zip(outs, single))
+    fma_per_step = float(sum(n * (n + 1) for n in sizes))  # two triangular products per instance
+    return {"batch": args.batch, "sizes": sizes, "T": args.T, "setup_s_total": t_setup,
+            "batch_run_ms_device": batch_ms, "batch_run_s_wall": t_batch,
+            "sequential_run_s_wall": t_single,
+            "instance_steps_per_s_batch": args.batch * args.T / (batch_ms / 1e3),
+            "instance_steps_per_s_sequential": args.batch * args.T / t_single,
+            "batch_fp64_tflops": 2.0 * fma_per_step * args.T / (batch_ms / 1e3) / 1e12,
+            "batch_equals_sequential_bitwise": bool(same), "launches": eddy.launch_count()}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--form", choices=["plain", "modal"], default="plain")
@@ -27,12 +76,18 @@ def main() -> None:
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--T", type=int, default=10)
     ap.add_argument("--no-electrodes", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="uneven plain-form instances (ec_batch_run)")
+    ap.add_argument("--nmin", type=int, default=1024)
+    ap.add_argument("--nmax", type=int, default=12288)
     args = ap.parse_args()
 
     from paper_2407_11993_gb300 import build, eddy
     from workloads import synth
 
     build.build()
+    if args.batch:
+        print(json.dumps(batch_case(args)))
+        return
     p = synth.small(args.n, T=args.T, seed=1, electrodes=not args.no_electrodes, coil=True,
                     probes=16, dt=0.5e-6)
     tm = eddy.ThetaMethod(args.form, p.theta, p.dt, solver=args.solver, profile=True)
