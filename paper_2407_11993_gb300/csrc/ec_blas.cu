@@ -367,6 +367,24 @@ void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* 
   }
 }
 
+// Lower triangle of B Lf^{-T} for a square B (n x n) whose product is symmetric (the
+// two-sided reduction C^{-1} L C^{-T}): block column k needs only rows >= k, and the
+// trailing update only the lower triangle of the trailing block, a third of the
+// flops of the full solve.  The strict upper triangle is left stale.
+void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lf, int64_t ldl,
+                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+  for (int64_t k = 0; k < n; k += NB) {
+    const int kb = (int)((n - k) < NB ? (n - k) : NB);
+    const double* Dk = Dinv + (k / NB) * NB * NB;
+    double* Bk = B + k * ldb;
+    dgemm(s, N_, T_, n - k, kb, kb, 1.0, Bk + k, ldb, Dk, NB, 0.0, Bk + k, ldb, 0, st);
+    const int64_t rest = n - k - kb;
+    if (rest > 0)  // lower(B[k+kb:, k+kb:]) -= B[k+kb:, k:k+kb] L[k+kb:, k:k+kb]^T
+      dgemm(s, N_, T_, rest, rest, kb, -1.0, Bk + k + kb, ldb, Lf + (k + kb) + k * ldl, ldl, 1.0,
+            B + (k + kb) + (k + kb) * ldb, ldb, 1, st);
+  }
+}
+
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));

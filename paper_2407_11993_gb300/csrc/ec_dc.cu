@@ -157,6 +157,8 @@ __global__ void __launch_bounds__(256) deflate_kernel(int64_t n, int64_t bs, con
   w.nrot[z] = nrot;
 }
 
+constexpr int64_t SECULAR_WARP_MIN = 256;   // merged size from which a warp solves each root
+
 __device__ __forceinline__ double secular(const double* dnd, const double* znd, int k, double rho,
                                           double dro, double mu) {
   double f0 = 0.0, f1 = 0.0;
@@ -227,6 +229,72 @@ __global__ void __launch_bounds__(256) secular_kernel(int64_t bs, DcWork w) {
   }
   w.orig[s + i] = o;
   w.mu[s + i] = mu;
+}
+
+// The same root search with one warp per root: lanes take the poles j = lane (mod 32)
+// and the three sums are reduced with shuffles, so every lane holds the same values
+// and the warp takes every branch together.  Used for the large merges, where one
+// thread per root leaves most of the GPU idle.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) secular_warp_kernel(int64_t bs, DcWork w) {
+  const int64_t z = blockIdx.x;
+  const int64_t s = z * bs;
+  const int k = w.kp[z];
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= k) return;
+  const double rho = w.rho[z];
+  const double* dnd = w.dnd + s;
+  const double* znd = w.znd + s;
+  int o;
+  double lo, hi;
+  if (i < k - 1) {
+    const double mid = 0.5 * (dnd[i + 1] - dnd[i]);
+    const double dro = dnd[i];
+    double part = 0.0;
+    for (int j = lane; j < k; j += 32) part += znd[j] * znd[j] / ((dnd[j] - dro) - mid);
+    const double f = fma(rho, warp_sum(part), 1.0);
+    if (f >= 0.0) { o = i; lo = 0.0; hi = mid; }
+    else { o = i + 1; lo = -mid; hi = 0.0; }
+  } else {
+    o = k - 1;
+    lo = 0.0;
+    hi = rho;
+  }
+  const double dro = dnd[o];
+  const double wo = rho * znd[o] * znd[o];
+  double mu = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    double phi = 0.0, dphi = 0.0;
+    for (int j = lane; j < k; j += 32) {
+      if (j == o) continue;
+      const double r = 1.0 / ((dnd[j] - dro) - mu);
+      const double t = rho * znd[j] * znd[j] * r;
+      phi += t;
+      dphi = fma(t, r, dphi);
+    }
+    phi = warp_sum(phi);
+    dphi = warp_sum(dphi);
+    const double h = wo - mu * (1.0 + phi);
+    const double hp = -(1.0 + phi) - mu * dphi;
+    const double f = 1.0 + phi - wo / mu;
+    if (f == 0.0) break;
+    if (f > 0.0) hi = mu; else lo = mu;
+    double nx = (hp != 0.0) ? mu - h / hp : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    const bool done = fabs(nx - mu) <= 2.0 * EPS * fabs(nx) || nx == lo || nx == hi;
+    mu = nx;
+    if (done) break;
+  }
+  if (lane == 0) {
+    w.orig[s + i] = o;
+    w.mu[s + i] = mu;
+  }
 }
 
 __device__ __forceinline__ double root_minus_pole(const DcWork& w, int64_t s, int j, double di) {
@@ -372,7 +440,11 @@ ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, 
     const int64_t groups = (n - half + bs - 1) / bs;   // merges with a non-empty right half
     const unsigned chunks = (unsigned)((bs + 255) / 256);
     deflate_kernel<<<(unsigned)groups, 256, 0, ::ec::counted(s)>>>(n, bs, e, lam, Q, *wk);
-    secular_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
+    if (bs >= SECULAR_WARP_MIN)
+      secular_warp_kernel<<<dim3((unsigned)groups, (unsigned)((bs + 7) / 8)), 256, 0,
+                            ::ec::counted(s)>>>(bs, *wk);
+    else
+      secular_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
     zhat_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
     rank_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, lam);
     qp_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, Q, Qtmp, *wk);

@@ -53,6 +53,11 @@ void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* 
                         int64_t ldl, const double* Dinv, double* B, int64_t ldb,
                         const DevStatus* st);
 
+// Lower triangle of B <- B Lfac^{-T} for square B whose result is symmetric
+// (n x n); the strict upper triangle is not written.
+void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lfac, int64_t ldl,
+                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+
 // Symmetrise: copy the lower triangle onto the upper one.
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda);
 // A <- (A + A^T) / 2.

@@ -482,8 +482,8 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   }
   // a5: A = C_R^{-1} L_i C_R^{-T}
   trsm_left_lower(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
-  trsm_right_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
-  symmetrize_avg(s, n0, a.Li, ld);
+  trsm_right_lower_t_sym(s, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
+  symmetrize_lower(s, n0, a.Li, ld);
   tim->reduce_ms = t.ms();
   // a6: tridiagonalisation
   double *d = nullptr, *e = nullptr, *th = nullptr, *v = nullptr, *w = nullptr, *part = nullptr;
