@@ -81,9 +81,12 @@ typedef struct ec_config {
   long long spin_limit;   /* polls before a kernel-side wait gives up (EC_ERR_TIMEOUT); 0 = default */
   int profile;            /* nonzero: ec_run times its dominant kernels with CUDA events (see ec_timing) */
   int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
-  int precision;          /* modal form: EC_PREC_FP64 (default) or EC_PREC_BF16, see below */
+  int precision;          /* EC_PREC_FP64 (default); modal form: EC_PREC_BF16 / EC_PREC_BF16X3;
+                             plain form: EC_PREC_FP32; see below */
   int integrator;         /* modal form: EC_INTEG_THETA (default) or EC_INTEG_EXACT, see below */
   int rhs_mode;           /* EC_RHS_SUM (default), EC_RHS_INDEPENDENT or EC_RHS_PAIRED, see below */
+  int refine_steps;       /* plain form with EC_PREC_FP32: FP64 iterative-refinement sweeps per
+                             step (0 .. 8; 0 = plain FP32 solves), see below */
   int tile_variant;       /* plain form, EC_SOLVE_INVERSE: 0 (default) = ec_setup times every launch
                              shape of the per-step products on the actual factor and keeps the
                              fastest; 1 .. 3 = use that shape.  No shape changes a result bit. */
@@ -123,7 +126,17 @@ enum { EC_INTEG_THETA = 0, EC_INTEG_EXACT = 1 };
  *   EC_PREC_BF16X3  split BF16: each operand is stored as hi + lo BF16 parts and each
  *                 product is hi*hi + hi*lo + lo*hi on the tensor cores, summed in
  *                 FP64 (about 2^-16 relative per entry, three times the tensor work). */
-enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2 };
+enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2, EC_PREC_FP32 = 3 };
+
+/* Arithmetic of the plain form's per-step solve (EC_SOLVE_INVERSE, EC_RHS_SUM, no
+ * electrodes).  The Cholesky factor and its inverse are computed in FP64 in every case.
+ *   EC_PREC_FP64  both triangular products in FP64 (default).
+ *   EC_PREC_FP32  the inverse factor is rounded to FP32 (half the bytes) and the two
+ *                 products run in FP32 with FP64 partial sums; each of cfg.refine_steps
+ *                 sweeps then forms the residual b - Z x in FP64 (L from its packed FP64
+ *                 lower half, R from its sparse form) and adds the FP32 solve of it.
+ *                 ec_grad, ec_get_inverse_factor and ec_batch_run need EC_PREC_FP64
+ *                 (EC_ERR_UNSUPPORTED); electrodes (m > 0) are EC_ERR_UNSUPPORTED. */
 
 /* How the plain form applies its Cholesky factor C each step (Sec. 3.3.1).
  *   EC_SOLVE_INVERSE       C^{-1} is formed once at setup (N^3/3 extra flops); each

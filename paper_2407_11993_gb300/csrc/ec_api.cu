@@ -37,6 +37,13 @@ struct ec_ctx {
                              // only for independent right-hand sides; freed otherwise)
   TilePlan tiles;            // packed-tile layout of C^{-1} (EC_SOLVE_INVERSE)
   double* dWp = nullptr;     // C^{-1} as packed lower 64 x 64 tiles
+  float* dWp32 = nullptr;    // EC_PREC_FP32: C^{-1} as packed FP32 tiles
+  double* dLh = nullptr;     // EC_PREC_FP32: lower half of L (diagonal halved), packed tiles
+  double* dDelta = nullptr;  // EC_PREC_FP32: refined solution (npad, zero tail)
+  double* dRes = nullptr;    // EC_PREC_FP32: residual (npad, zero tail)
+  double* dT1 = nullptr;     // EC_PREC_FP32: halves of L x
+  double* dT2 = nullptr;
+  float* dV32 = nullptr;     // EC_PREC_FP32: FP32 copy of the product input (npad, zero tail)
   double* dPart1 = nullptr;  // unit partials of C^{-1} b
   double* dPart2 = nullptr;  // unit partials of C^{-T} y
   double* dYsol = nullptr;   // C^{-1} b (npad, zero tail)
@@ -124,7 +131,8 @@ ec_status grow(T** p, size_t& cap, size_t count) {
 
 void free_setup(ec_ctx* c) {
   dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
-  dfree(c->dW); dfree(c->dWp); tile_plan_free(&c->tiles); dfree(c->dPart1); dfree(c->dPart2); dfree(c->dYsol);
+  dfree(c->dW); dfree(c->dWp); tile_plan_free(&c->tiles); dfree(c->dPart1);
+  dfree(c->dWp32); dfree(c->dLh); dfree(c->dDelta); dfree(c->dRes); dfree(c->dT1); dfree(c->dT2); dfree(c->dV32); dfree(c->dPart2); dfree(c->dYsol);
   dfree(c->dRhsM); dfree(c->dYM); dfree(c->dXM);
   dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
   dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
@@ -246,15 +254,32 @@ ec_status plain_factor(ec_ctx* c) {
     EC_TRY(alloc(&c->dW, (size_t)n0 * n0));
     EC_TRY(tile_plan_create(n0, &c->tiles));
     const size_t prow = (size_t)tile_partial_rows(c->tiles), npad = (size_t)c->tiles.npad;
-    EC_TRY(alloc(&c->dWp, tile_packed_doubles(c->tiles)));
     EC_TRY(alloc(&c->dPart1, prow * npad));
     EC_TRY(alloc(&c->dPart2, prow * npad));
     EC_TRY(alloc(&c->dYsol, npad));
     cudaMemsetAsync(c->dYsol, 0, sizeof(double) * npad, c->stream);
     trtri_lower(c->stream, n0, c->dZ, n0, c->dDinv, c->dW, n0, c->st);
-    tile_pack_lower(c->stream, c->tiles, c->dW, n0, c->dWp);
-    EC_TRY(tile_autotune(c->stream, &c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
-                         c->st, c->cfg.tile_variant));
+    if (c->cfg.precision == EC_PREC_FP32) {
+      // FP32 copy of C^{-1} for the solves; the lower half of L (= L_i, no electrodes)
+      // in FP64 for the refinement residual.
+      EC_TRY(alloc(&c->dWp32, tile_packed_doubles(c->tiles)));
+      EC_TRY(alloc(&c->dLh, tile_packed_doubles(c->tiles)));
+      for (double** v : {&c->dDelta, &c->dRes, &c->dT1, &c->dT2}) {
+        EC_TRY(alloc(v, npad));
+        cudaMemsetAsync(*v, 0, sizeof(double) * npad, c->stream);
+      }
+      EC_TRY(alloc(&c->dV32, npad));
+      cudaMemsetAsync(c->dV32, 0, sizeof(float) * npad, c->stream);
+      tile_pack_lower_f32(c->stream, c->tiles, c->dW, n0, c->dWp32);
+      tile_pack_lower(c->stream, c->tiles, c->dL, c->n, c->dLh, 0.5);
+      EC_TRY(tile_autotune_f32(c->stream, &c->tiles, c->dWp32, c->dWork, c->dV32, c->dPart1,
+                               c->dYsol, c->dPart2, c->st, c->cfg.tile_variant));
+    } else {
+      EC_TRY(alloc(&c->dWp, tile_packed_doubles(c->tiles)));
+      tile_pack_lower(c->stream, c->tiles, c->dW, n0, c->dWp);
+      EC_TRY(tile_autotune(c->stream, &c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
+                           c->st, c->cfg.tile_variant));
+    }
     c->tim.tile_variant = c->tiles.variant + 1;
     for (int v = 0; v < TILE_VARIANTS && v < 4; ++v) c->tim.tile_tune_ms[v] = c->tiles.tune_ms[v];
   }
@@ -264,6 +289,35 @@ ec_status plain_factor(ec_ctx* c) {
   // for the GEMMs of independent right-hand sides.
   if (rc == EC_OK && c->dW && c->cfg.rhs_mode == EC_RHS_SUM) dfree(c->dW);
   return rc;
+}
+
+// x = Z^{-1} b for the plain step, in the context's arithmetic; returns where x is.
+//   FP64 inverse factor:  x overwrites b.
+//   FP32 inverse factor:  x0 = C^{-T} C^{-1} b in FP32, then refine_steps sweeps
+//                         x += C^{-T} C^{-1} (b - Z x) with the residual in FP64;
+//                         x is in dDelta, b is kept.
+//   substitution:         x overwrites b.
+double* plain_solve(ec_ctx* c, const StepArgs& a, double* b, cudaEvent_t* e3) {
+  if (c->cfg.plain_solver != EC_SOLVE_INVERSE) {
+    TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
+    trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, b, b, b, sy, c->trsv_grid, c->spin_limit,
+              c->st, e3);
+    return b;
+  }
+  if (c->cfg.precision != EC_PREC_FP32) {
+    tile_trmv_pair(c->stream, c->tiles, c->dWp, b, c->dPart1, c->dYsol, c->dPart2, b, c->st, e3);
+    return b;
+  }
+  tile_trmv_pair_f32(c->stream, c->tiles, c->dWp32, b, c->dV32, c->dPart1, c->dYsol, c->dPart2,
+                     c->dDelta, 0, c->st, e3);
+  for (int r = 0; r < c->cfg.refine_steps; ++r) {
+    tile_sym_product(c->stream, c->tiles, c->dLh, c->dDelta, c->dPart1, c->dPart2, c->dT1, c->dT2,
+                     c->st);
+    plain_residual(c->stream, a, b, c->dDelta, c->dT1, c->dT2, c->dRes);
+    tile_trmv_pair_f32(c->stream, c->tiles, c->dWp32, c->dRes, c->dV32, c->dPart1, c->dYsol,
+                       c->dPart2, c->dDelta, 1, c->st);
+  }
+  return c->dDelta;
 }
 
 }  // namespace
@@ -294,8 +348,16 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
   if (cfg->plain_solver != EC_SOLVE_INVERSE && cfg->plain_solver != EC_SOLVE_SUBSTITUTION)
     return EC_ERR_ARG;
   if (cfg->precision != EC_PREC_FP64 && cfg->precision != EC_PREC_BF16 &&
-      cfg->precision != EC_PREC_BF16X3)
+      cfg->precision != EC_PREC_BF16X3 && cfg->precision != EC_PREC_FP32)
     return EC_ERR_ARG;
+  if ((cfg->precision == EC_PREC_BF16 || cfg->precision == EC_PREC_BF16X3) &&
+      cfg->form != EC_FORM_MODAL)
+    return EC_ERR_UNSUPPORTED;
+  if (cfg->precision == EC_PREC_FP32 &&
+      (cfg->form != EC_FORM_PLAIN || cfg->plain_solver != EC_SOLVE_INVERSE ||
+       cfg->rhs_mode != EC_RHS_SUM))
+    return EC_ERR_UNSUPPORTED;
+  if (cfg->refine_steps < 0 || cfg->refine_steps > 8) return EC_ERR_ARG;
   if (cfg->integrator != EC_INTEG_THETA && cfg->integrator != EC_INTEG_EXACT) return EC_ERR_ARG;
   if (cfg->rhs_mode != EC_RHS_SUM && cfg->rhs_mode != EC_RHS_INDEPENDENT &&
       cfg->rhs_mode != EC_RHS_PAIRED)
@@ -359,6 +421,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   if ((m > 0 && !E) || (s > 0 && !M) || (p > 0 && !C)) return EC_ERR_ARG;
   if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
   if (m >= n) return EC_ERR_SHAPE;
+  if (c->cfg.precision == EC_PREC_FP32 && m > 0) return EC_ERR_UNSUPPORTED;
   const bool indep = c->cfg.rhs_mode != EC_RHS_SUM;
   if (m > MAXM || (!indep && s > 64) || p + 2 * m > MAXD) return EC_ERR_UNSUPPORTED;
   if (indep && (m != 0 || s < 1 || s > 65535)) return EC_ERR_UNSUPPORTED;
@@ -590,7 +653,6 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
         copy_matrix(c->stream, n0, S, c->dIi, n0, outS + ((k + 1) / stride - 1) * S * n, n);
     }
   } else if (c->cfg.form == EC_FORM_PLAIN) {
-    TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
     const int64_t every = T > 512 ? (T + 511) / 512 : 1;
     for (int64_t k = 0; k < T; ++k) {
       plain_rhs(c->stream, a);
@@ -600,14 +662,9 @@ ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, doub
         e3 = &ev[ev.size() - 3];
         for (int q = 0; q < 3; ++q) cudaEventCreate(&e3[q]);
       }
-      if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
-        tile_trmv_pair(c->stream, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
-                       c->dWork, c->st, e3);
-      } else {
-        trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
-                  c->trsv_grid, c->spin_limit, c->st, e3);
-      }
-      plain_update(c->stream, a, c->update_grid, 0);
+      StepArgs au = a;
+      au.work = plain_solve(c, a, c->dWork, e3);
+      plain_update(c->stream, au, c->update_grid, 0);
       if (outS) plain_snapshot(c->stream, a);
     }
   } else {
@@ -655,7 +712,7 @@ ec_status ec_batch_run(ec_ctx* const* ctxs, int count, int64_t T, const double* 
       if (ctxs[j] == c) return EC_ERR_ARG;
     if (!c->ready) return EC_ERR_STATE;
     if (c->cfg.form != EC_FORM_PLAIN || c->cfg.plain_solver != EC_SOLVE_INVERSE ||
-        c->cfg.rhs_mode != EC_RHS_SUM)
+        c->cfg.rhs_mode != EC_RHS_SUM || c->cfg.precision != EC_PREC_FP64)
       return EC_ERR_UNSUPPORTED;
     if (c->cfg.device != ctxs[0]->cfg.device) return EC_ERR_ARG;
     if ((c->S > 0 && (!src || !src[i])) || (c->m > 0 && (!iD || !iD[i]))) return EC_ERR_ARG;
@@ -845,16 +902,12 @@ ec_status ec_solve_z(ec_ctx* c, const double* b, double* x, int mem) {
   cudaSetDevice(c->cfg.device);
   const int64_t n0 = c->n0;
   EC_TRY(copy_in(c, c->dWork, b, (size_t)n0, mem));
-  if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
-    tile_trmv_pair(c->stream, c->tiles, c->dWp, c->dWork, c->dPart1, c->dYsol, c->dPart2,
-                   c->dWork, c->st);
-  } else {
+  if (c->cfg.plain_solver != EC_SOLVE_INVERSE) {
     TrsvSync sy{c->dFlags, c->dFlags + (n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
     trsv_begin(c->stream, sy);
-    trsv_pair(c->stream, n0, c->dZ, n0, c->dDinv, c->dWork, c->dWork, c->dWork, sy,
-              c->trsv_grid, c->spin_limit, c->st);
   }
-  EC_TRY(copy_out(c, x, c->dWork, (size_t)n0, mem));
+  const double* out = plain_solve(c, step_args(c, 0, nullptr, nullptr, 0), c->dWork, nullptr);
+  EC_TRY(copy_out(c, x, out, (size_t)n0, mem));
   return collect(c);
 }
 
@@ -862,6 +915,7 @@ ec_status ec_get_inverse_factor(ec_ctx* c, double* W, int mem) {
   if (!c || !W) return EC_ERR_ARG;
   if (!c->ready || c->cfg.form != EC_FORM_PLAIN || c->cfg.plain_solver != EC_SOLVE_INVERSE)
     return EC_ERR_STATE;
+  if (c->cfg.precision != EC_PREC_FP64) return EC_ERR_UNSUPPORTED;
   if (c->dW) {
     EC_TRY(copy_out(c, W, c->dW, (size_t)c->n0 * c->n0, mem));
     return collect(c);
@@ -886,7 +940,9 @@ ec_status ec_grad(ec_ctx* c, int64_t T, const double* src, const double* v, int6
   if (!c || T < 1 || !v || ckpt < 1) return EC_ERR_ARG;
   if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
   if (!c->ready || c->cfg.form != EC_FORM_PLAIN) return EC_ERR_STATE;
-  if (c->m != 0 || c->P < 1 || c->cfg.plain_solver != EC_SOLVE_INVERSE) return EC_ERR_UNSUPPORTED;
+  if (c->m != 0 || c->P < 1 || c->cfg.plain_solver != EC_SOLVE_INVERSE ||
+      c->cfg.precision != EC_PREC_FP64)
+    return EC_ERR_UNSUPPORTED;
   if (c->S > 0 && !src) return EC_ERR_ARG;
   cudaSetDevice(c->cfg.device);
   const int64_t n = c->n0;

@@ -68,6 +68,9 @@ struct StepArgs {
 void plain_rhs(cudaStream_t s, const StepArgs& a);
 void plain_update(cudaStream_t s, const StepArgs& a, int grid, int mode);  // mode 0: += work; 1: dots only
 void plain_snapshot(cudaStream_t s, const StepArgs& a);
+// r = b - (t1 + t2) - theta dt R x: residual of Z x = b with t1 + t2 = L x (m = 0).
+void plain_residual(cudaStream_t s, const StepArgs& a, const double* b, const double* x,
+                    const double* t1, const double* t2, double* r);
 // Batched forms over `count` instances (dA: device array of their StepArgs): one
 // launch each, blockIdx.y = instance; each instance computes exactly what its own
 // launch computes (the update uses the instance's own ugrid).

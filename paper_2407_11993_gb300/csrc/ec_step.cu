@@ -227,6 +227,20 @@ __global__ void plain_snapshot_batch_kernel(const StepArgs* A) {
   plain_snapshot_body(A[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
+// FP64 residual of the step equation for an approximate solution x (no electrodes,
+// so R_i = R):  r = b - Z x,  Z x = (t1 + t2) + theta dt R x,  t1 + t2 = L x.
+__global__ void __launch_bounds__(256) plain_residual_kernel(StepArgs a, const double* b,
+                                                             const double* x, const double* t1,
+                                                             const double* t2, double* r) {
+  const double tdt = a.theta * a.dt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n0;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double rx = 0.0;
+    for (long long e = a.R.ptr[i]; e < a.R.ptr[i + 1]; ++e) rx = fma(a.R.val[e], x[a.R.col[e]], rx);
+    r[i] = fma(-tdt, rx, b[i] - (t1[i] + t2[i]));
+  }
+}
+
 int rows_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
@@ -296,6 +310,11 @@ void ri_apply(cudaStream_t s, const StepArgs& a, double* out) {
 
 void plain_snapshot(cudaStream_t s, const StepArgs& a) {
   plain_snapshot_kernel<<<rows_grid(a.n), 256, 0, ::ec::counted(s)>>>(a);
+}
+
+void plain_residual(cudaStream_t s, const StepArgs& a, const double* b, const double* x,
+                    const double* t1, const double* t2, double* r) {
+  plain_residual_kernel<<<rows_grid(a.n0), 256, 0, ::ec::counted(s)>>>(a, b, x, t1, t2, r);
 }
 
 void plain_rhs_batch(cudaStream_t s, const StepArgs* dA, int count, int64_t max_n0) {

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ec_async.cuh"
@@ -35,9 +36,7 @@ namespace ec {
 namespace {
 
 constexpr int TB = 64;
-constexpr int TILE_DBL = TB * TB;
-constexpr uint32_t TILE_BYTES = TILE_DBL * 8;
-constexpr uint32_t SEG_BYTES = TB * 8;
+constexpr int TILE_DBL = TB * TB;   // entries of a tile
 constexpr long long WAIT_LIMIT = 1ll << 26;
 constexpr int CW = 8;   // consumer warps: 2 output halves x 4 quarters of the inner index
 constexpr int F_FIRST = 1, F_LAST = 2, F_END = 4;
@@ -49,22 +48,22 @@ struct Meta {
   int flags;
 };
 
-template <int ST>
+template <int ST, typename WT>
 struct Smem {
-  double W[ST][TILE_DBL];
-  double v[ST][TB];
+  WT W[ST][TILE_DBL];
+  WT v[ST][TB];        // the 64 vector entries the tile multiplies (same type as the factor)
   uint64_t full[ST], empty[ST];
   Meta meta[ST];
 };
-template <int ST>
+template <int ST, typename WT>
 constexpr size_t smem_bytes() {
-  return sizeof(Smem<ST>) + 128;   // + alignment slack
+  return sizeof(Smem<ST, WT>) + 128;   // + alignment slack
 }
 
 // One instance of the products (NI of them per launch, passed by value).
 struct TileDesc {
-  const double* Wp;    // packed tiles
-  const double* x;     // input vector (npad, zero tail)
+  const void* Wp;      // packed tiles (double or float entries)
+  const void* x;       // input vector (npad, zero tail), same entry type as the factor
   double* part;        // partial rows x npad
   int64_t nblk, npad;
   int chunk;
@@ -101,11 +100,13 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, DevSta
 
 // 8 consumer warps, ST ring stages, MINB CTAs per SM.  Every variant sums each
 // output entry in the same order, so all variants give bitwise identical results.
-template <bool TRANS, int ST, int MINB, int NI>
+template <bool TRANS, int ST, int MINB, int NI, typename WT>
 __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __grid_constant__ TileArgs<NI> a) {
+  constexpr uint32_t TILE_BYTES = TILE_DBL * sizeof(WT);
+  constexpr uint32_t SEG_BYTES = TB * sizeof(WT);
   if (*(volatile const int*)&a.st->code) return;
   extern __shared__ uint8_t smem_raw[];
-  Smem<ST>& sm = *reinterpret_cast<Smem<ST>*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  Smem<ST, WT>& sm = *reinterpret_cast<Smem<ST, WT>*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -145,8 +146,9 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
         const int64_t I = TRANS ? t : K, J = TRANS ? K : t;
         sm.meta[s] = Meta{out, d.npad, (t == t0 ? F_FIRST : 0) | (t == t1 - 1 ? F_LAST : 0)};
         dev::mbar_expect_tx(&sm.full[s], TILE_BYTES + SEG_BYTES);
-        dev::bulk_g2s_hint(sm.W[s], d.Wp + tile_index(I, J) * TILE_DBL, TILE_BYTES, &sm.full[s], pol);
-        dev::bulk_g2s(sm.v[s], d.x + t * TB, SEG_BYTES, &sm.full[s]);
+        dev::bulk_g2s_hint(sm.W[s], static_cast<const WT*>(d.Wp) + tile_index(I, J) * TILE_DBL,
+                           TILE_BYTES, &sm.full[s], pol);
+        dev::bulk_g2s(sm.v[s], static_cast<const WT*>(d.x) + t * TB, SEG_BYTES, &sm.full[s]);
         ++it;
       }
     }
@@ -178,9 +180,10 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
   // as much as an FMA: a shuffle reduction per unit would double the FP64 work).
   const int h = warp & 1, q = warp >> 1;
   const int o = h * 32 + lane;     // output index within the tile
-  double acc[4];
+  // (FP64 factor: FP64 arithmetic; FP32 factor: FP32 products and sums within a unit)
+  WT acc[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 4; ++k) acc[k] = WT(0);
   for (int64_t it = 0;; ++it) {
     const int s = (int)(it % ST);
     const uint32_t ph = (uint32_t)((it / ST) & 1);
@@ -189,15 +192,16 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
     if (m.flags & F_END) break;
     if (m.flags & F_FIRST) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+      for (int k = 0; k < 4; ++k) acc[k] = WT(0);
     }
-    const double* Wt = sm.W[s];
-    const double2* vv = reinterpret_cast<const double2*>(sm.v[s] + q * 16);
+    const WT* Wt = sm.W[s];
+    using WT2 = typename std::conditional<sizeof(WT) == 8, double2, float2>::type;
+    const WT2* vv = reinterpret_cast<const WT2*>(sm.v[s] + q * 16);
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) {
-      const double2 v = vv[k2];                // inner indices i0, i0 + 1 (broadcast)
+      const WT2 v = vv[k2];                    // inner indices i0, i0 + 1 (broadcast)
       const int i0 = q * 16 + 2 * k2, i1 = i0 + 1;
-      double w0, w1;
+      WT w0, w1;
       if (!TRANS) {                            // W[o, i]: column i, row o
         w0 = Wt[i0 * TB + (o ^ i0)];
         w1 = Wt[i1 * TB + (o ^ i1)];
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
     __syncwarp();
     if (lane == 0) dev::mbar_arrive(&sm.empty[s]);
     if (m.flags & F_LAST) {
-      m.out[q * m.npad + o] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      m.out[q * m.npad + o] = double((acc[0] + acc[1]) + (acc[2] + acc[3]));
     }
   }
 }
@@ -223,14 +227,21 @@ __device__ __forceinline__ int64_t tile_row_of(int64_t t) {
   return I;
 }
 
-__global__ void pack_kernel(int64_t n, int64_t ntiles, const double* W, int64_t ldw, double* Wp) {
+// Packed tiles of the lower triangle of W (column-major, ld ldw), entries converted to
+// WT; the diagonal is multiplied by diag_scale (0.5 stores the half of a symmetric
+// matrix whose product with its transpose-sum gives the full product).
+template <typename WT>
+__global__ void pack_kernel(int64_t n, int64_t ntiles, const double* W, int64_t ldw, WT* Wp,
+                            double diag_scale) {
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t I = tile_row_of(t), J = t - I * (I + 1) / 2;
     for (int e = threadIdx.x; e < TILE_DBL; e += blockDim.x) {
       const int c = e >> 6, r = (e & 63) ^ c;
       const int64_t row = I * TB + r, col = J * TB + c;
       const bool in = row < n && col < n && (I != J || r >= c);
-      Wp[t * TILE_DBL + e] = in ? W[row + col * ldw] : 0.0;
+      double v = in ? W[row + col * ldw] : 0.0;
+      if (row == col) v *= diag_scale;
+      Wp[t * TILE_DBL + e] = WT(v);
     }
   }
 }
@@ -259,12 +270,14 @@ struct SumDesc {
   double* out;
   int64_t n, nblk, npad;
   int chunk;
+  float* out32;        // optional FP32 copy of out (input of an FP32-factor product)
 };
 
 template <int NI>
 struct SumArgs {
   SumDesc d[NI];
   int trans;
+  int accumulate;      // 1: out[i] += sum (refinement corrections)
 };
 
 template <int NI>
@@ -292,7 +305,17 @@ __global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(const __grid_const
     if (g < h) red[g][tx] += red[g + h][tx];
     __syncthreads();
   }
-  if (g == 0 && i < d.n) d.out[i] = red[0][tx];
+  if (g == 0 && i < d.n) {
+    const double v = a.accumulate ? d.out[i] + red[0][tx] : red[0][tx];
+    d.out[i] = v;
+    if (d.out32) d.out32[i] = (float)v;
+  }
+}
+
+__global__ void to_f32_kernel(int64_t n, const double* x, float* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 template <int NI>
@@ -303,13 +326,17 @@ struct Variant {
   size_t smem;
 };
 
-// Launch shapes the autotuner chooses from: (ring stages, CTAs per SM).
-template <int NI>
+// Launch shapes the autotuner chooses from: (ring stages, CTAs per SM), for factors
+// with WT entries.
+template <int NI, typename WT = double>
 const Variant<NI>* variants() {
   static const Variant<NI> v[TILE_VARIANTS] = {
-      {tile_trmv_kernel<false, 4, 1, NI>, tile_trmv_kernel<true, 4, 1, NI>, CW * 32 + 32, smem_bytes<4>()},
-      {tile_trmv_kernel<false, 3, 2, NI>, tile_trmv_kernel<true, 3, 2, NI>, CW * 32 + 32, smem_bytes<3>()},
-      {tile_trmv_kernel<false, 6, 1, NI>, tile_trmv_kernel<true, 6, 1, NI>, CW * 32 + 32, smem_bytes<6>()},
+      {tile_trmv_kernel<false, 4, 1, NI, WT>, tile_trmv_kernel<true, 4, 1, NI, WT>, CW * 32 + 32,
+       smem_bytes<4, WT>()},
+      {tile_trmv_kernel<false, 3, 2, NI, WT>, tile_trmv_kernel<true, 3, 2, NI, WT>, CW * 32 + 32,
+       smem_bytes<3, WT>()},
+      {tile_trmv_kernel<false, 6, 1, NI, WT>, tile_trmv_kernel<true, 6, 1, NI, WT>, CW * 32 + 32,
+       smem_bytes<6, WT>()},
   };
   return v;
 }
@@ -317,10 +344,10 @@ const Variant<NI>* variants() {
 std::mutex g_attr_mu;
 bool g_attr_done[64] = {};
 
-template <int NI>
+template <int NI, typename WT = double>
 void set_attributes() {
   for (int i = 0; i < TILE_VARIANTS; ++i) {
-    const Variant<NI>& v = variants<NI>()[i];
+    const Variant<NI>& v = variants<NI, WT>()[i];
     cudaFuncSetAttribute(v.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     cudaFuncSetAttribute(v.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
   }
@@ -334,6 +361,7 @@ void tile_prepare_launches() {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   if (dev < 0 || dev >= 64 || g_attr_done[dev]) return;
   set_attributes<1>();
+  set_attributes<1, float>();
   set_attributes<TILE_BATCH_MAX>();
   g_attr_done[dev] = true;
 }
@@ -426,9 +454,16 @@ void tile_plan_free(TilePlan* p) {
 }
 
 void tile_pack_lower(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
-                     double* Wp) {
+                     double* Wp, double diag_scale) {
   const int64_t g = std::min<int64_t>(p.ntiles, (int64_t)num_sms() * 16);
-  pack_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, W, ldw, Wp);
+  pack_kernel<double><<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, W, ldw, Wp,
+                                                                  diag_scale);
+}
+
+void tile_pack_lower_f32(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
+                         float* Wp) {
+  const int64_t g = std::min<int64_t>(p.ntiles, (int64_t)num_sms() * 16);
+  pack_kernel<float><<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, W, ldw, Wp, 1.0);
 }
 
 void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, double* W,
@@ -438,33 +473,78 @@ void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, doub
   unpack_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, Wp, W, ldw);
 }
 
-void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out) {
+namespace {
+
+void sum_launch(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out,
+                int accumulate, float* out32 = nullptr) {
   SumArgs<1> a{};
-  a.d[0] = SumDesc{part, out, p.n, p.nblk, p.npad, p.chunk};
+  a.d[0] = SumDesc{part, out, p.n, p.nblk, p.npad, p.chunk, out32};
   a.trans = trans;
+  a.accumulate = accumulate;
   tile_sum_kernel<1><<<(unsigned)p.nblk, TB * SUM_G, 0, ::ec::counted(s)>>>(a);
 }
 
-void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const double* b,
-                    double* part1, double* y, double* part2, double* x, DevStatus* st,
-                    cudaEvent_t* ev) {
+// b_in / y_in: the vectors the two products read (b and y themselves for an FP64
+// factor; their FP32 copies b32 / y32 for an FP32 factor).
+template <typename WT>
+void pair_launch(cudaStream_t s, const TilePlan& p, const WT* Wp, const void* b_in,
+                 double* part1, double* y, float* y32, double* part2, double* x, int accumulate,
+                 DevStatus* st, cudaEvent_t* ev) {
   tile_prepare_launches();
-  const Variant<1>& v = variants<1>()[p.variant];
+  const Variant<1>& v = variants<1, WT>()[p.variant];
   const int grid = p.grids[p.variant];
   TileArgs<1> a{};
-  a.d[0] = TileDesc{Wp, b, part1, p.nblk, p.npad, p.chunk};
+  a.d[0] = TileDesc{Wp, b_in, part1, p.nblk, p.npad, p.chunk};
   a.units = p.units_fwd;
   a.nunits = p.nunits;
   a.st = st;
   if (ev) cudaEventRecord(ev[0], s);
   v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[1], s);
-  tile_sum(s, p, 0, part1, y);
-  a.d[0] = TileDesc{Wp, y, part2, p.nblk, p.npad, p.chunk};
+  sum_launch(s, p, 0, part1, y, 0, y32);
+  a.d[0] = TileDesc{Wp, y32 ? (const void*)y32 : (const void*)y, part2, p.nblk, p.npad, p.chunk};
   a.units = p.units_bwd;
   v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[2], s);
-  tile_sum(s, p, 1, part2, x);
+  sum_launch(s, p, 1, part2, x, accumulate);
+}
+
+}  // namespace
+
+void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out) {
+  sum_launch(s, p, trans, part, out, 0);
+}
+
+void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const double* b,
+                    double* part1, double* y, double* part2, double* x, DevStatus* st,
+                    cudaEvent_t* ev) {
+  pair_launch<double>(s, p, Wp, b, part1, y, nullptr, part2, x, 0, st, ev);
+}
+
+void tile_trmv_pair_f32(cudaStream_t s, const TilePlan& p, const float* Wp, const double* b,
+                        float* v32, double* part1, double* y, double* part2, double* x,
+                        int accumulate, DevStatus* st, cudaEvent_t* ev) {
+  const int64_t g = std::min<int64_t>((p.n + 255) / 256, 1024);
+  to_f32_kernel<<<(unsigned)(g < 1 ? 1 : g), 256, 0, ::ec::counted(s)>>>(p.n, b, v32);
+  pair_launch<float>(s, p, Wp, v32, part1, y, v32, part2, x, accumulate, st, ev);
+}
+
+void tile_sym_product(cudaStream_t s, const TilePlan& p, const double* Hp, const double* x,
+                      double* part1, double* part2, double* out1, double* out2, DevStatus* st) {
+  tile_prepare_launches();
+  const Variant<1>& v = variants<1>()[p.variant];
+  const int grid = p.grids[p.variant];
+  TileArgs<1> a{};
+  a.d[0] = TileDesc{Hp, x, part1, p.nblk, p.npad, p.chunk};
+  a.units = p.units_fwd;
+  a.nunits = p.nunits;
+  a.st = st;
+  v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  sum_launch(s, p, 0, part1, out1, 0);
+  a.d[0] = TileDesc{Hp, x, part2, p.nblk, p.npad, p.chunk};
+  a.units = p.units_bwd;
+  v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
+  sum_launch(s, p, 1, part2, out2, 0);
 }
 
 namespace {
@@ -515,6 +595,25 @@ ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const dou
       [&](int v) {
         p->variant = v;
         tile_trmv_pair(s, *p, Wp, b, part1, y, part2, y, st);
+      },
+      &best, p->tune_ms);
+  p->variant = best;
+  return rc;
+}
+
+ec_status tile_autotune_f32(cudaStream_t s, TilePlan* p, const float* Wp, const double* b,
+                            float* v32, double* part1, double* y, double* part2, DevStatus* st,
+                            int forced) {
+  if (forced >= 1 && forced <= TILE_VARIANTS) {
+    p->variant = forced - 1;
+    return EC_OK;
+  }
+  int best = 0;
+  ec_status rc = autotune_shapes(
+      s,
+      [&](int v) {
+        p->variant = v;
+        tile_trmv_pair_f32(s, *p, Wp, b, v32, part1, y, part2, y, 0, st);
       },
       &best, p->tune_ms);
   p->variant = best;

@@ -33,9 +33,13 @@ void tile_plan_free(TilePlan* p);
 inline int64_t tile_partial_rows(const TilePlan& p) { return 4 * ((p.nblk - 1) / p.chunk + 1); }
 inline size_t tile_packed_doubles(const TilePlan& p) { return (size_t)p.ntiles * 4096; }
 
-// Packed tiles <- lower triangle of the column-major W (n x n, ld ldw).
+// Packed tiles <- lower triangle of the column-major W (n x n, ld ldw), the
+// diagonal multiplied by diag_scale.
 void tile_pack_lower(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
-                     double* Wp);
+                     double* Wp, double diag_scale = 1.0);
+// The same, rounded to FP32 entries (same layout, half the bytes).
+void tile_pack_lower_f32(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
+                         float* Wp);
 // Column-major W (n x n, ld ldw) <- packed tiles, zeros above the diagonal.
 void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, double* W,
                        int64_t ldw);
@@ -49,6 +53,21 @@ void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const d
                     double* part1, double* y, double* part2, double* x, DevStatus* st,
                     cudaEvent_t* ev = nullptr);
 
+// The same pair with an FP32 factor: the vectors are rounded to FP32 (b into v32, y
+// again into v32 by the partial-sum kernel), products and sums within each unit are
+// FP32, partial rows and y, x are FP64.  v32: npad floats with a zero tail.
+// accumulate = 1 adds the result into x instead of overwriting it (x must then not
+// alias b).
+void tile_trmv_pair_f32(cudaStream_t s, const TilePlan& p, const float* Wp, const double* b,
+                        float* v32, double* part1, double* y, double* part2, double* x,
+                        int accumulate, DevStatus* st, cudaEvent_t* ev = nullptr);
+
+// Symmetric product from a half: with Hp the packed lower triangle of H (diagonal
+// included), out1 = H x and out2 = H^T-part: out1 + out2 = (H + H^T) x.  Packing a
+// symmetric S with diag_scale 0.5 gives out1 + out2 = S x.
+void tile_sym_product(cudaStream_t s, const TilePlan& p, const double* Hp, const double* x,
+                      double* part1, double* part2, double* out1, double* out2, DevStatus* st);
+
 // Self-tuning of the launch shape: times every shape on the actual factor (one
 // warm-up and three timed product pairs each, synchronising the stream) and keeps
 // the fastest.  forced in 1 .. TILE_VARIANTS selects shape forced - 1 instead.
@@ -56,6 +75,10 @@ void tile_trmv_pair(cudaStream_t s, const TilePlan& p, const double* Wp, const d
 // of any sum, so the choice never changes a result bit.
 ec_status tile_autotune(cudaStream_t s, TilePlan* p, const double* Wp, const double* b,
                         double* part1, double* y, double* part2, DevStatus* st, int forced);
+// The same for an FP32 factor.
+ec_status tile_autotune_f32(cudaStream_t s, TilePlan* p, const float* Wp, const double* b,
+                            float* v32, double* part1, double* y, double* part2, DevStatus* st,
+                            int forced);
 
 // out[i] = sum over the partial rows unit products wrote for row i, in row order
 // (trans = 0: partials of W b; trans = 1: partials of W^T y).

@@ -19,7 +19,8 @@ EC_FORM_PLAIN, EC_FORM_MODAL = 0, 1
 EC_MEM_HOST, EC_MEM_DEVICE = 0, 1
 EC_SOLVE_INVERSE, EC_SOLVE_SUBSTITUTION = 0, 1
 EC_PREC_FP64, EC_PREC_BF16, EC_PREC_BF16X3 = 0, 1, 2
-_PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3}
+EC_PREC_FP32 = 3
+_PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3, "fp32": EC_PREC_FP32}
 
 STATUS = {
     0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_SHAPE", 3: "EC_ERR_NOT_SPD", 4: "EC_ERR_RANK",
@@ -39,7 +40,7 @@ class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
                 ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int),
-                ("rhs_mode", c_int), ("tile_variant", c_int)]
+                ("rhs_mode", c_int), ("refine_steps", c_int), ("tile_variant", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -207,11 +208,12 @@ class ThetaMethod:
     def __init__(self, form: str = "plain", theta: float = 0.5, dt: float = 1e-6,
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
-                 integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0):
+                 integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0,
+                 refine_steps: int = 0):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
-            raise ValueError("precision must be 'fp64', 'bf16' or 'bf16x3'")
+            raise ValueError("precision must be 'fp64', 'bf16', 'bf16x3' or 'fp32'")
         if integrator not in ("theta", "exact"):
             raise ValueError("integrator must be 'theta' or 'exact'")
         if rhs not in ("sum", "independent", "paired"):
@@ -223,7 +225,8 @@ class ThetaMethod:
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
                         _PREC[precision], 1 if integrator == "exact" else 0,
-                        {"sum": 0, "independent": 1, "paired": 2}[rhs], int(tile_variant))
+                        {"sum": 0, "independent": 1, "paired": 2}[rhs], int(refine_steps),
+                        int(tile_variant))
         self.rhs = rhs
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")

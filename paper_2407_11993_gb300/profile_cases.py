@@ -76,6 +76,8 @@ def main() -> None:
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--T", type=int, default=10)
     ap.add_argument("--no-electrodes", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--refine", type=int, default=0, help="plain fp32: refinement sweeps per step")
     ap.add_argument("--config4", action="store_true",
                     help="the N=65,536 headline recipe (one coil, 4 pickups, dt = 0.1 us, no "
                          "electrodes, snapshots every 1000 steps) at size --n")
@@ -96,7 +98,8 @@ def main() -> None:
     else:
         p = synth.small(args.n, T=args.T, seed=1, electrodes=not args.no_electrodes, coil=True,
                         probes=16, dt=0.5e-6)
-    tm = eddy.ThetaMethod(args.form, p.theta, p.dt, solver=args.solver, profile=True)
+    tm = eddy.ThetaMethod(args.form, p.theta, p.dt, solver=args.solver, profile=True,
+                          precision=args.precision, refine_steps=args.refine)
     m = p.E.shape[0]
     import time
     t0 = time.perf_counter()
@@ -107,7 +110,8 @@ def main() -> None:
     out = tm.timings()
     out.update(setup_wall_s=t1 - t0, run_wall_s=t2 - t1,
                steps_per_s=p.T / (out["run_ms"] / 1e3) if out["run_ms"] > 0 else None)
-    out.update(form=args.form, n=args.n, T=args.T, launches=eddy.launch_count())
+    out.update(form=args.form, n=args.n, T=args.T, precision=args.precision, refine=args.refine,
+               launches=eddy.launch_count())
     print(json.dumps(out))
 
 
