@@ -144,6 +144,27 @@ __global__ void __launch_bounds__(256) dgemm_grouped_kernel(int64_t n, int64_t b
                   blockIdx.y);
 }
 
+// Merge products of divide and conquer: group z covers [s, s + nb), s = z bs, with the
+// children's blocks [s, s + bs/2) and [s + bs/2, s + nb) of the block-diagonal Qin;
+//   Qout[top rows, s : s + nb]    = Qin[top, top]       Wm[top rows, s : s + nb]
+//   Qout[bottom rows, s : s + nb] = Qin[bottom, bottom] Wm[bottom rows, s : s + nb]
+// blockIdx.z = 2 z + (0: top, 1: bottom).
+__global__ void __launch_bounds__(256) dgemm_halves_kernel(int64_t n, int64_t bs, const double* Qin,
+                                                           const double* Wm, double* Qout,
+                                                           int64_t ld, const DevStatus* st) {
+  if (failed(st)) return;
+  const int64_t s0 = (int64_t)(blockIdx.z >> 1) * bs;
+  const int64_t nb = (n - s0) < bs ? (n - s0) : bs;
+  const int64_t half = bs / 2;
+  const int64_t off = (blockIdx.z & 1) ? half : 0;
+  const int64_t M = (blockIdx.z & 1) ? nb - half : half;
+  if (M <= 0 || (int64_t)blockIdx.x * GEMM_TILE >= M || (int64_t)blockIdx.y * GEMM_TILE >= nb)
+    return;
+  const int64_t r0 = s0 + off;
+  gemm_tile<0, 0>(M, nb, M, 1.0, Qin + r0 + r0 * ld, ld, Wm + r0 + s0 * ld, ld, 0.0,
+                  Qout + r0 + s0 * ld, ld, 0, blockIdx.x, blockIdx.y);
+}
+
 // Cholesky of one diagonal block (kb <= 64) in shared memory, plus the inverse
 // of the resulting lower-triangular factor.  One CTA of 256 threads.
 __global__ void __launch_bounds__(256) potf2_diag_kernel(double* A, int64_t lda, int kb,
@@ -299,6 +320,16 @@ void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const 
   if (groups <= 0) return;
   const unsigned t = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
   dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, A, B, C, ld, st);
+}
+
+void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* Qin,
+                  const double* Wm, double* Qout, int64_t ld, const DevStatus* st) {
+  if (groups <= 0) return;
+  const int64_t half = bs / 2;
+  const unsigned tm = (unsigned)((half + GEMM_TILE - 1) / GEMM_TILE);
+  const unsigned tn = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
+  dgemm_halves_kernel<<<dim3(tm, tn, (unsigned)(2 * groups)), 256, 0, ::ec::counted(s)>>>(
+      n, bs, Qin, Wm, Qout, ld, st);
 }
 
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {

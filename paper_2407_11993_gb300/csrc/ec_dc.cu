@@ -337,27 +337,11 @@ __global__ void __launch_bounds__(256) rank_kernel(int64_t n, int64_t bs, DcWork
   lam[s + r] = v;
 }
 
-// Qp[:, p] = Q[:, perm[p]] on the block, then the deflation rotations.
-__global__ void __launch_bounds__(256) qp_kernel(int64_t n, int64_t bs, const double* Q,
-                                                 double* Qp, DcWork w) {
-  const int64_t z = blockIdx.x;
-  const int64_t s = z * bs;
-  const int64_t nb = (n - s) < bs ? (n - s) : bs;
-  const int64_t r = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= nb) return;
-  const int64_t row = s + r;
-  for (int64_t p = 0; p < nb; ++p) Qp[row + (s + p) * n] = Q[row + (s + w.perm[s + p]) * n];
-  const int nrot = w.nrot[z];
-  for (int t = 0; t < nrot; ++t) {
-    const int64_t pa = s + w.rot_a[s + t], pb = s + w.rot_b[s + t];
-    const double c = w.rot_c[s + t], sn = w.rot_s[s + t];
-    const double x = Qp[row + pa * n], y = Qp[row + pb * n];
-    Qp[row + pa * n] = c * x - sn * y;
-    Qp[row + pb * n] = sn * x + c * y;
-  }
-}
-
-// Column rank(p) of the small eigenvector matrix W for item p.
+// Column rank(p) of the small eigenvector matrix for item p, written with its rows in
+// the children's column order: the entry of sorted item r goes to row perm[r].  With
+// the deflation rotations applied afterwards (rot_kernel), the merged eigenvectors are
+// diag(Q1, Q2) W, so the product needs only the two diagonal blocks (half the flops
+// of multiplying a permuted full block).
 __global__ void __launch_bounds__(256) vec_kernel(int64_t n, int64_t bs, DcWork w, double* W) {
   const int64_t z = blockIdx.y;
   const int64_t s = z * bs;
@@ -366,8 +350,9 @@ __global__ void __launch_bounds__(256) vec_kernel(int64_t n, int64_t bs, DcWork 
   if (p >= nb) return;
   __shared__ double sh[33];
   double* col = W + s + (s + w.rank[s + p]) * n;
+  const int* perm = w.perm + s;
   if (w.defl[s + p]) {
-    for (int64_t r = threadIdx.x; r < nb; r += blockDim.x) col[r] = (r == p) ? 1.0 : 0.0;
+    for (int64_t r = threadIdx.x; r < nb; r += blockDim.x) col[perm[r]] = (r == p) ? 1.0 : 0.0;
     return;
   }
   const int k = w.kp[z];
@@ -393,7 +378,30 @@ __global__ void __launch_bounds__(256) vec_kernel(int64_t n, int64_t bs, DcWork 
   const double inv = sh[32];
   for (int64_t r = threadIdx.x; r < nb; r += blockDim.x) {
     const int q = w.cmp[s + r];
-    col[r] = (q >= 0) ? inv * (w.zhat[s + q] / ((w.dnd[s + q] - dro) - mu)) : 0.0;
+    col[perm[r]] = (q >= 0) ? inv * (w.zhat[s + q] / ((w.dnd[s + q] - dro) - mu)) : 0.0;
+  }
+}
+
+// The deflation rotations act on columns (pa, pb) of the permuted children's vectors:
+// col_pa <- c col_pa - s col_pb, col_pb <- s col_pa + c col_pb, in rotation order.
+// Moved onto the small matrix they become row operations, applied last rotation
+// first: row_pa <- c row_pa + s row_pb, row_pb <- -s row_pa + c row_pb (rows in the
+// children's order, i.e. perm[pa], perm[pb]).  One thread per column.
+__global__ void __launch_bounds__(256) rot_kernel(int64_t n, int64_t bs, DcWork w, double* W) {
+  const int64_t z = blockIdx.y;
+  const int64_t s = z * bs;
+  const int64_t nb = (n - s) < bs ? (n - s) : bs;
+  const int nrot = w.nrot[z];
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (nrot == 0 || c >= nb) return;
+  double* col = W + s + (s + c) * n;
+  const int* perm = w.perm + s;
+  for (int t = nrot - 1; t >= 0; --t) {
+    const int64_t ra = perm[w.rot_a[s + t]], rb = perm[w.rot_b[s + t]];
+    const double cs = w.rot_c[s + t], sn = w.rot_s[s + t];
+    const double x = col[ra], y = col[rb];
+    col[ra] = fma(cs, x, sn * y);
+    col[rb] = fma(-sn, x, cs * y);
   }
 }
 
@@ -435,11 +443,13 @@ ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, 
   cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * n, s);
   leaf_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
       n, d, e, lam, Q);
+  double* cur = Q;      // eigenvectors of the current blocks
+  double* nxt = Qtmp;   // the merged blocks' eigenvectors
   for (int64_t bs = 2; bs / 2 < n; bs *= 2) {
     const int64_t half = bs / 2;
     const int64_t groups = (n - half + bs - 1) / bs;   // merges with a non-empty right half
     const unsigned chunks = (unsigned)((bs + 255) / 256);
-    deflate_kernel<<<(unsigned)groups, 256, 0, ::ec::counted(s)>>>(n, bs, e, lam, Q, *wk);
+    deflate_kernel<<<(unsigned)groups, 256, 0, ::ec::counted(s)>>>(n, bs, e, lam, cur, *wk);
     if (bs >= SECULAR_WARP_MIN)
       secular_warp_kernel<<<dim3((unsigned)groups, (unsigned)((bs + 7) / 8)), 256, 0,
                             ::ec::counted(s)>>>(bs, *wk);
@@ -447,10 +457,17 @@ ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, 
       secular_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
     zhat_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(bs, *wk);
     rank_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, lam);
-    qp_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, Q, Qtmp, *wk);
     vec_kernel<<<dim3((unsigned)bs, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, W);
-    dgemm_grouped(s, n, bs, groups, Qtmp, W, Q, n, st);
+    rot_kernel<<<dim3(chunks, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, W);
+    dgemm_halves(s, n, bs, groups, cur, W, nxt, n, st);
+    const int64_t done = groups * bs;
+    if (done < n)   // a trailing block without a right half is carried over unmerged
+      copy_matrix(s, n - done, n - done, cur + done + done * n, n, nxt + done + done * n, n);
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
   }
+  if (cur != Q) copy_matrix(s, n, n, cur, n, Q, n);
   return EC_OK;
 }
 

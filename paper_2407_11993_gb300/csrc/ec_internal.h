@@ -31,6 +31,12 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
            double* C, int64_t ldc, int tri, const DevStatus* st);
 
+// Divide-and-conquer merge products: for each merge z (rows / columns [z bs,
+// min((z+1) bs, n))), the top and bottom children's diagonal blocks of Qin times the
+// matching rows of Wm, into the same rows of Qout (columns of the whole merge).
+void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* Qin,
+                  const double* Wm, double* Qout, int64_t ld, const DevStatus* st);
+
 // Block-diagonal batched product: for z < groups, the bs x bs diagonal block z
 // (clipped at n) of C = A B, all three n x n with leading dimension ld.
 void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,

@@ -7,8 +7,12 @@
 // Column j: reflector H_j = I - tau_j v_j v_j^T with v_j = 0 above row j+1,
 // v_j[j+1] = 1, annihilating A[j+2:, j]; then
 //   p = tau A22 v,  w = p - (tau/2)(p^T v) v,  A22 <- A22 - v w^T - w v^T.
-// The full symmetric matrix is kept up to date so that A22 v is a coalesced
-// column-major GEMV.  v_j[j+2:] is stored back into A[j+2:, j].
+// Blocking (delaying the rank-2 updates into a GEMM) does not pay on GB300: the
+// update is FP64-bound either way (2 FMAs per element per column), and FP64 GEMM
+// runs at the same ~1.2 TFLOP/s as the streamed rank-2 update.
+// Only the lower triangle is kept up to date (half the FP64 work of the rank-2
+// update); A22 v is read from it as a row part and a column part, both coalesced.
+// v_j[j+2:] is stored back into A[j+2:, j].
 
 #include <cmath>
 
@@ -79,7 +83,10 @@ __global__ void __launch_bounds__(HT) house_col_kernel(int64_t n, double* A, int
   }
 }
 
-// partial[c * n + i] = sum over column chunk c of A[i, k] v[k], i, k in [j+1, n)
+// Only the lower triangle of the trailing matrix is kept up to date, so A22 v is
+// split into its row part and its column part:
+//   partial[c * n + i] = sum over column chunk c of A[i, k] v[k], k <= i   (row part)
+//   colpart[i]         = sum_{k > i} A[k, i] v[k]                        (column part)
 __global__ void __launch_bounds__(256) symv_partial_kernel(int64_t n, const double* A, int64_t lda,
                                                            int64_t j, const double* v,
                                                            double* partial, int64_t kc) {
@@ -87,6 +94,7 @@ __global__ void __launch_bounds__(256) symv_partial_kernel(int64_t n, const doub
   const int64_t k0 = j + 1 + blockIdx.y * kc;
   int64_t k1 = k0 + kc;
   if (k1 > n) k1 = n;
+  if (k1 > i + 1) k1 = i + 1;
   if (i >= n) return;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int64_t k = k0;
@@ -100,24 +108,80 @@ __global__ void __launch_bounds__(256) symv_partial_kernel(int64_t n, const doub
   partial[blockIdx.y * n + i] = (s0 + s1) + (s2 + s3);
 }
 
-__global__ void __launch_bounds__(HT) w_kernel(int64_t n, int64_t j, const double* v,
-                                               const double* tau, const double* partial,
-                                               int nchunk, double* w) {
-  __shared__ double sh[40];
-  const double t = tau[j];
-  double dot = 0.0;
-  for (int64_t i = j + 1 + threadIdx.x; i < n; i += HT) {
-    double p = 0.0;
-    for (int c = 0; c < nchunk; ++c) p += partial[c * n + i];
-    p *= t;
-    w[i] = p;
-    dot = fma(p, v[i], dot);
+// One warp per column i: colpart[i] = sum_{k > i} A[k, i] v[k] (coalesced down the column).
+__global__ void __launch_bounds__(256) symv_col_kernel(int64_t n, const double* A, int64_t lda,
+                                                       int64_t j, const double* v, double* colpart) {
+  const int64_t i = j + 1 + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const double* col = A + i * lda;
+  double s0 = 0.0, s1 = 0.0;
+  int64_t k = i + 1 + lane;
+  for (; k + 32 < n; k += 64) {
+    s0 = fma(col[k], v[k], s0);
+    s1 = fma(col[k + 32], v[k + 32], s1);
   }
-  dot = block_sum1024(dot, sh);
-  const double f = 0.5 * t * dot;
-  for (int64_t i = j + 1 + threadIdx.x; i < n; i += HT) w[i] = fma(-f, v[i], w[i]);
+  if (k < n) s0 = fma(col[k], v[k], s0);
+  double t = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) colpart[i] = t;
 }
 
+// p = tau A22 v from the row and column partials (rows j+1 .. n-1), then
+// w = p - f v with f = (tau/2) p^T v: each CTA owns a contiguous row range and writes
+// its part of p^T v; the last CTA to finish sums the parts in CTA order and turns p
+// into w in place.
+__global__ void __launch_bounds__(256) p_kernel(int64_t n, int64_t j, const double* v,
+                                                const double* tau, const double* partial,
+                                                int nchunk, const double* colpart, double* p,
+                                                double* dots, unsigned* counter) {
+  __shared__ double sh[9];
+  __shared__ bool last;
+  const double t = tau[j];
+  const int64_t len = n - j - 1;
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = j + 1 + blockIdx.x * chunk;
+  const int64_t r1 = (r0 + chunk < n) ? r0 + chunk : n;
+  double dot = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double q = colpart[i];
+    for (int c = 0; c < nchunk; ++c) q += partial[c * n + i];
+    q *= t;
+    p[i] = q;
+    dot = fma(q, v[i], dot);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if (lane == 0) sh[w] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) b += sh[q];
+    dots[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double b = 0.0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) b += __ldcg(dots + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (threadIdx.x == 0) {
+      sh[8] = 0.5 * t * b;
+      *counter = 0u;
+    }
+  }
+  __syncthreads();
+  const double f = sh[8];
+  for (int64_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) p[i] = fma(-f, v[i], p[i]);
+}
+
+// lower(A22) <- lower(A22 - v w^T - w v^T).
 __global__ void syr2_kernel(int64_t n, double* A, int64_t lda, int64_t j, const double* v,
                             const double* w, const double* tau) {
   if (tau[j] == 0.0) return;
@@ -126,7 +190,7 @@ __global__ void syr2_kernel(int64_t n, double* A, int64_t lda, int64_t j, const 
     const int64_t k = j + 1 + kk;
     const double vk = v[k], wk = w[k];
     double* colk = A + k * lda;
-    for (int64_t i = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+    for (int64_t i = k + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
       colk[i] = fma(-v[i], wk, fma(-w[i], vk, colk[i]));
   }
@@ -187,6 +251,13 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
                  double* tau, double* v, double* w, double* partial, int64_t partial_cap,
                  const DevStatus* st) {
   const int sms = num_sms();
+  const int pgrid = 2 * sms;
+  // the tail of the partial buffer: per-CTA parts of p^T v and the last-CTA counter
+  double* dots = partial + partial_cap - (pgrid + 2);
+  unsigned* counter = reinterpret_cast<unsigned*>(dots + pgrid);
+  partial_cap -= pgrid + 2 + n;
+  double* colpart = partial + partial_cap;   // n entries before the tail
+  cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   for (int64_t j = 0; j + 2 < n; ++j) {
     const int64_t len = n - j - 1;
     house_col_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, A, lda, j, v, d, e, tau, st);
@@ -199,7 +270,11 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
     nchunk = (len + kc - 1) / kc;
     symv_partial_kernel<<<dim3((unsigned)rb, (unsigned)nchunk), 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v,
                                                                              partial, kc);
-    w_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, j, v, tau, partial, (int)nchunk, w);
+    symv_col_kernel<<<(unsigned)((len + 7) / 8), 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v,
+                                                                              colpart);
+    const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;
+    p_kernel<<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(n, j, v, tau, partial, (int)nchunk,
+                                                         colpart, w, dots, counter);
     dim3 g2((unsigned)((len + 255) / 256 < 8 ? (len + 255) / 256 : 8),
             (unsigned)(len < 4096 ? len : 4096));
     syr2_kernel<<<g2, 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v, w, tau);
