@@ -144,6 +144,32 @@ __global__ void __launch_bounds__(256) dgemm_grouped_kernel(int64_t n, int64_t b
                   blockIdx.y);
 }
 
+// Split-K partial products for C = A^T B with a short output (M <= 64 rows): slice z of
+// the K range [z kc, (z+1) kc) goes to ws + z M N (ld M).
+__global__ void __launch_bounds__(256) dgemm_tn_split_kernel(int64_t M, int64_t N, int64_t K,
+                                                             int64_t kc, const double* A,
+                                                             int64_t lda, const double* B,
+                                                             int64_t ldb, double* ws,
+                                                             const DevStatus* st) {
+  if (failed(st)) return;
+  const int64_t k0 = (int64_t)blockIdx.z * kc;
+  const int64_t kl = (K - k0) < kc ? (K - k0) : kc;
+  double* C = ws + (int64_t)blockIdx.z * M * N;
+  gemm_tile<1, 0>(M, N, kl > 0 ? kl : 0, 1.0, A + k0, lda, B + k0, ldb, 0.0, C, M, 0, blockIdx.x,
+                  blockIdx.y);
+}
+
+__global__ void split_sum_kernel(int64_t M, int64_t N, int splits, const double* ws, double* C,
+                                 int64_t ldc) {
+  const int64_t tot = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += ws[(int64_t)z * tot + idx];
+    C[(idx % M) + (idx / M) * ldc] = v;
+  }
+}
+
 // Merge products of divide and conquer: group z covers [s, s + nb), s = z bs, with the
 // children's blocks [s, s + bs/2) and [s + bs/2, s + nb) of the block-diagonal Qin;
 //   Qout[top rows, s : s + nb]    = Qin[top, top]       Wm[top rows, s : s + nb]
@@ -320,6 +346,32 @@ void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const 
   if (groups <= 0) return;
   const unsigned t = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
   dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, A, B, C, ld, st);
+}
+
+int dgemm_tn_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + GEMM_TILE - 1) / GEMM_TILE) * ((N + GEMM_TILE - 1) / GEMM_TILE);
+  int64_t sp = (4 * (int64_t)num_sms() + tiles - 1) / tiles;
+  if (sp > 64) sp = 64;
+  if (sp > K / 256) sp = K / 256;
+  return sp < 1 ? 1 : (int)sp;
+}
+
+void dgemm_tn_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double* C, int64_t ldc, double* ws, int splits,
+                    const DevStatus* st) {
+  if (M <= 0 || N <= 0) return;
+  if (splits <= 1 || !ws) {
+    dgemm(s, T_, N_, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, 0, st);
+    return;
+  }
+  int64_t kc = (K + splits - 1) / splits;
+  kc = (kc + GEMM_KC - 1) / GEMM_KC * GEMM_KC;
+  const int sp = (int)((K + kc - 1) / kc);
+  dim3 grid((unsigned)((M + GEMM_TILE - 1) / GEMM_TILE), (unsigned)((N + GEMM_TILE - 1) / GEMM_TILE),
+            (unsigned)sp);
+  dgemm_tn_split_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, kc, A, lda, B, ldb, ws, st);
+  const int64_t g = (M * N + 255) / 256 < 2048 ? (M * N + 255) / 256 : 2048;
+  split_sum_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(M, N, sp, ws, C, ldc);
 }
 
 void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* Qin,

@@ -31,6 +31,14 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
            double* C, int64_t ldc, int tri, const DevStatus* st);
 
+// C (M x N, ld ldc) = A^T B for a short output (M <= 64) and long K, with K split
+// into `splits` slices whose partial products (ws: splits x M x N) are summed in
+// slice order; dgemm_tn_splits picks the slice count that fills the GPU.
+int dgemm_tn_splits(int64_t M, int64_t N, int64_t K);
+void dgemm_tn_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double* C, int64_t ldc, double* ws, int splits,
+                    const DevStatus* st);
+
 // Divide-and-conquer merge products: for each merge z (rows / columns [z bs,
 // min((z+1) bs, n))), the top and bottom children's diagonal blocks of Qin times the
 // matching rows of Wm, into the same rows of Qout (columns of the whole merge).

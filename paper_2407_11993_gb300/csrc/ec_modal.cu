@@ -23,6 +23,7 @@
 // partial sums are then added in CTA order by a second kernel (deterministic).
 // Snapshot amplitudes are stored and turned into currents by one GEMM.
 
+#include <algorithm>
 #include <cmath>
 
 #include "ec_modal.h"
@@ -525,7 +526,17 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
            (unsigned)(n0 < 65535 ? n0 : 65535));
     reverse_kernel<<<g, 256, 0, ::ec::counted(s)>>>(n0, lam, Q1, ms->tau, ms->U);
   }
-  ormtr_lower(s, n0, a.Li, ld, th, ms->U, n0, n0, Vb, Gb, Tb, W1, W2, a.st);
+  {
+    const int64_t ws_cap = std::max<int64_t>((int64_t)dgemm_tn_splits(NB, n0, n0) * NB * n0,
+                                             (int64_t)dgemm_tn_splits(NB, NB, n0) * NB * NB);
+    double* ws = nullptr;
+    if (alloc_n(&ws, (size_t)ws_cap)) ws = nullptr;   // without it the products run unsplit
+    ormtr_lower(s, n0, a.Li, ld, th, ms->U, n0, n0, Vb, Gb, Tb, W1, W2, ws, ws ? ws_cap : 0, a.st);
+    if (ws) {
+      cudaStreamSynchronize(s);
+      cudaFree(ws);
+    }
+  }
   trsm_left_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, ms->U, n0, a.st);
   tim->backtransform_ms = t.ms();
   cleanup();

@@ -284,7 +284,7 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
 
 void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const double* tau,
                  double* Y, int64_t ldy, int64_t ncol, double* V, double* G, double* T,
-                 double* W, double* W2, const DevStatus* st) {
+                 double* W, double* W2, double* ws, int64_t ws_cap, const DevStatus* st) {
   const int64_t nref = n - 2;
   if (nref <= 0) return;
   const int64_t nblk = (nref + NB - 1) / NB;
@@ -293,9 +293,15 @@ void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const 
     const int kb = (int)((nref - b) < NB ? (nref - b) : NB);
     form_v_kernel<<<dim3(32, kb), 256, 0, ::ec::counted(s)>>>(n, A, lda, b, kb, V);
     const int64_t r0 = b + 1, len = n - r0;
-    dgemm(s, T_, N_, kb, kb, len, 1.0, V + r0, n, V + r0, n, 0.0, G, kb, 0, st);
+    // G = V^T V: one 64 x 64 output over a long K; one CTA would carry it alone
+    int spg = dgemm_tn_splits(kb, kb, len);
+    while (spg > 1 && (int64_t)spg * kb * kb > ws_cap) --spg;
+    dgemm_tn_split(s, kb, kb, len, V + r0, n, V + r0, n, G, kb, ws, spg, st);
     form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G, tau, b, T);
-    dgemm(s, T_, N_, kb, ncol, len, 1.0, V + r0, n, Y + r0, ldy, 0.0, W, kb, 0, st);
+    // W = V^T Y: a 64-row output with a long K, split over K to fill the GPU
+    int sp = dgemm_tn_splits(kb, ncol, len);
+    while (sp > 1 && (int64_t)sp * kb * ncol > ws_cap) --sp;
+    dgemm_tn_split(s, kb, ncol, len, V + r0, n, Y + r0, ldy, W, kb, ws, sp, st);
     dgemm(s, N_, N_, kb, ncol, kb, 1.0, T, kb, W, kb, 0.0, W2, kb, 0, st);
     dgemm(s, N_, N_, len, ncol, kb, -1.0, V + r0, n, W2, kb, 1.0, Y + r0, ldy, 0, st);
   }

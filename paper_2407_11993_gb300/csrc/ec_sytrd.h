@@ -14,10 +14,11 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
                  const DevStatus* st);
 
 // Y (n x ncol) <- Q Y with Q = H_0 ... H_{n-3} from sytrd_lower.  Scratch: V (n x 64),
-// G, T (64 x 64), W, W2 (64 x ncol).
+// G, T (64 x 64), W, W2 (64 x ncol), ws (ws_cap doubles, for the split-K product
+// V^T Y; up to dgemm_tn_splits(64, ncol, n) x 64 x ncol are used).
 void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const double* tau,
                  double* Y, int64_t ldy, int64_t ncol, double* V, double* G, double* T,
-                 double* W, double* W2, const DevStatus* st);
+                 double* W, double* W2, double* ws, int64_t ws_cap, const DevStatus* st);
 
 // Divide-and-conquer eigensolver of the symmetric tridiagonal (d, e):
 // lam (n, ascending) and Q (n x n, column-major, ld n) with T = Q diag(lam) Q^T.
