@@ -320,10 +320,89 @@ int num_sms() {
   return sms;
 }
 
+// Products with few columns (N <= SKINNY_N: initial modal state, projections, a few
+// snapshots): a 64 x 64 output tile would spend most of its FMAs on padding, so these
+// stream A once with all N accumulators per output row.
+constexpr int SKINNY_N = 16;
+
+// C = alpha A B + beta C, A: M x K.  Block: 64 rows x 4 K-groups; each thread sums
+// every 4th K index of its row, the four partial sums are added in a fixed order.
+__global__ void __launch_bounds__(256) skinny_nn_kernel(int64_t M, int N, int64_t K, double alpha,
+                                                        const double* A, int64_t lda,
+                                                        const double* B, int64_t ldb, double beta,
+                                                        double* C, int64_t ldc, const DevStatus* st) {
+  if (failed(st)) return;
+  __shared__ double red[4][SKINNY_N][64];
+  const int tr = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int64_t r = (int64_t)blockIdx.x * 64 + tr;
+  double acc[SKINNY_N];
+#pragma unroll
+  for (int j = 0; j < SKINNY_N; ++j) acc[j] = 0.0;
+  if (r < M) {
+    for (int64_t k = g; k < K; k += 4) {
+      const double a = A[r + k * lda];
+#pragma unroll
+      for (int j = 0; j < SKINNY_N; ++j)
+        if (j < N) acc[j] = fma(a, B[k + j * ldb], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < SKINNY_N; ++j) red[g][j][tr] = acc[j];
+  __syncthreads();
+  if (g == 0 && r < M) {
+    for (int j = 0; j < N; ++j) {
+      const double v = alpha * ((red[0][j][tr] + red[1][j][tr]) + (red[2][j][tr] + red[3][j][tr]));
+      double* c = C + r + j * ldc;
+      *c = beta != 0.0 ? fma(beta, *c, v) : v;
+    }
+  }
+}
+
+// C = alpha A^T B + beta C, A: K x M.  One warp per output row: lanes stride down the
+// contiguous column A[:, r], then a shuffle reduction per output column.
+__global__ void __launch_bounds__(256) skinny_tn_kernel(int64_t M, int N, int64_t K, double alpha,
+                                                        const double* A, int64_t lda,
+                                                        const double* B, int64_t ldb, double beta,
+                                                        double* C, int64_t ldc, const DevStatus* st) {
+  if (failed(st)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= M) return;
+  const double* col = A + r * lda;
+  double acc[SKINNY_N];
+#pragma unroll
+  for (int j = 0; j < SKINNY_N; ++j) acc[j] = 0.0;
+  for (int64_t k = lane; k < K; k += 32) {
+    const double a = col[k];
+#pragma unroll
+    for (int j = 0; j < SKINNY_N; ++j)
+      if (j < N) acc[j] = fma(a, B[k + j * ldb], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < SKINNY_N; ++j) {
+    double v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && j < N) {
+      double* c = C + r + j * ldc;
+      *c = beta != 0.0 ? fma(beta, *c, alpha * v) : alpha * v;
+    }
+  }
+}
+
 void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
            int64_t ldc, int tri, const DevStatus* st) {
   if (M <= 0 || N <= 0) return;
+  if (!tri && tb == N_ && N <= SKINNY_N && K >= 4 * GEMM_TILE) {
+    if (ta == N_)
+      skinny_nn_kernel<<<(unsigned)((M + 63) / 64), 256, 0, ::ec::counted(s)>>>(
+          M, (int)N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    else
+      skinny_tn_kernel<<<(unsigned)((M + 7) / 8), 256, 0, ::ec::counted(s)>>>(
+          M, (int)N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    return;
+  }
   dim3 grid;
   if (tri) {
     int64_t nt = (M + GEMM_TILE - 1) / GEMM_TILE;
