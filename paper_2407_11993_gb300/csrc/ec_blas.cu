@@ -359,11 +359,14 @@ __global__ void __launch_bounds__(256) skinny_nn_kernel(int64_t M, int N, int64_
 }
 
 // C = alpha A^T B + beta C, A: K x M.  One warp per output row: lanes stride down the
-// contiguous column A[:, r], then a shuffle reduction per output column.
+// contiguous column A[:, r], then a shuffle reduction per output column.  With ct = 1
+// the result is stored transposed (C[j + r ldc]), which serves a short A^T B computed
+// as (B^T A)^T.
 __global__ void __launch_bounds__(256) skinny_tn_kernel(int64_t M, int N, int64_t K, double alpha,
                                                         const double* A, int64_t lda,
                                                         const double* B, int64_t ldb, double beta,
-                                                        double* C, int64_t ldc, const DevStatus* st) {
+                                                        double* C, int64_t ldc, int ct,
+                                                        const DevStatus* st) {
   if (failed(st)) return;
   const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(256) skinny_tn_kernel(int64_t M, int N, int64_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0 && j < N) {
-      double* c = C + r + j * ldc;
+      double* c = ct ? C + j + r * ldc : C + r + j * ldc;
       *c = beta != 0.0 ? fma(beta, *c, alpha * v) : alpha * v;
     }
   }
@@ -400,7 +403,21 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
           M, (int)N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     else
       skinny_tn_kernel<<<(unsigned)((M + 7) / 8), 256, 0, ::ec::counted(s)>>>(
-          M, (int)N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+          M, (int)N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, st);
+    return;
+  }
+  if (!tri && ta == T_ && tb == N_ && M <= SKINNY_N && K >= 4 * GEMM_TILE) {
+    // few output rows: C^T = B^T A, one warp per column of C, stored transposed
+    skinny_tn_kernel<<<(unsigned)((N + 7) / 8), 256, 0, ::ec::counted(s)>>>(
+        N, (int)M, K, alpha, B, ldb, A, lda, beta, C, ldc, 1, st);
+    return;
+  }
+  if (!tri && tb == N_ && N > GEMM_TILE && N % GEMM_TILE != 0 && N % GEMM_TILE <= SKINNY_N &&
+      K >= 4 * GEMM_TILE) {
+    // a ragged last column tile would be mostly padding: full tiles + a skinny remainder
+    const int64_t r = N % GEMM_TILE, Nf = N - r;
+    dgemm(s, ta, tb, M, Nf, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, st);
+    dgemm(s, ta, tb, M, r, K, alpha, A, lda, B + Nf * ldb, ldb, beta, C + Nf * ldc, ldc, 0, st);
     return;
   }
   dim3 grid;

@@ -81,6 +81,9 @@ def main() -> None:
     ap.add_argument("--config4", action="store_true",
                     help="the N=65,536 headline recipe (one coil, 4 pickups, dt = 0.1 us, no "
                          "electrodes, snapshots every 1000 steps) at size --n")
+    ap.add_argument("--config2", action="store_true",
+                    help="the N=8,192 electrode recipe (2 electrodes, 1 A step, 16 pickups, "
+                         "dt = 0.5 us, snapshots every 100 steps) at size --n")
     ap.add_argument("--batch", type=int, default=0, help="uneven plain-form instances (ec_batch_run)")
     ap.add_argument("--nmin", type=int, default=1024)
     ap.add_argument("--nmax", type=int, default=12288)
@@ -95,6 +98,8 @@ def main() -> None:
         return
     if args.config4:
         p = synth.config4(T=args.T, n=args.n)
+    elif args.config2:
+        p = synth.config2(T=args.T, n=args.n)
     else:
         p = synth.small(args.n, T=args.T, seed=1, electrodes=not args.no_electrodes, coil=True,
                         probes=16, dt=0.5e-6)
@@ -103,15 +108,18 @@ def main() -> None:
     m = p.E.shape[0]
     import time
     t0 = time.perf_counter()
-    tm.setup(p.L, p.R, p.E if m else None, p.M, p.MD if m else None, p.C)
+    tm.setup(p.L, p.R, p.E if m else None, p.M if p.M.shape[1] else None, p.MD if m else None,
+             p.C)
     t1 = time.perf_counter()
-    tm.run(p.T, p.src, p.iD if m else None, p.snap_stride if args.config4 else 0)
+    setup_launches = eddy.launch_count()
+    tm.run(p.T, p.src if p.M.shape[1] else None, p.iD if m else None,
+           p.snap_stride if (args.config4 or args.config2) else 0)
     t2 = time.perf_counter()
     out = tm.timings()
     out.update(setup_wall_s=t1 - t0, run_wall_s=t2 - t1,
                steps_per_s=p.T / (out["run_ms"] / 1e3) if out["run_ms"] > 0 else None)
     out.update(form=args.form, n=args.n, T=args.T, precision=args.precision, refine=args.refine,
-               launches=eddy.launch_count())
+               setup_launches=setup_launches, launches=eddy.launch_count())
     print(json.dumps(out))
 
 
