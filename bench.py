@@ -337,6 +337,29 @@ def our_arm(args) -> None:
                "setup_h2d_bytes": 8 * (2 * n * n + (m + S + m + P) * n),
                "note": "modal form via ThetaMethod with numpy host arrays; run H2D/D2H inside"}
 
+    # precision variants of the modal form on the same workload, error stated against the
+    # FP64 run just above (one run each, outside the timed region)
+    variants = None
+    if rank == 0 and e2e is not None:
+        def rel(a, b):
+            nb = float(np.linalg.norm(b))
+            return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0))
+        try:
+            variants = {}
+            for prec in ("bf16x3", "bf16"):
+                hv = eddy.ThetaMethod("modal", p.theta, p.dt, device=local,
+                                      stream=stream.cuda_stream, precision=prec)
+                hv.setup(p.L, p.R, p.E if m else None, p.M if S else None, p.MD if m else None, p.C)
+                pv, sv = hv.run(T, src_h, iD_h, stride)
+                tv = hv.timings()
+                hv.close()
+                variants["modal_" + prec] = {
+                    "steps_per_s": T / (tv["run_ms"] / 1e3), "setup_s": tv["setup_ms"] / 1e3,
+                    "probe_rel_err_vs_fp64": rel(pv, pr),
+                    "snapshot_rel_err_vs_fp64": rel(sv, sn) if nsnap else None}
+        except Exception as ex:  # noqa: BLE001 - the main line must still be printed
+            variants = {"error": str(ex)[:300]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -373,6 +396,7 @@ def our_arm(args) -> None:
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "precision_variants": variants,
         "gpu_launches": launches,
         "clocks": clk,
     }
