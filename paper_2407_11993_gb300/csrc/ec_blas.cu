@@ -130,20 +130,6 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int64_t M, int64_t N, int64_
   gemm_tile<TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, tm, tn);
 }
 
-// Block-diagonal batch: group z covers rows/cols [z*bs, min((z+1)*bs, n)) of
-// three n x n matrices; C_z = A_z B_z.
-__global__ void __launch_bounds__(256) dgemm_grouped_kernel(int64_t n, int64_t bs, const double* A,
-                                                            const double* B, double* C, int64_t ld,
-                                                            const DevStatus* st) {
-  if (failed(st)) return;
-  const int64_t s0 = (int64_t)blockIdx.z * bs;
-  const int64_t nb = (n - s0) < bs ? (n - s0) : bs;
-  if ((int64_t)blockIdx.x * GEMM_TILE >= nb || (int64_t)blockIdx.y * GEMM_TILE >= nb) return;
-  const int64_t off = s0 + s0 * ld;
-  gemm_tile<0, 0>(nb, nb, nb, 1.0, A + off, ld, B + off, ld, 0.0, C + off, ld, 0, blockIdx.x,
-                  blockIdx.y);
-}
-
 // Split-K partial products for C = A^T B with a short output (M <= 64 rows): slice z of
 // the K range [z kc, (z+1) kc) goes to ws + z M N (ld M).
 __global__ void __launch_bounds__(256) dgemm_tn_split_kernel(int64_t M, int64_t N, int64_t K,
@@ -256,16 +242,6 @@ __global__ void __launch_bounds__(256) potf2_diag_kernel(double* A, int64_t lda,
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     int r = idx % NB, c = idx / NB;
     Dinv[idx] = (r < kb && c < kb && r >= c) ? X[c * 65 + r] : 0.0;
-  }
-}
-
-__global__ void symmetrize_avg_kernel(int64_t n, double* A, int64_t lda) {
-  const int64_t c = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r < n && c < n && r > c) {
-    const double v = 0.5 * (A[r + c * lda] + A[c + r * lda]);
-    A[r + c * lda] = v;
-    A[c + r * lda] = v;
   }
 }
 
@@ -437,13 +413,6 @@ void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double
     dgemm_kernel<1, 1><<<grid, 256, 0, ::ec::counted(s)>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
 }
 
-void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,
-                   const double* B, double* C, int64_t ld, const DevStatus* st) {
-  if (groups <= 0) return;
-  const unsigned t = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
-  dgemm_grouped_kernel<<<dim3(t, t, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, A, B, C, ld, st);
-}
-
 int dgemm_tn_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = ((M + GEMM_TILE - 1) / GEMM_TILE) * ((N + GEMM_TILE - 1) / GEMM_TILE);
   int64_t sp = (4 * (int64_t)num_sms() + tiles - 1) / tiles;
@@ -532,20 +501,6 @@ void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf
   }
 }
 
-void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* Lf, int64_t ldl,
-                        const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
-  for (int64_t k = 0; k < n; k += NB) {
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    const double* Dk = Dinv + (k / NB) * NB * NB;
-    double* Bk = B + k * ldb;
-    dgemm(s, N_, T_, nrows, kb, kb, 1.0, Bk, ldb, Dk, NB, 0.0, Bk, ldb, 0, st);
-    const int64_t rest = n - k - kb;
-    if (rest > 0)  // B[:, k+kb:] -= B_k L[k+kb:, k:k+kb]^T
-      dgemm(s, N_, T_, nrows, rest, kb, -1.0, Bk, ldb, Lf + (k + kb) + k * ldl, ldl, 1.0,
-            B + (k + kb) * ldb, ldb, 0, st);
-  }
-}
-
 // Lower triangle of B Lf^{-T} for a square B (n x n) whose product is symmetric (the
 // two-sided reduction C^{-1} L C^{-T}): block column k needs only rows >= k, and the
 // trailing update only the lower triangle of the trailing block, a third of the
@@ -568,12 +523,6 @@ void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda) {
   dim3 blk(32, 8);
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
   symmetrize_kernel<<<grid, blk, 0, ::ec::counted(s)>>>(n, A, lda);
-}
-
-void symmetrize_avg(cudaStream_t s, int64_t n, double* A, int64_t lda) {
-  dim3 blk(32, 8);
-  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 7) / 8));
-  symmetrize_avg_kernel<<<grid, blk, 0, ::ec::counted(s)>>>(n, A, lda);
 }
 
 void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,

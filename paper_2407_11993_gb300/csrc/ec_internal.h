@@ -27,6 +27,9 @@ enum Op { N_ = 0, T_ = 1 };
 // ---- FP64 dense kernels (ec_blas.cu); all column-major -------------------
 // C[MxN] = alpha op(A) op(B) + beta C.  tri = 1 restricts work to the lower
 // triangle of C (tiles above the diagonal skipped, diagonal tiles masked).
+// Products with at most 16 columns (or, for A^T B, at most 16 rows) go to streaming
+// kernels instead of 64 x 64 tiles, and a last column tile of at most 16 columns is
+// split off the same way (no FMAs spent on padding).
 void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
            double* C, int64_t ldc, int tri, const DevStatus* st);
@@ -45,11 +48,6 @@ void dgemm_tn_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, const doubl
 void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* Qin,
                   const double* Wm, double* Qout, int64_t ld, const DevStatus* st);
 
-// Block-diagonal batched product: for z < groups, the bs x bs diagonal block z
-// (clipped at n) of C = A B, all three n x n with leading dimension ld.
-void dgemm_grouped(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* A,
-                   const double* B, double* C, int64_t ld, const DevStatus* st);
-
 // Blocked right-looking Cholesky of the lower triangle of A (n x n, ld lda), in
 // place.  Dinv receives, per NB block, the inverse of the diagonal block of the
 // factor (NB x NB column-major, zero above the diagonal).  A non-positive pivot
@@ -62,11 +60,6 @@ void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac
 // B <- Lfac^{-T} B  (left, lower factor, transposed = upper solve).
 void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac, int64_t ldl,
                        const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
-// B <- B Lfac^{-T}  (right side, lower factor transposed); B is nrows x n.
-void trsm_right_lower_t(cudaStream_t s, int64_t nrows, int64_t n, const double* Lfac,
-                        int64_t ldl, const double* Dinv, double* B, int64_t ldb,
-                        const DevStatus* st);
-
 // Lower triangle of B <- B Lfac^{-T} for square B whose result is symmetric
 // (n x n); the strict upper triangle is not written.
 void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lfac, int64_t ldl,
@@ -74,8 +67,6 @@ void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lfac, int64
 
 // Symmetrise: copy the lower triangle onto the upper one.
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda);
-// A <- (A + A^T) / 2.
-void symmetrize_avg(cudaStream_t s, int64_t n, double* A, int64_t lda);
 // A <- A + alpha B on the lower triangle (n x n).
 void add_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, const double* B, int64_t ldb,
                double alpha);
