@@ -317,6 +317,22 @@ def our_arm(args) -> None:
     except (OSError, ValueError):
         pass
 
+    # FP64-pipe rooflines of the modal setup's dominant phases, from their event-timed
+    # durations and the algorithmic flops of the algorithms used: reduction N^3 + N^3/3
+    # (left solve, lower-triangle right solve), tridiagonalisation 2 x (2/3) N^3 FMA
+    # (symmetric product + lower-triangle rank-2 update), back-transformation 2N^3 + N^3
+    # (blocked Householder application + triangular solve)
+    nf = float(n0)
+    setup_rooflines = {}
+    for ph, fl in (("reduce_ms", 4.0 / 3.0 * nf ** 3), ("tridiag_ms", 4.0 / 3.0 * nf ** 3),
+                   ("backtransform_ms", 3.0 * nf ** 3)):
+        ms_ph = mean(ph, "modal")
+        if ms_ph > 0:
+            tf = fl / (ms_ph * 1e-3) / 1e12
+            setup_rooflines[ph[:-3]] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS,
+                                        "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+                                        "algorithmic_flop": fl}
+
     # end to end through the public API with host buffers (modal form)
     e2e = None
     if True:
@@ -394,6 +410,7 @@ def our_arm(args) -> None:
                   "phases_ms": {k: mean(k, "plain") for k in ("elim_ms", "factor_ms")},
                   "fwd_solve_ms": fwd_ms, "bwd_solve_ms": bwd_ms},
         "roofline": roofline,
+        "setup_rooflines": setup_rooflines,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "precision_variants": variants,
