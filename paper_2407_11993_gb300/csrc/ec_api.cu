@@ -423,7 +423,10 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   if (m >= n) return EC_ERR_SHAPE;
   if (c->cfg.precision == EC_PREC_FP32 && m > 0) return EC_ERR_UNSUPPORTED;
   const bool indep = c->cfg.rhs_mode != EC_RHS_SUM;
-  if (m > MAXM || (!indep && s > 64) || p + 2 * m > MAXD) return EC_ERR_UNSUPPORTED;
+  const bool paired = c->cfg.rhs_mode == EC_RHS_PAIRED;
+  // (paired read-out computes each trajectory's own probe directly: no per-step dot
+  // products, so no limit on the number of coils / probe rows)
+  if (m > MAXM || (!indep && s > 64) || (!paired && p + 2 * m > MAXD)) return EC_ERR_UNSUPPORTED;
   if (indep && (m != 0 || s < 1 || s > 65535)) return EC_ERR_UNSUPPORTED;
   if (c->cfg.rhs_mode == EC_RHS_PAIRED && p != s) return EC_ERR_SHAPE;
   cudaSetDevice(c->cfg.device);
@@ -432,7 +435,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   c->last_info = -1;
   c->tim = ec_timing{};
   c->n = n; c->m = (int)m; c->S = (int)s; c->P = (int)p; c->n0 = n - m;
-  c->D = c->P + 2 * c->m;
+  c->D = paired ? 0 : c->P + 2 * c->m;
   const int64_t n0 = c->n0;
   const size_t nn = (size_t)n * n;
   EventTimer whole(c->stream);
@@ -508,7 +511,7 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   EC_TRY(alloc(&c->dGsrc, (size_t)n0 * (2 * c->m + c->S > 0 ? 2 * c->m + c->S : 1)));
   EC_TRY(alloc(&c->dDmat, (size_t)n0 * (c->D > 0 ? c->D : 1)));
   form_sources(c);
-  if (p > 0) copy_matrix(c->stream, n0, p, c->dC + c->m, n, c->dDmat, n0);
+  if (p > 0 && c->D > 0) copy_matrix(c->stream, n0, p, c->dC + c->m, n, c->dDmat, n0);
   if (m > 0) {
     copy_matrix(c->stream, n0, c->m, c->dV + c->m, n, c->dDmat + n0 * p, n0);
     copy_matrix(c->stream, n0, c->m, c->dWR + c->m, n, c->dDmat + n0 * (p + c->m), n0);

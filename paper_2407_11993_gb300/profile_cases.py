@@ -69,6 +69,33 @@ def batch_case(args) -> dict:
             "batch_equals_sequential_bitwise": bool(same), "launches": eddy.launch_count()}
 
 
+def coil_scan_case(args) -> dict:
+    """Independent coil excitations (paired read-out: each coil's own pickup) on one
+    setup: plain and modal forms, T steps each (plain: --plain-T steps)."""
+    import time
+
+    from paper_2407_11993_gb300 import eddy
+    from workloads import synth
+
+    T = max(args.T, args.plain_T)
+    p = synth.coil_scan(args.n, T, n_side=args.coil_side, dt=1e-6)
+    S = p.M.shape[1]
+    out = {"n": args.n, "rhs": S, "T_modal": args.T, "T_plain": args.plain_T}
+    for form, steps in (("plain", args.plain_T), ("modal", args.T)):
+        tm = eddy.ThetaMethod(form, p.theta, p.dt, rhs="paired")
+        t0 = time.perf_counter()
+        tm.setup(p.L, p.R, None, p.M, None, p.C)
+        t1 = time.perf_counter()
+        probes, _ = tm.run(steps, p.src[:, :steps + 1], None, 0)
+        tim = tm.timings()
+        tm.close()
+        out[form] = {"setup_s": t1 - t0, "run_ms": tim["run_ms"],
+                     "steps_per_s": steps / (tim["run_ms"] / 1e3),
+                     "rhs_steps_per_s": S * steps / (tim["run_ms"] / 1e3)}
+        out[form + "_probes_head"] = probes[:2, :, :3].tolist()
+    return out
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--form", choices=["plain", "modal"], default="plain")
@@ -85,6 +112,10 @@ def main() -> None:
                     help="the N=8,192 electrode recipe (2 electrodes, 1 A step, 16 pickups, "
                          "dt = 0.5 us, snapshots every 100 steps) at size --n")
     ap.add_argument("--batch", type=int, default=0, help="uneven plain-form instances (ec_batch_run)")
+    ap.add_argument("--coil-scan", action="store_true",
+                    help="coil_side^2 independent coil excitations on one setup, both forms")
+    ap.add_argument("--coil-side", type=int, default=16)
+    ap.add_argument("--plain-T", type=int, default=20)
     ap.add_argument("--nmin", type=int, default=1024)
     ap.add_argument("--nmax", type=int, default=12288)
     args = ap.parse_args()
@@ -95,6 +126,9 @@ def main() -> None:
     build.build()
     if args.batch:
         print(json.dumps(batch_case(args)))
+        return
+    if args.coil_scan:
+        print(json.dumps(coil_scan_case(args)))
         return
     if args.config4:
         p = synth.config4(T=args.T, n=args.n)

@@ -41,14 +41,17 @@ def test_independent_coils_with_probe_grid(eddy, form):
 
 
 @pytest.mark.parametrize("form", ["plain", "modal"])
-def test_paired_self_pickup(eddy, form):
-    """Config 3 read-out: trajectory r is read by its own coil (C = M^T)."""
-    p = synth.coil_scan(256, T=25, n_side=3)
+@pytest.mark.parametrize("side", [3, 9])
+def test_paired_self_pickup(eddy, form, side):
+    """Config 3 read-out: trajectory r is read by its own coil (C = M^T); 81 coils is
+    past the 64 probe rows of the summed mode (paired read-out has no such limit)."""
+    p = synth.coil_scan(256, T=25, n_side=side)
+    S = side * side
     tm = eddy.ThetaMethod(form, p.theta, p.dt, rhs="paired")
     tm.setup(p.L, p.R, None, p.M, None, p.C)
     probes, _ = tm.run(p.T, p.src, None, 0)
-    assert probes.shape == (9, 1, p.T)
-    for r in range(9):
+    assert probes.shape == (S, 1, p.T)
+    for r in sorted({0, S // 2, S - 1}):
         ref = per_coil_oracle(p, r)
         assert rel(probes[r, 0], ref.probes[r]) < TOL, r
 
