@@ -40,6 +40,7 @@ WORKLOADS = {
                            "theta=1/2, T=2000, FP64"),
 }
 DEFAULT_WORKLOAD = "n8192_electrodes"
+METRIC = "modal theta-steps/s (setup s alongside), modal vs Cholesky theta-method"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 
 
@@ -172,7 +173,7 @@ def reference_arm(args) -> None:
     value = T_sample / per
     w = WORKLOADS[args.workload]
     line = {
-        "impl": "reference", "metric": "modal theta-steps/s (setup s alongside)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -391,7 +392,7 @@ def our_arm(args) -> None:
         return
     w = WORKLOADS[args.workload]
     line = {
-        "metric": "modal theta-steps/s (setup s alongside), modal vs Cholesky theta-method",
+        "metric": METRIC,
         "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
