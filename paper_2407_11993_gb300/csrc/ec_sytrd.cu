@@ -275,8 +275,10 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
     const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;
     p_kernel<<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(n, j, v, tau, partial, (int)nchunk,
                                                          colpart, w, dots, counter);
-    dim3 g2((unsigned)((len + 255) / 256 < 8 ? (len + 255) / 256 : 8),
-            (unsigned)(len < 4096 ? len : 4096));
+    // a few CTAs per SM, each sweeping many columns: the per-column work of the lower
+    // triangle is too small to amortise one CTA launch per column
+    const int64_t gy = len < 4 * (int64_t)sms ? len : 4 * (int64_t)sms;
+    dim3 g2((unsigned)((len + 255) / 256 < 4 ? (len + 255) / 256 : 4), (unsigned)gy);
     syr2_kernel<<<g2, 256, 0, ::ec::counted(s)>>>(n, A, lda, j, v, w, tau);
   }
   tail_kernel<<<1, 1, 0, ::ec::counted(s)>>>(n, A, lda, d, e);
