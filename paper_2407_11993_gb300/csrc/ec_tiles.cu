@@ -175,15 +175,16 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
   // ---- consumers ------------------------------------------------------------
   // Warp w = (h, q): lane l owns output row (forward) / column (transposed)
   // h * 32 + l of the tile and sums over the 16 inner indices q * 16 .. q * 16 + 15
-  // with 4 independent accumulators.  Each (unit, q) writes its own partial row,
+  // with 2 independent accumulators.  Each (unit, q) writes its own partial row,
   // so no sum crosses lanes or warps inside the kernel (on GB300 an FP64 add costs
   // as much as an FMA: a shuffle reduction per unit would double the FP64 work).
   const int h = warp & 1, q = warp >> 1;
   const int o = h * 32 + lane;     // output index within the tile
   // (FP64 factor: FP64 arithmetic; FP32 factor: FP32 products and sums within a unit)
-  WT acc[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) acc[k] = WT(0);
+  // Two accumulators: the unit's closing add is then one DADD per lane (each DADD costs
+  // the FP64 pipe a DFMA slot); two chains per lane and two warps per SMSP already
+  // cover the DFMA latency at GB300's FP64 issue rate.
+  WT acc[2] = {WT(0), WT(0)};
   for (int64_t it = 0;; ++it) {
     const int s = (int)(it % ST);
     const uint32_t ph = (uint32_t)((it / ST) & 1);
@@ -191,8 +192,7 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
     const Meta m = sm.meta[s];
     if (m.flags & F_END) break;
     if (m.flags & F_FIRST) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = WT(0);
+      acc[0] = acc[1] = WT(0);
     }
     const WT* Wt = sm.W[s];
     using WT2 = typename std::conditional<sizeof(WT) == 8, double2, float2>::type;
@@ -209,13 +209,13 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
         w0 = Wt[o * TB + (i0 ^ o)];
         w1 = Wt[o * TB + (i1 ^ o)];
       }
-      acc[(2 * k2) & 3] = fma(w0, v.x, acc[(2 * k2) & 3]);
-      acc[(2 * k2 + 1) & 3] = fma(w1, v.y, acc[(2 * k2 + 1) & 3]);
+      acc[0] = fma(w0, v.x, acc[0]);
+      acc[1] = fma(w1, v.y, acc[1]);
     }
     __syncwarp();
     if (lane == 0) dev::mbar_arrive(&sm.empty[s]);
     if (m.flags & F_LAST) {
-      m.out[q * m.npad + o] = double((acc[0] + acc[1]) + (acc[2] + acc[3]));
+      m.out[q * m.npad + o] = double(acc[0] + acc[1]);
     }
   }
 }
