@@ -12,8 +12,9 @@
  * with the theta-method of Sec. 3.3, in one of two forms:
  *
  *   EC_FORM_PLAIN  Sec. 3.3.1, Eq. time_integration: Z = L_i + theta dt R_i is
- *                  factored once, Z = C C^T, and every step does a forward and a
- *                  backward substitution.
+ *                  factored once, Z = C C^T, and every step solves with C and C^T
+ *                  (by default as two products with the inverted factor C^{-1},
+ *                  EC_SOLVE_INVERSE; by substitution with EC_SOLVE_SUBSTITUTION).
  *   EC_FORM_MODAL  Sec. 3.2 (Eq. generalized_eigenvalues_discrete,
  *                  modal_decomposition_discrete) and Sec. 3.3.2: the pencil
  *                  L_i u = tau R_i u is solved once; every mode then follows a
@@ -204,8 +205,7 @@ EC_API ec_status ec_set_step(ec_ctx* ctx, double theta, double dt);
 EC_API ec_status ec_run(ec_ctx* ctx, int64_t T, const double* src, const double* iD,
                         double* probes, int64_t snap_stride, double* snaps, int mem);
 
-/* Batched instances (spec batching; no counterpart in the paper, which runs one
- * problem).  Advances `count` independent plain-form problems of different sizes by T
+/* Batched instances (no counterpart in the paper, which runs one problem at a time).  Advances `count` independent plain-form problems of different sizes by T
  * steps each, as if ec_run were called on each (same arguments per instance, one common
  * snap_stride), in one pass per step:
  *   - every instance's tile products go into one work list (all instances' units,
@@ -320,12 +320,16 @@ EC_API ec_status ec_set_mode_count(ec_ctx* ctx, int64_t n_keep);
 EC_API ec_status ec_phasors(int64_t T, int64_t p, const double* y, double t0, double dt,
                             int64_t nf, const double* freqs, double* out, int mem);
 
+/* Copy the context's phase timings (see ec_timing) into *out. */
 EC_API ec_status ec_timings(ec_ctx* ctx, ec_timing* out);
 /* Wait for the context's stream and report any error raised inside kernels. */
 EC_API ec_status ec_sync(ec_ctx* ctx);
 /* Extra information about the last error (global pivot index for EC_ERR_NOT_SPD). */
 EC_API int64_t ec_last_info(const ec_ctx* ctx);
+/* Static English text for a status code (never NULL). */
 EC_API const char* ec_error_string(ec_status status);
+/* Wait for the context's stream, free everything the context owns, and the context
+ * itself.  NULL is a no-op. */
 EC_API void ec_destroy(ec_ctx* ctx);
 
 /* Number of CUDA kernels the library has launched in this process, over all
