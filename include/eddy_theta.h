@@ -67,7 +67,7 @@ typedef enum ec_status {
   EC_ERR_TIMEOUT = 7,      /* a bounded inter-block wait inside a kernel gave up */
   EC_ERR_STATE = 8,        /* call out of order (e.g. ec_run before ec_setup) */
   EC_ERR_NOT_CONVERGED = 9,/* an iterative eigen step did not converge */
-  EC_ERR_UNSUPPORTED = 10  /* valid request this build does not implement */
+  EC_ERR_UNSUPPORTED = 10  /* valid request outside what the library implements */
 } ec_status;
 
 typedef enum ec_form { EC_FORM_PLAIN = 0, EC_FORM_MODAL = 1 } ec_form;
