@@ -450,12 +450,10 @@ void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const d
 }
 
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr_set{0};
   const int smem = 2 * 64 * 65 * (int)sizeof(double);
-  if (!attr) {
+  if (first_on_device(attr_set))
     cudaFuncSetAttribute(potf2_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
   for (int64_t k = 0; k < n; k += NB) {
     const int kb = (int)((n - k) < NB ? (n - k) : NB);
     double* Akk = A + k + k * lda;

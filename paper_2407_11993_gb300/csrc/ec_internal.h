@@ -2,6 +2,7 @@
 // theta-method library.  Not part of the C ABI (that is include/eddy_theta.h).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -107,6 +108,16 @@ void sum_partials(cudaStream_t s, int64_t n, int nin, const double* part, double
 void wait_timeout_probe(cudaStream_t s, int* flag, long long spin_limit, DevStatus* st);
 
 int num_sms();
+
+// True the first time it is called with `mask` while a given device is current (one bit
+// per device; devices past 63 always get true).  For per-device one-time setup such as
+// raising a kernel's dynamic shared-memory limit.
+inline bool first_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  const unsigned long long bit = 1ull << dev;
+  return (mask.fetch_or(bit) & bit) == 0;
+}
 
 // Every kernel launch of the library passes its stream through counted(), which
 // increments the process-wide launch counter reported by ec_launch_count().

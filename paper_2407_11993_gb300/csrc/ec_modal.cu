@@ -615,11 +615,9 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   const int ncs = a.ncoef > 0 ? a.ncoef : 1;
   const size_t smem1 = sizeof(double) * (size_t)(2 * TS * ncs);
   const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + Pout * MT);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set))
     cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   for (int64_t k0 = 0; k0 < T; k0 += SUPER) {
     a.k0 = k0;
     a.kn = (T - k0) < SUPER ? (T - k0) : SUPER;

@@ -279,11 +279,9 @@ ec_status tc_gemm_bf16(cudaStream_t s, int64_t M, int64_t N, int64_t K, double a
   if (M > (1ll << 31) - TM || N > (1ll << 31) - TN || K > (1ll << 31)) return EC_ERR_UNSUPPORTED;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, lda, TM) || !make_map(&mb, B, N, K, ldb, TN)) return EC_ERR_CUDA;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set))
     cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    attr = true;
-  }
   dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((N + TN - 1) / TN));
   tc_gemm_kernel<<<grid, 128, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb, (int)M, (int)N, (int)K,
                                                               alpha, beta, C, ldc, st);
