@@ -209,7 +209,7 @@ class ThetaMethod:
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
                  integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0,
-                 refine_steps: int = 0):
+                 refine_steps: int = 0, log_path: str | None = None):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
@@ -228,6 +228,10 @@ class ThetaMethod:
                         {"sum": 0, "independent": 1, "paired": 2}[rhs], int(refine_steps),
                         int(tile_variant))
         self.rhs = rhs
+        self.log_path = log_path
+        self._desc = {"form": form, "theta": float(theta), "dt": float(dt), "solver": solver,
+                      "precision": precision, "integrator": integrator, "rhs": rhs,
+                      "refine_steps": int(refine_steps), "device": int(device)}
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h
@@ -283,6 +287,10 @@ class ThetaMethod:
         pn = c_void_p(snaps.data_ptr() if mem == EC_MEM_DEVICE else snaps.ctypes.data) if nsnap else None
         check(lib().ec_run(self._h, int(T), ps, pi, pp, int(snap_stride) if nsnap else 0, pn, mem),
               "ec_run", self._h)
+        if self.log_path:
+            append_run_record(self.log_path, dict(self._desc, n=self.n, m=self.m, S=self.S,
+                                                  P=self.P, T=int(T), snap_stride=int(snap_stride)),
+                              self.timings())
         if nt > 1:
             # (T, nt, pout) -> (nt, pout, T); (nsnap, nt, n) -> (nt, n, nsnap)
             return probes.transpose(1, 2, 0) if mem != EC_MEM_DEVICE else probes.permute(1, 2, 0), \
@@ -369,6 +377,21 @@ class ThetaMethod:
 
 
 EC_BATCH_MAX = 64
+
+
+def append_run_record(path: str, config: dict, timings: dict) -> dict:
+    """Append one JSON line describing a run (configuration, sizes, the library's phase
+    timings and the derived steps/s) to ``path``; returns the record."""
+    import json
+    import time
+
+    rec = {"time": time.time(), "config": config, "timings": timings}
+    run_ms = float(timings.get("run_ms") or 0.0)
+    steps = int(timings.get("run_steps") or 0)
+    rec["steps_per_s"] = steps / (run_ms / 1e3) if run_ms > 0 else None
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
+    return rec
 
 
 def batch_run(models, T: int, srcs=None, iDs=None, snap_stride: int = 0):
