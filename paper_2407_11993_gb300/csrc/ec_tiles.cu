@@ -663,7 +663,7 @@ void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, D
   for (int i = 0; i < B.count; ++i) {
     const TilePlan& p = *inst[i].plan;
     a.d[i] = TileDesc{inst[i].Wp, inst[i].b, inst[i].part1, p.nblk, p.npad, p.chunk};
-    sa.d[i] = SumDesc{inst[i].part1, inst[i].y, p.n, p.nblk, p.npad, p.chunk};
+    sa.d[i] = SumDesc{inst[i].part1, inst[i].y, p.n, p.nblk, p.npad, p.chunk, nullptr};
   }
   a.units = B.units_fwd;
   a.nunits = B.nunits_fwd;
@@ -675,7 +675,7 @@ void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, D
   for (int i = 0; i < B.count; ++i) {
     const TilePlan& p = *inst[i].plan;
     a.d[i] = TileDesc{inst[i].Wp, inst[i].y, inst[i].part2, p.nblk, p.npad, p.chunk};
-    sa.d[i] = SumDesc{inst[i].part2, inst[i].x, p.n, p.nblk, p.npad, p.chunk};
+    sa.d[i] = SumDesc{inst[i].part2, inst[i].x, p.n, p.nblk, p.npad, p.chunk, nullptr};
   }
   a.units = B.units_bwd;
   a.nunits = B.nunits_bwd;
