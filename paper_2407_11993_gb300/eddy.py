@@ -199,7 +199,7 @@ def solve_inverse_noalloc(Winv, b, x, stream=None, n: int | None = None) -> None
 class ThetaMethod:
     """One context of the C library: setup once, then run / continue.
 
-    Array conventions follow the oracle: L, R (N, N); E (m, N); M (N, S) coil
+    Array conventions (row-major numpy shapes): L, R (N, N); E (m, N); M (N, S) coil
     mutual columns; MD (N, m); C (P, N); src (S, T+1); iD (m, T+1).  Results:
     probes (P, T) and snaps (N, T // stride).  ``mem`` selects host numpy
     arrays or CUDA torch tensors for inputs and outputs alike.
