@@ -21,3 +21,15 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_clock_summary_reads_throttle_reasons():
+    import bench
+    lines = ["2070, 2070, 812.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "1980, 2070, 1391.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "2070, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "garbage line", "N/A, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = bench.ClockSampler.summarize(lines)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler.summarize([])["sm_mhz"] is None
