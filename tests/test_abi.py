@@ -49,3 +49,44 @@ def test_binding_rejects_bad_config_without_gpu():
     with pytest.raises(eddy.EcError) as e:
         eddy.ThetaMethod("plain", theta=1.5, dt=1e-6)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("kwargs,code", [
+    (dict(form="plain", precision="bf16"), 10),                    # BF16 variants: modal only
+    (dict(form="modal", precision="fp32"), 10),                    # FP32 factor: plain only
+    (dict(form="plain", precision="fp32", solver="substitution"), 10),
+    (dict(form="plain", precision="fp32", rhs="independent"), 10),
+    (dict(form="plain", integrator="exact"), 10),                  # exact integrator: modal only
+    (dict(form="plain", rhs="paired", solver="substitution"), 10),
+    (dict(form="plain", precision="fp32", refine_steps=9), 1),     # 0 .. 8 sweeps
+    (dict(form="modal", dt=0.0), 1),
+    (dict(form="modal", theta=-0.1), 1),
+])
+def test_config_combinations_checked_without_gpu(kwargs, code):
+    """ec_create rejects unsupported or invalid configurations before touching the GPU."""
+    from paper_2407_11993_gb300 import build, eddy
+    build.build()
+    kw = dict(theta=0.5, dt=1e-6)
+    kw.update(kwargs)
+    form = kw.pop("form")
+    with pytest.raises(eddy.EcError) as e:
+        eddy.ThetaMethod(form, **kw)
+    assert e.value.code == code
+
+
+def test_entry_points_check_arguments_without_gpu():
+    from paper_2407_11993_gb300 import build, eddy
+    build.build()
+    so = eddy.lib()
+    # a batch needs 1 .. EC_BATCH_MAX contexts
+    assert so.ec_batch_run(None, 0, 1, None, None, None, 0, None, 0) == 1
+    hs = (ctypes.c_void_p * 65)()
+    assert so.ec_batch_run(hs, 65, 1, None, None, None, 0, None, 0) == 1
+    # the allocation-free solve rejects sizes past its scratch before any CUDA call
+    dummy = ctypes.c_void_p(16)
+    assert so.ec_solve_inverse_noalloc(eddy.NOALLOC_MAX_N + 1, dummy, eddy.NOALLOC_MAX_N + 1,
+                                       dummy, dummy, None) == 2
+    assert so.ec_solve_inverse_noalloc(0, dummy, 1, dummy, dummy, None) == 1
+    # null context
+    assert so.ec_run(None, 1, None, None, None, 0, None, 0) == 1
+    assert so.ec_state_size(None) == 0
