@@ -186,7 +186,9 @@ EC_API ec_status ec_create(ec_ctx** out, const ec_config* cfg);
  *            the coils induce V_0 = -M^T di_0/dt.  M may be NULL if s = 0.
  *   MD       electrode-source mutuals, m x n (row j: M^D column j), or NULL for zero.
  *   p, C     probe rows, p x n; probe outputs are y = C I.  C may be NULL if p = 0.
- * Copies every input; the caller's buffers are not retained.  Resets the state to I = 0. */
+ * Copies every input; the caller's buffers are not retained.  Resets the state to I = 0.
+ * A NaN or infinite entry in L, R, E, M, MD or C is refused with EC_ERR_ARG before any
+ * factorisation (ec_last_info: 0 L, 1 R, 2 E, 3 M, 4 MD, 5 C). */
 EC_API ec_status ec_setup(ec_ctx* ctx, int64_t n, const double* L, const double* R, int64_t m,
                           const double* E, int64_t s, const double* M, const double* MD,
                           int64_t p, const double* C, int mem);
@@ -264,16 +266,19 @@ EC_API ec_status ec_get_inverse_factor(ec_ctx* ctx, double* W, int mem);
  * cudaMalloc -- and therefore cannot create a context.
  *
  *   n        system size, 1 <= n <= EC_NOALLOC_MAX_N (larger n: EC_ERR_SHAPE, nothing runs)
- *   Winv     device pointer, n x n column-major with leading dimension ldw >= n; only
- *            the lower triangle is read (the 64 x 64 diagonal blocks must hold zeros
- *            above the diagonal, as ec_get_inverse_factor returns them)
+ *   Winv     device pointer, n x n column-major with leading dimension ldw >= n (at
+ *            least ldw (n - 1) + n elements); the lower block triangle is read in
+ *            64 x 64 tiles, including the whole diagonal tiles, which must hold zeros
+ *            above the diagonal (as ec_get_inverse_factor returns them); blocks above
+ *            the block diagonal are never read
  *   b, x     device pointers of length n (b is read, x written; they may alias)
  *   stream   cudaStream_t to enqueue on (NULL = legacy default stream)
  * Allocates nothing: no cudaMalloc or cudaFree is called.  Its scratch is a
  * fixed-size device array inside the library (about 1.1 MB, held on every GPU
  * that loads the library until the process exits).  The first call on a device
- * looks up that array's device address with the device current; make that first
- * call before any stream capture.  All calls share the array, so calls that may
+ * looks up that array's device address with the device current, and the lookup is
+ * repeated on the first call after the device's context was replaced (for example
+ * by cudaDeviceReset); make that first call before any stream capture.  All calls share the array, so calls that may
  * overlap on the GPU (different streams without ordering) race and corrupt each
  * other's results.  The call is asynchronous: it returns after enqueueing, and
  * reports only argument and launch errors. */
@@ -302,6 +307,22 @@ EC_API ec_status ec_grad(ec_ctx* ctx, int64_t T, const double* src, const double
  * K x N, C is M x N; inputs are rounded to BF16 into temporary buffers.  Synchronous. */
 EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, const double* B,
                               double* C, void* stream);
+
+/* FP64-accurate dense product on the tensor cores (the kernel behind the setup's large
+ * contractions, Sec. 3.2 and Sec. 3.3.1; the paper, which ran ScaLAPACK on CPUs, has no
+ * counterpart):  C = alpha op(A) op(B) + beta C, op(X) = X (t = 0) or X^T (t = 1).
+ * Device pointers, column-major FP64 with leading dimensions lda, ldb, ldc; op(A) is
+ * M x K, op(B) is K x N.  lower = 1 (M = N) updates only the lower triangle of C.
+ * Each row of op(A) and column of op(B) is scaled by a power of two and cut into seven
+ * 8-bit integer slices held exactly in BF16; the slice products (tcgen05, FP32
+ * accumulation kept exact per slice diagonal) are recombined in integer arithmetic.
+ * Error per entry: below 2^-53 sqrt(K) max_k|op(A)_ik| max_k|op(B)_kj| plus one FP64
+ * rounding per 192-long K chunk, comparable to an FP64 GEMM.  Allocates a temporary
+ * workspace (about 14 (M + N) K bytes, in panels beyond 4 GB).  Synchronous. */
+EC_API ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, int64_t K,
+                                      double alpha, const double* A, int64_t lda, const double* B,
+                                      int64_t ldb, double beta, double* C, int64_t ldc, int lower,
+                                      void* stream);
 
 /* Modal form only: selective integration (the decoupled modes can be advanced "in a
  * selective manner", Sec. 2.3).  From now on only the n_keep modes of largest tau are
@@ -340,6 +361,14 @@ EC_API int64_t ec_launch_count(void);
  * nothing sets, with at most spin_limit polls, and stores the status the kernel
  * reported (EC_ERR_TIMEOUT when the bound works) in *code_out. */
 EC_API ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out);
+
+/* Test hook for the out-of-memory paths (failures are made on the host; nothing is
+ * injected on the GPU).  With after >= 0, the library's next `after` device
+ * allocations succeed and every later one reports failure, as cudaMalloc does when
+ * device memory is exhausted: the call that needed it returns EC_ERR_OOM and leaves
+ * the context usable for ec_destroy or a new ec_setup.  after < 0 disarms the hook
+ * (the default).  Process-wide; not for use while other threads call the library. */
+EC_API ec_status ec_selftest_fail_alloc(int64_t after);
 
 #ifdef __cplusplus
 }

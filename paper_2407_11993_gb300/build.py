@@ -60,7 +60,24 @@ def build(verbose: bool = False, force: bool = False) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    build_peaks(force)
     return LIB
+
+
+PEAKS_SRC = os.path.join(CSRC, "peaks", "ec_peaks.cu")
+PEAKS_LIB = os.path.join(BUILD, "libec_peaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The arithmetic-peak probes (FP64 FMA, FP64 mma.sync, FP32 FMA) as their own
+    small library, used by the benchmark for its roofline denominators."""
+    os.makedirs(BUILD, exist_ok=True)
+    if force or _stale(PEAKS_LIB, [PEAKS_SRC]):
+        cmd = [nvcc(), *ARCH, *FLAGS, "-shared", "-o", PEAKS_LIB, PEAKS_SRC, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":

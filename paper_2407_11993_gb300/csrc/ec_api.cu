@@ -98,9 +98,45 @@ struct ec_ctx {
   ModalState* modal = nullptr;
 };
 
+namespace ec {
+// Test hook of ec_selftest_fail_alloc: < 0 disarmed; otherwise the number of
+// allocations that still succeed before every later one reports failure.
+std::atomic<long long> g_fail_alloc_after{-1};
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  long long left = g_fail_alloc_after.load();
+  while (left >= 0) {
+    if (left == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) break;
+  }
+  return cudaMalloc(p, bytes ? bytes : 8);
+}
+}  // namespace ec
 namespace {
 
-cudaError_t dev_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 8); }
+cudaError_t dev_alloc(void** p, size_t bytes) { return device_alloc(p, bytes); }
+
+// Non-finite entries in the copied inputs: the status records EC_ERR_ARG and the
+// input's index (0 L, 1 R, 2 E, 3 M, 4 MD, 5 C) as the info value.
+__global__ void finite_check_kernel(const double* a, int64_t count, int which, DevStatus* st) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!isfinite(a[i])) {
+      if (atomicCAS(&st->code, 0, (int)EC_ERR_ARG) == 0) st->info = which;
+      return;
+    }
+  }
+}
+
+void finite_check(cudaStream_t s, const double* a, int64_t count, int which, DevStatus* st) {
+  if (count <= 0) return;
+  int64_t g = (count + 255) / 256;
+  if (g > (int64_t)num_sms() * 8) g = num_sms() * 8;
+  finite_check_kernel<<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(a, count, which, st);
+}
 
 template <typename T>
 ec_status alloc(T** p, size_t count) {
@@ -456,6 +492,13 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     else cudaMemsetAsync(c->dMD, 0, sizeof(double) * n * m, c->stream);
   }
   EC_TRY(copy_in(c, c->dC, C, (size_t)n * p, mem));
+  // NaN or infinite inputs are refused before any factorisation sees them
+  finite_check(c->stream, c->dL, (int64_t)nn, 0, c->st);
+  finite_check(c->stream, c->dR, (int64_t)nn, 1, c->st);
+  finite_check(c->stream, c->dM, (int64_t)n * s, 3, c->st);
+  if (m > 0 && MD) finite_check(c->stream, c->dMD, (int64_t)n * m, 4, c->st);
+  finite_check(c->stream, c->dC, (int64_t)n * p, 5, c->st);
+  EC_TRY(collect(c));
 
   // CSR of the original R, for the O(nnz) R_i products of the plain step
   {
@@ -483,6 +526,8 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     EC_TRY(alloc(&c->dSm, (size_t)mi * (wcols > mi ? wcols : mi)));
     EC_TRY(alloc(&c->dZm, (size_t)mi * (wcols > mi ? wcols : mi)));
     EC_TRY(copy_in(c, c->dE, E, (size_t)n * mi, mem));
+    finite_check(c->stream, c->dE, (int64_t)n * mi, 2, c->st);
+    EC_TRY(collect(c));
     house_qr(c->stream, n, mi, c->dE, c->dV, c->dT, c->dRrinvT, c->st);
     // WR = R V with the original R, and V^T WR
     dgemm(c->stream, N_, N_, n, mi, n, 1.0, c->dR, n, c->dV, n, 0.0, c->dWR, n, 0, c->st);
@@ -1069,6 +1114,11 @@ ec_status ec_selftest_wait_timeout(long long spin_limit, int* code_out) {
   cudaFree(flag);
   if (e != cudaSuccess) return cuda_status(e);
   *code_out = h.code;
+  return EC_OK;
+}
+
+ec_status ec_selftest_fail_alloc(int64_t after) {
+  ec::g_fail_alloc_after.store(after < 0 ? -1 : (long long)after);
   return EC_OK;
 }
 

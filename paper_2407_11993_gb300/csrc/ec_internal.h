@@ -109,6 +109,11 @@ void wait_timeout_probe(cudaStream_t s, int* flag, long long spin_limit, DevStat
 
 int num_sms();
 
+// Every device allocation the library makes for a context goes through here
+// (cudaMalloc, or a reported failure while the test hook set by
+// ec_selftest_fail_alloc is armed and has run out).
+cudaError_t device_alloc(void** p, size_t bytes);
+
 // True the first time it is called with `mask` while a given device is current (one bit
 // per device; devices past 63 always get true).  For per-device one-time setup such as
 // raising a kernel's dynamic shared-memory limit.

@@ -76,7 +76,7 @@ constexpr int TS = 16;             // steps per shared-memory block of the probe
 constexpr int64_t SUPER = 32768;   // steps per launch group (bounds the partial-sum buffer)
 constexpr int64_t CH_MIN = 1024;   // shortest time chunk; runs up to this length are one chunk
 
-cudaError_t dalloc(void** p, size_t b) { return cudaMalloc(p, b ? b : 8); }
+cudaError_t dalloc(void** p, size_t b) { return device_alloc(p, b); }
 
 template <typename T>
 ec_status alloc_n(T** p, size_t count) {

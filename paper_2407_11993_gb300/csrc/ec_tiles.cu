@@ -398,8 +398,8 @@ void order_units(std::vector<int4>& u, const std::vector<int64_t>& nblk,
 
 ec_status upload_units(const std::vector<int4>& fwd, const std::vector<int4>& bwd, int4** dfwd,
                        int4** dbwd) {
-  if (cudaMalloc((void**)dfwd, sizeof(int4) * fwd.size()) != cudaSuccess ||
-      cudaMalloc((void**)dbwd, sizeof(int4) * bwd.size()) != cudaSuccess) {
+  if (device_alloc((void**)dfwd, sizeof(int4) * fwd.size()) != cudaSuccess ||
+      device_alloc((void**)dbwd, sizeof(int4) * bwd.size()) != cudaSuccess) {
     cudaGetLastError();
     return EC_ERR_OOM;
   }

@@ -191,23 +191,61 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+unsigned long long g_noalloc_ctx[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device; looked up once per
-// device with that device current (host code cannot use the symbol itself).
+// Unique id of the current CUDA context (cuCtxGetId, resolved through the runtime's
+// driver entry-point query so the library needs no link against libcuda).  A
+// cudaDeviceReset replaces the device's primary context, and the new one has a new
+// id.  Returns 0 when the id is unavailable.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (GetIdFn)p;
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, with that device
+// current (host code cannot use the symbol itself).  Set up once per device and
+// context: the address is looked up on the first call on a device and again after
+// the device's context has been replaced (cudaDeviceReset), since the array may then
+// sit at another address.  Without a context id the lookup is repeated every call.
 ec_status noalloc_scratch(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
     cudaGetLastError();
     return EC_ERR_CUDA;
   }
+  // before the first runtime call that needs the device, no context may be current
+  // yet (id 0): the lookup below creates it, and the id is read again afterwards
+  unsigned long long ctx_id = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || ctx_id == 0 || g_noalloc_ctx[dev] != ctx_id) {
     double* p = nullptr;
     if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
+      g_noalloc_ptr[dev] = nullptr;
       return EC_ERR_CUDA;
     }
+    if (ctx_id == 0) ctx_id = current_context_id();
     g_noalloc_ptr[dev] = p;
+    g_noalloc_ctx[dev] = ctx_id;
   }
   *out = g_noalloc_ptr[dev];
   return EC_OK;

@@ -32,7 +32,8 @@ EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "
            "ec_get_state", "ec_set_state", "ec_get_modes", "ec_timings", "ec_sync",
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
            "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
-           "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors", "ec_batch_run")
+           "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors", "ec_batch_run",
+           "ec_selftest_fail_alloc", "ec_gemm_f64_emulated")
 NOALLOC_MAX_N = 8192
 
 
@@ -102,6 +103,9 @@ def lib() -> ctypes.CDLL:
             "ec_set_mode_count": (c_int, [P, c_int64]),
             "ec_phasors": (c_int, [c_int64, c_int64, P, c_double, c_double, c_int64, P, P, c_int]),
             "ec_batch_run": (c_int, [P, c_int, c_int64, P, P, P, c_int64, P, c_int]),
+            "ec_selftest_fail_alloc": (c_int, [c_int64]),
+            "ec_gemm_f64_emulated": (c_int, [c_int, c_int, c_int64, c_int64, c_int64, c_double, P,
+                                             c_int64, P, c_int64, c_double, P, c_int64, c_int, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -159,6 +163,31 @@ def gemm_bf16(A, B, C=None, stream=None):
     return Ct.t()
 
 
+def gemm_f64_emulated(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, ta: bool = False,
+                      tb: bool = False, lower: bool = False, stream=None):
+    """C = alpha op(A) op(B) + beta C to FP64 accuracy on the tensor cores (CUDA float64
+    tensors, any memory order is copied to column-major; returns C as a tensor)."""
+    import torch
+    opA = A.t() if ta else A
+    opB = B.t() if tb else B
+    M, K = opA.shape
+    K2, N = opB.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    # column-major buffers: the memory of X^T in row-major order
+    Acm = A.t().contiguous()          # column-major A (rows x cols of A)
+    Bcm = B.t().contiguous()
+    lda = max(1, A.shape[0])
+    ldb = max(1, B.shape[0])
+    Ct = torch.zeros((N, M), dtype=torch.float64, device=A.device) if C is None else \
+        C.t().contiguous()
+    check(lib().ec_gemm_f64_emulated(int(ta), int(tb), M, N, K, float(alpha),
+                                     c_void_p(Acm.data_ptr()), lda, c_void_p(Bcm.data_ptr()), ldb,
+                                     float(beta), c_void_p(Ct.data_ptr()), max(1, M), int(lower),
+                                     c_void_p(stream or 0)), "ec_gemm_f64_emulated")
+    return Ct.t()
+
+
 def phasors(probes, t0: float, dt: float, freqs):
     """probes (P, T) host array -> (F, P) complex phasors computed on the GPU."""
     y = np.ascontiguousarray(np.asarray(probes, np.float64).T)       # T x P
@@ -181,19 +210,41 @@ def selftest_wait_timeout(spin_limit: int) -> int:
     return out.value
 
 
-def solve_inverse_noalloc(Winv, b, x, stream=None, n: int | None = None) -> None:
+def selftest_fail_alloc(after: int) -> None:
+    """Arm (after >= 0) or disarm (after < 0) the library's out-of-memory test hook."""
+    check(lib().ec_selftest_fail_alloc(int(after)), "ec_selftest_fail_alloc")
+
+
+def solve_inverse_noalloc(Winv, b, x, stream=None, n: int | None = None,
+                          ldw: int | None = None) -> None:
     """x = Winv^T (Winv b) on device tensors without any device allocation.
 
     ``Winv`` is the column-major inverse Cholesky factor as returned by
-    ``ThetaMethod.inverse_factor(mem=EC_MEM_DEVICE)`` (an (n, n) tensor whose
-    memory is C^{-1} in column-major order).  ``stream`` is a raw cudaStream_t.
+    ``ThetaMethod.inverse_factor(mem=EC_MEM_DEVICE)`` (its memory is C^{-1} in
+    column-major order with leading dimension ``ldw``, default n).  ``stream`` is a
+    raw cudaStream_t.  Sizes and devices are checked here, before anything runs:
+    Winv must hold at least ldw (n - 1) + n elements and b, x at least n, and all
+    three must be contiguous float64 tensors on one CUDA device, on which the call
+    then runs.
     """
     n = int(b.shape[0]) if n is None else int(n)
+    ldw = n if ldw is None else int(ldw)
+    if n < 1 or ldw < n:
+        raise ValueError("need 1 <= n <= ldw")
+    for name, t, need in (("Winv", Winv, ldw * (n - 1) + n), ("b", b, n), ("x", x, n)):
+        if not _is_torch(t):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs at least {need}")
+    if not (Winv.device == b.device == x.device):
+        raise ValueError("Winv, b and x must be on one device")
     pw, k1 = _ptr(Winv, EC_MEM_DEVICE)
     pb, k2 = _ptr(b, EC_MEM_DEVICE)
     px, k3 = _ptr(x, EC_MEM_DEVICE)
-    check(lib().ec_solve_inverse_noalloc(n, pw, n, pb, px, c_void_p(stream or 0)),
-          "ec_solve_inverse_noalloc")
+    import torch
+    with torch.cuda.device(b.device):
+        check(lib().ec_solve_inverse_noalloc(n, pw, ldw, pb, px, c_void_p(stream or 0)),
+              "ec_solve_inverse_noalloc")
 
 
 class ThetaMethod:

@@ -90,3 +90,23 @@ def test_entry_points_check_arguments_without_gpu():
     # null context
     assert so.ec_run(None, 1, None, None, None, 0, None, 0) == 1
     assert so.ec_state_size(None) == 0
+
+
+def test_noalloc_binding_checks_sizes_and_devices_without_gpu():
+    """The allocation-free solve's binding refuses short or mismatched tensors before it
+    touches the library (so a short buffer can never reach a kernel)."""
+    import torch
+    from paper_2407_11993_gb300 import eddy
+    n = 100
+    W = torch.zeros(n * n, dtype=torch.float64)
+    b = torch.zeros(n, dtype=torch.float64)
+    with pytest.raises(ValueError):          # Winv shorter than n * n
+        eddy.solve_inverse_noalloc(W[: n * n - 1], b, b)
+    with pytest.raises(ValueError):          # b shorter than the n override
+        eddy.solve_inverse_noalloc(W, b, b, n=n + 1)
+    with pytest.raises(ValueError):          # x too short
+        eddy.solve_inverse_noalloc(W, b, b[:-1])
+    with pytest.raises(ValueError):          # ldw * (n - 1) + n elements needed
+        eddy.solve_inverse_noalloc(W, b, b, ldw=n + 1)
+    with pytest.raises(TypeError):           # host memory is not device memory
+        eddy.solve_inverse_noalloc(W, b, b)

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import exponential as ex
+from parity import rel_snaps, rel_traces
 from workloads import synth
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +32,7 @@ def test_config1_exact(eddy):
     p = synth.config1(T=500)
     ref = ex.run_problem(p)
     _, (probes, _) = run_exact(eddy, p)
-    assert rel(probes, ref.probes) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
 
 
 @pytest.mark.parametrize("n,T", [(65, 40), (300, 80), (700, 2500)])
@@ -39,8 +40,8 @@ def test_electrodes_and_coil_exact(eddy, n, T):
     p = synth.small(n, T=T, seed=n, electrodes=True, coil=True, snap_stride=20, dt=1e-6)
     ref = ex.run_problem(p)
     _, (probes, snaps) = run_exact(eddy, p)
-    assert rel(probes, ref.probes) < TOL
-    assert rel(snaps, ref.snaps) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
+    assert rel_snaps(snaps, ref.snaps) < TOL
 
 
 def test_exact_set_step(eddy):
@@ -51,4 +52,4 @@ def test_exact_set_step(eddy):
     tm.set_step(0.5, q.dt)
     probes, snaps = tm.run(q.T, q.src, q.iD, q.snap_stride)
     ref = ex.run_problem(q)
-    assert rel(probes, ref.probes) < TOL and rel(snaps, ref.snaps) < TOL
+    assert rel_traces(probes, ref.probes) < TOL and rel_snaps(snaps, ref.snaps) < TOL

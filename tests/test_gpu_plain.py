@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import theta as orc
+from parity import rel_snaps, rel_traces
 from workloads import synth
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +48,7 @@ def test_config1_coil_n512(eddy, solver):
     ref = orc.run_problem(p, "plain")
     _, probes, _ = run_gpu(eddy, p, solver=solver)
     assert probes.shape == ref.probes.shape
-    assert rel(probes, ref.probes) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
 
 
 @pytest.mark.parametrize("solver", SOLVERS)
@@ -57,8 +58,8 @@ def test_ragged_sizes_with_electrode_and_coil(eddy, n, solver):
     p = synth.small(n, T=40, seed=n, electrodes=electrodes, coil=True, snap_stride=7)
     ref = orc.run_problem(p, "plain")
     _, probes, snaps = run_gpu(eddy, p, solver=solver)
-    assert rel(probes, ref.probes) < TOL
-    assert rel(snaps, ref.snaps) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
+    assert rel_snaps(snaps, ref.snaps) < TOL
 
 
 def test_two_electrode_rows(eddy):
@@ -73,8 +74,8 @@ def test_two_electrode_rows(eddy):
     p.iD = np.stack([p.iD[0], 0.3 * np.sin(np.arange(31) * 0.2)])
     ref = orc.run_problem(p, "plain")
     _, probes, snaps = run_gpu(eddy, p)
-    assert rel(probes, ref.probes) < TOL
-    assert rel(snaps, ref.snaps) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
+    assert rel_snaps(snaps, ref.snaps) < TOL
     # constraint E I = i_D holds on the GPU snapshots
     assert np.allclose(p.E @ snaps, p.iD[:, 5::5], atol=1e-12)
 
@@ -84,7 +85,7 @@ def test_initial_current_and_zero_source_decay(eddy):
     I0 = np.random.default_rng(3).standard_normal(96)
     ref = orc.run_problem(p, "plain", I0=I0)
     _, probes, snaps = run_gpu(eddy, p, I0=I0)
-    assert rel(snaps, ref.snaps) < TOL
+    assert rel_snaps(snaps, ref.snaps) < TOL
     W = [orc.magnetic_energy(p.L, snaps[:, k]) for k in range(25)]
     assert np.all(np.diff(W) <= 1e-12 * W[0])
 
@@ -132,8 +133,8 @@ def test_config2_electrodes_n8192_first_steps(eddy, config2_ref, solver):
     """N = 8192 with the electrode step, 16 pickups: first 40 steps + snapshots."""
     p, ref = config2_ref
     _, probes, snaps = run_gpu(eddy, p, solver=solver)
-    assert rel(probes, ref.probes) < TOL
-    assert rel(snaps, ref.snaps) < TOL
+    assert rel_traces(probes, ref.probes) < TOL
+    assert rel_snaps(snaps, ref.snaps) < TOL
 
 
 def test_solvers_agree_and_set_step_refactors(eddy):
@@ -148,9 +149,9 @@ def test_solvers_agree_and_set_step_refactors(eddy):
         tm.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
         tm.set_step(q.theta, q.dt)
         probes, snaps = tm.run(q.T, q.src, q.iD, q.snap_stride)
-        assert rel(probes, ref.probes) < TOL and rel(snaps, ref.snaps) < TOL
+        assert rel_traces(probes, ref.probes) < TOL and rel_snaps(snaps, ref.snaps) < TOL
         outs.append(probes)
-    assert rel(outs[0], outs[1]) < TOL
+    assert rel_traces(outs[0], outs[1]) < TOL
 
 
 @pytest.mark.parametrize("solver", SOLVERS)

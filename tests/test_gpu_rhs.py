@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import theta as orc
+from parity import rel_snaps, rel_traces
 from workloads import synth
 
 pytestmark = pytest.mark.gpu
@@ -36,8 +37,8 @@ def test_independent_coils_with_probe_grid(eddy, form):
     assert probes.shape == (4, p.C.shape[0], p.T) and snaps.shape == (4, 200, 3)
     for r in range(4):
         ref = per_coil_oracle(p, r)
-        assert rel(probes[r], ref.probes) < TOL, r
-        assert rel(snaps[r], ref.snaps) < TOL, r
+        assert rel_traces(probes[r], ref.probes) < TOL, r
+        assert rel_snaps(snaps[r], ref.snaps) < TOL, r
 
 
 @pytest.mark.parametrize("form", ["plain", "modal"])
@@ -53,7 +54,7 @@ def test_paired_self_pickup(eddy, form, side):
     assert probes.shape == (S, 1, p.T)
     for r in sorted({0, S // 2, S - 1}):
         ref = per_coil_oracle(p, r)
-        assert rel(probes[r, 0], ref.probes[r]) < TOL, r
+        assert rel_traces(probes[r, 0], ref.probes[r]) < TOL, r
 
 
 def test_independent_modal_long_run(eddy):
@@ -63,7 +64,7 @@ def test_independent_modal_long_run(eddy):
     probes, _ = tm.run(p.T, p.src, None, 0)
     for r in (0, 3):
         ref = per_coil_oracle(p, r)
-        assert rel(probes[r], ref.probes) < TOL
+        assert rel_traces(probes[r], ref.probes) < TOL
 
 
 def test_rhs_modes_reject_electrodes(eddy):
