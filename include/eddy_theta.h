@@ -91,7 +91,18 @@ typedef struct ec_config {
   int tile_variant;       /* plain form, EC_SOLVE_INVERSE: 0 (default) = ec_setup times every launch
                              shape of the per-step products on the actual factor and keeps the
                              fastest; 1 .. 3 = use that shape.  No shape changes a result bit. */
+  int setup_gemm;         /* EC_GEMM_TENSOR (default) or EC_GEMM_FP64, see below */
 } ec_config;
+
+/* Arithmetic units of the setup's large dense products (both FP64-accurate): the
+ * Cholesky factorisations' trailing updates, the triangular solves of the reduction
+ * and back-transformation, the divide-and-conquer merges, the inverse factor and
+ * the modal snapshot reconstruction.
+ *   EC_GEMM_TENSOR  FP64 operands cut into 8-bit integer slices and multiplied on the
+ *                   tensor cores with exact accumulation (see ec_gemm_f64_emulated).
+ *   EC_GEMM_FP64    the FP64 CUDA cores (about 1.1 TFLOP/s on GB300).
+ * The two differ by rounding only. */
+enum { EC_GEMM_TENSOR = 0, EC_GEMM_FP64 = 1 };
 
 /* How the s coil columns of M drive the system (batched right-hand sides).
  *   EC_RHS_SUM          all coils act on one trajectory (their voltages add).

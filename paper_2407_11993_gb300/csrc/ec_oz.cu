@@ -1,0 +1,593 @@
+// FP64-accurate dense products on the tensor cores (tcgen05), for the dense
+// contractions of the modal setup (Sec. 3.2: Cholesky of R_i, the two-sided
+// reduction to standard form, the eigenvector merges and back-transformation) and
+// of the plain setup (Sec. 3.3.1: Cholesky of Z and its inverse).
+//
+// GB300 retires about two FP64 FMAs per SM per clock (1.2 TFLOP/s), but about
+// 3,500 BF16 multiply-adds.  The product is therefore computed exactly on integer
+// slices (the error-free splitting of Ozaki et al., 2012), restated here:
+//
+//   * every row i of op(A) is scaled by 2^-e_i with max_k |a_ik| < 2^(e_i - 1) and
+//     rounded to a 56-bit fixed-point integer F_ik (|F| < 2^55; an entry loses only
+//     the bits below 2^(e_i - 56), i.e. 2^-55 of its row's largest entry);
+//   * F is cut into seven balanced base-256 digits, F = sum_s d_s 256^(6-s),
+//     |d_s| <= 128, and slice s holds d_s 2^-8s in BF16 (exact: 8 significant bits);
+//   * columns of op(B) likewise (exponents f_j, slices t);
+//   * a_ik b_kj = 2^(e_i + f_j - 16) sum_{s,t} A_s B_t, and the pairs with s + t <= 6
+//     are kept (the rest lie below 2^-53 of the row / column scales).
+//
+// One CTA computes a 128 x 64 tile of C over a K range of at most 192:
+//   * warp 0 / lane 0 streams, per 32-wide K block, all seven A slices (one 3-D TMA
+//     box of 128 x 32 x 7) and all seven B slices (64 x 32 x 7) into a two-stage
+//     shared-memory ring (64-byte swizzle), guarded by mbarriers;
+//   * warp 1 / lane 0 issues one tcgen05.mma (kind::f16, BF16 in, FP32 accumulate,
+//     M = 128, N = 64, K = 16) per slice pair and 16-wide K step into six FP32
+//     accumulators in tensor memory: one per diagonal s + t = d for d <= 4, whose
+//     sums are exact (integers times 2^-8d below 2^24 in magnitude, because
+//     (d + 1) 2^14 K < 2^24 for K <= 192), and one shared by d = 5, 6, whose FP32
+//     rounding lies below 2^-60 of the leading diagonal;
+//   * all four warps then read the accumulators (warp w owns TMEM lanes 32w..32w+31,
+//     the tile's rows), rebuild each entry as an exact 64-bit integer at granularity
+//     2^-40, convert it to binary64 with integer instructions (one rounding), apply
+//     2^(e_i + f_j - 56) and alpha, and add beta C.
+// Longer K is done as consecutive launches that accumulate into C in FP64.
+// Every mbarrier wait is bounded; a wait that runs out records EC_ERR_TIMEOUT in the
+// status block and the kernel skips its remaining work and frees its TMEM.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ec_async.cuh"
+#include "ec_internal.h"
+#include "ec_oz.h"
+#include "ec_oz_int.h"
+#include "ec_tc.h"
+
+namespace ec {
+
+namespace {
+
+constexpr int OZ_S = 7;                 // slices per operand
+constexpr int OZ_DMAX = 6;              // slice pairs with s + t <= OZ_DMAX
+constexpr int OZ_EXACT = 5;             // diagonals 0 .. 4 have their own accumulator
+constexpr int NACC = OZ_EXACT + 1;      // + one shared by the diagonals 5 .. 6
+constexpr int TM = 128, TN = 64, TK = 32;
+constexpr int STAGES = 2;
+constexpr int A_SLICE = TM * TK * 2;    // 8 KB
+constexpr int B_SLICE = TN * TK * 2;    // 4 KB
+constexpr int A_BYTES = OZ_S * A_SLICE;
+constexpr int B_BYTES = OZ_S * B_SLICE;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 84 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int TMEM_COLS = 512;
+constexpr int GROUP_M = 16;             // tile rows per raster group (L2 reuse of A)
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+static_assert(NACC * TN <= TMEM_COLS, "accumulators exceed tensor memory");
+static_assert(5 * 128 * 128 * OZ_KCHUNK < (1 << 24), "diagonal 4 would not be exact");
+
+using dev::mbar_expect_tx;
+using dev::mbar_init;
+using dev::smem_u32;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st,
+                                          int where) {
+  return dev::mbar_wait(bar, parity, st, where, WAIT_LIMIT);
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 64 bytes, 64-byte swizzle,
+// 8-row groups 512 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return ((uint64_t)(addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) |
+         (1ull << 46) | (4ull << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = TN, M = TM.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+struct OzArgs {
+  int M, N;                // C block (rows, columns)
+  int k0, klen;            // K range of this launch
+  int tiles_m, tiles_n;
+  int tri;                 // keep only rows >= columns (of the C block)
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  const int* ea;           // row exponents of op(A)
+  const int* eb;           // column exponents of op(B)
+};
+
+// Tile of a launch: row groups of GROUP_M tile rows, columns innermost within a group
+// (the group's A slices stay in L2 while B streams).
+__device__ __forceinline__ void tile_of(int t, int tiles_m, int tiles_n, int& bm, int& bn) {
+  const int per_group = GROUP_M * tiles_n;
+  const int g = t / per_group;
+  const int r = t - g * per_group;
+  const int gm = min(GROUP_M, tiles_m - g * GROUP_M);
+  bn = r / gm;
+  bm = g * GROUP_M + (r - bn * gm);
+}
+
+__global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                         const __grid_constant__ CUtensorMap mapB,
+                                                         const OzArgs a, DevStatus* st) {
+  int bm, bn;
+  tile_of(blockIdx.x, a.tiles_m, a.tiles_n, bm, bn);
+  const int m0 = bm * TM, n0 = bn * TN;
+  // lower-triangle products: tiles entirely above the diagonal have nothing to do
+  if (a.tri && n0 > m0 + TM - 1) return;
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag, issued, consumed, skip;
+  // an earlier failure in the pipeline: the whole CTA leaves together
+  if (threadIdx.x == 0) skip = *(volatile int*)&st->code;
+  __syncthreads();
+  if (skip) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (a.klen + TK - 1) / TK;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // producer: all seven slices of A and of B for each 32-wide K block
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t use = kb / STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty_bar[s], (use - 1) & 1, st, 41)) {
+        abort_flag = 1;
+        break;
+      }
+      uint8_t* sa = smem + s * STAGE_BYTES;
+      uint8_t* sb = sa + A_BYTES;
+      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+      tma_load_3d(sa, &mapA, &full_bar[s], a.k0 + kb * TK, m0, 0);
+      tma_load_3d(sb, &mapB, &full_bar[s], a.k0 + kb * TK, n0, 0);
+      *(volatile int*)&issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: one MMA per slice pair and 16-wide K step
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, st, 42)) {
+        abort_flag = 1;
+        break;
+      }
+      *(volatile int*)&consumed = kb + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+      for (int d = 0; d <= OZ_DMAX; ++d) {
+        const int acc = d < OZ_EXACT ? d : OZ_EXACT;
+        const uint32_t tacc = tmem + (uint32_t)(acc * TN);
+#pragma unroll
+        for (int si = 0; si <= d; ++si) {
+          const int ti = d - si;
+          if (si >= OZ_S || ti >= OZ_S) continue;
+          const uint64_t da = smem_desc(sa + si * A_SLICE);
+          const uint64_t db = smem_desc(sb + ti * B_SLICE);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk) {
+            // the first product into each accumulator overwrites it
+            const bool first = kb == 0 && kk == 0 && si == 0 && (d < OZ_EXACT || d == OZ_EXACT);
+            mma_bf16(tacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+          }
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    // always committed: arrives once every MMA this thread issued has completed
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(&done_bar, 0, st, 43)) abort_flag = 1;
+    if (abort_flag)
+      for (int kb = consumed; kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, st, 44);
+  }
+  __syncthreads();
+  const bool good = (abort_flag == 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (good) {
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < a.M;
+    const int erow = row_ok ? a.ea[row] : 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      uint32_t r[NACC][16];
+#pragma unroll
+      for (int q = 0; q < NACC; ++q) tmem_ld16(lane_base + (uint32_t)(q * TN + c0), r[q]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!row_ok) continue;
+#pragma unroll 4
+      for (int j = 0; j < 16; ++j) {
+        const int col = n0 + c0 + j;
+        if (col >= a.N || (a.tri && col > row)) continue;
+        // exact integer at granularity 2^-40 (diagonal d holds integers times 2^-8d)
+        int64_t X = 0;
+#pragma unroll
+        for (int q = 0; q < OZ_EXACT; ++q) {
+          const float v = __uint_as_float(r[q][j]) * __int_as_float((127 + 8 * q) << 23);
+          X += (int64_t)__float2int_rn(v) << (40 - 8 * q);
+        }
+        X += (int64_t)__float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);  // 2^40
+        const int sc = erow + a.eb[col] - 56;
+        uint64_t bits;
+        double v;
+        if (oz::i64_scaled_to_f64_bits(X, sc, &bits))
+          v = __longlong_as_double((long long)bits);
+        else
+          v = ldexp((double)X, sc);
+        if (a.alpha == -1.0) v = -v;
+        else if (a.alpha != 1.0) v *= a.alpha;
+        double* cp = a.C + (int64_t)row + (int64_t)col * a.ldc;
+        if (a.beta == 0.0) *cp = v;
+        else if (a.beta == 1.0) *cp += v;
+        else *cp = fma(a.beta, *cp, v);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// ---- operand split --------------------------------------------------------
+// Logical operand X (R x K): element (r, k) at src[r * rs + k * ks] (one of rs, ks is 1).
+constexpr int ST = 64;   // split tile: 64 rows x 64 K
+
+// maxb[r] = max over k of the bits of |X(r, k)| (non-negative binary64 bits order as
+// unsigned integers).
+__global__ void __launch_bounds__(256) oz_absmax_kernel(int64_t R, int64_t K, const double* src,
+                                                        int64_t rs, int64_t ks,
+                                                        unsigned long long* maxb) {
+  __shared__ unsigned long long tile[ST][ST + 1];
+  const int64_t r0 = (int64_t)blockIdx.x * ST, k0 = (int64_t)blockIdx.y * ST;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < ST * ST; q += 256) {
+    int rr, kk;
+    if (rs == 1) { rr = q % ST; kk = q / ST; } else { kk = q % ST; rr = q / ST; }
+    const int64_t r = r0 + rr, k = k0 + kk;
+    unsigned long long b = 0;
+    if (r < R && k < K)
+      b = (unsigned long long)__double_as_longlong(fabs(src[r * rs + k * ks]));
+    tile[rr][kk] = b;
+  }
+  __syncthreads();
+  if (tid < ST) {
+    const int64_t r = r0 + tid;
+    unsigned long long m = 0;
+    for (int kk = 0; kk < ST; ++kk) m = tile[tid][kk] > m ? tile[tid][kk] : m;
+    if (r < R && m) atomicMax(maxb + r, m);
+  }
+}
+
+// Slices (K-major, leading dimension ldk, slice stride R * ldk):
+//   out[s][r][k] = bf16(d_s(r, k) 2^-8s),  exps[r] = e_r.
+__global__ void __launch_bounds__(256) oz_split_kernel(int64_t R, int64_t K, const double* src,
+                                                       int64_t rs, int64_t ks,
+                                                       const unsigned long long* maxb,
+                                                       __nv_bfloat16* out, int64_t ldk,
+                                                       int* exps) {
+  __shared__ double tile[ST][ST + 1];
+  __shared__ int ex[ST];
+  const int64_t r0 = (int64_t)blockIdx.x * ST, k0 = (int64_t)blockIdx.y * ST;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < ST * ST; q += 256) {
+    int rr, kk;
+    if (rs == 1) { rr = q % ST; kk = q / ST; } else { kk = q % ST; rr = q / ST; }
+    const int64_t r = r0 + rr, k = k0 + kk;
+    tile[rr][kk] = (r < R && k < K) ? src[r * rs + k * ks] : 0.0;
+  }
+  if (tid < ST) {
+    const int64_t r = r0 + tid;
+    const int e = r < R ? oz::row_exponent(maxb[r]) : 0;
+    ex[tid] = e;
+    if (r < R && blockIdx.y == 0) exps[r] = e;
+  }
+  __syncthreads();
+  const int64_t slice = R * ldk;
+  // thread -> (row, pair of K entries): 32 pairs per row, 8 rows per pass
+  const int kp = (tid & 31) * 2, rsub = tid >> 5;
+  for (int rr = rsub; rr < ST; rr += 8) {
+    const int64_t r = r0 + rr;
+    const int64_t k = k0 + kp;
+    if (r >= R || k >= K) continue;
+    int d0[7], d1[7];
+    oz::digits7(oz::f64_to_fixed56((uint64_t)__double_as_longlong(tile[rr][kp]), ex[rr]), d0);
+    const bool two = (k + 1 < K);
+    oz::digits7(two ? oz::f64_to_fixed56((uint64_t)__double_as_longlong(tile[rr][kp + 1]), ex[rr])
+                    : 0,
+                d1);
+    __nv_bfloat16* o = out + r * ldk + k;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const float sc = __int_as_float((127 - 8 * s) << 23);   // 2^-8s
+      const __nv_bfloat16 h0 = __float2bfloat16_rn((float)d0[s] * sc);
+      if (two && ((k & 1) == 0)) {
+        __nv_bfloat162 pr;
+        pr.x = h0;
+        pr.y = __float2bfloat16_rn((float)d1[s] * sc);
+        *reinterpret_cast<__nv_bfloat162*>(o + s * slice) = pr;
+      } else {
+        o[s * slice] = h0;
+        if (two) o[s * slice + 1] = __float2bfloat16_rn((float)d1[s] * sc);
+      }
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 7.
+bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
+                    int64_t ldk, int box_rows) {
+  EncodeTiledFn fn = (EncodeTiledFn)tensor_map_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)OZ_S};
+  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(R * ldk) * 2};
+  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+ec_status grow_ws(OzWork* w, int64_t slice_elems, int64_t rows) {
+  if (slice_elems > w->slices_cap) {
+    if (w->slices) cudaFree(w->slices);
+    w->slices = nullptr;
+    w->slices_cap = 0;
+    if (device_alloc((void**)&w->slices, sizeof(__nv_bfloat16) * (size_t)slice_elems) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      w->slices = nullptr;
+      return EC_ERR_OOM;
+    }
+    w->slices_cap = slice_elems;
+  }
+  if (rows > w->rows_cap) {
+    if (w->exps) cudaFree(w->exps);
+    if (w->maxb) cudaFree(w->maxb);
+    w->exps = nullptr;
+    w->maxb = nullptr;
+    w->rows_cap = 0;
+    if (device_alloc((void**)&w->exps, sizeof(int) * (size_t)rows) != cudaSuccess ||
+        device_alloc((void**)&w->maxb, sizeof(unsigned long long) * (size_t)rows) != cudaSuccess) {
+      cudaGetLastError();
+      return EC_ERR_OOM;
+    }
+    w->rows_cap = rows;
+  }
+  return EC_OK;
+}
+
+// Split rows [r0, r0 + R) of the logical operand into slices at `out` (ld ldk) with
+// exponents at `exps`; maxb is scratch of R entries.
+void split(cudaStream_t s, int64_t R, int64_t K, const double* src, int64_t rs, int64_t ks,
+           unsigned long long* maxb, __nv_bfloat16* out, int64_t ldk, int* exps) {
+  cudaMemsetAsync(maxb, 0, sizeof(unsigned long long) * (size_t)R, s);
+  dim3 grid((unsigned)((R + ST - 1) / ST), (unsigned)((K + ST - 1) / ST));
+  oz_absmax_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(R, K, src, rs, ks, maxb);
+  oz_split_kernel<<<grid, 256, 0, ::ec::counted(s)>>>(R, K, src, rs, ks, maxb, out, ldk, exps);
+}
+
+}  // namespace
+
+int64_t oz_kchunk() { return OZ_KCHUNK; }
+
+namespace {
+__global__ void set_status_kernel(DevStatus* st, int code) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->where = 45;
+}
+}  // namespace
+
+void gemm_auto(cudaStream_t s, OzWork* oz, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, int tri, const DevStatus* st) {
+  // below these sizes the split and the integer epilogue outweigh the FP64 work saved
+  if (oz && M >= 64 && N >= 32 && K >= 16 && M * N >= 32768 && (!tri || M == N)) {
+    const ec_status rc = oz_gemm(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, oz,
+                                 const_cast<DevStatus*>(st));
+    if (rc == EC_OK) return;
+    if (rc != EC_ERR_OOM) {   // launched work may be incomplete: fail the pipeline
+      set_status_kernel<<<1, 1, 0, ::ec::counted(s)>>>(const_cast<DevStatus*>(st), (int)rc);
+      return;
+    }
+    // no room for the slices (nothing was launched): the FP64 kernels do the product
+  }
+  dgemm(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+}
+
+void oz_free(OzWork* w) {
+  if (!w) return;
+  if (w->slices) cudaFree(w->slices);
+  if (w->exps) cudaFree(w->exps);
+  if (w->maxb) cudaFree(w->maxb);
+  *w = OzWork{};
+}
+
+ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                  double* C, int64_t ldc, int tri, OzWork* w, DevStatus* st) {
+  if (M <= 0 || N <= 0) return EC_OK;
+  if (!w || K < 0) return EC_ERR_ARG;
+  if (K == 0) {
+    if (beta != 1.0) {
+      // C = beta C: no product; done with the FP64 kernels' K = 0 path
+      dgemm(s, N_, N_, M, N, 0, alpha, A, lda, B, ldb, beta, C, ldc, tri, st);
+    }
+    return EC_OK;
+  }
+  if (tri && M != N) return EC_ERR_ARG;
+  if (M > (1ll << 30) || N > (1ll << 30)) return EC_ERR_UNSUPPORTED;
+  if (!tensor_map_encode_fn()) return EC_ERR_UNSUPPORTED;
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set))
+    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  const int64_t ldk = (K + 7) / 8 * 8;
+  // panels so that the slices of one A panel and one B panel fit the workspace cap
+  const int64_t per_row = (int64_t)OZ_S * ldk;
+  int64_t cap_rows = w->cap_elems / per_row;
+  if (cap_rows < 2 * TM) cap_rows = 2 * TM;
+  int64_t pm = M, pn = N;
+  if (pm + pn > cap_rows) {
+    pm = std::min<int64_t>(M, std::max<int64_t>(TM, cap_rows / 2 / TM * TM));
+    pn = std::min<int64_t>(N, std::max<int64_t>(TN, (cap_rows - pm) / TN * TN));
+  }
+  if (tri) {            // square lower-triangle update: panels of equal size along both
+    pm = pn = std::min(pm, pn) / TM * TM;
+    if (pm < TM) pm = pn = TM;
+  }
+  {
+    const ec_status g = grow_ws(w, per_row * (pm + pn), pm + pn);
+    if (g != EC_OK) return g;
+  }
+  __nv_bfloat16* sA = w->slices;
+  __nv_bfloat16* sB = w->slices + per_row * pm;
+  int* eA = w->exps;
+  int* eB = w->exps + pm;
+  // op(A) row r, k: A[r + k lda] (N) or A[k + r lda] (T); op(B) column c, k:
+  // B[k + c ldb] (N) or B[c + k ldb] (T)
+  const int64_t ars = ta == N_ ? 1 : lda, aks = ta == N_ ? lda : 1;
+  const int64_t brs = tb == N_ ? ldb : 1, bks = tb == N_ ? 1 : ldb;
+  for (int64_t i0 = 0; i0 < M; i0 += pm) {
+    const int64_t mi = std::min(pm, M - i0);
+    split(s, mi, K, A + i0 * ars, ars, aks, w->maxb, sA, ldk, eA);
+    for (int64_t j0 = 0; j0 < N; j0 += pn) {
+      const int64_t nj = std::min(pn, N - j0);
+      if (tri && j0 > i0 + mi - 1) break;            // panel entirely above the diagonal
+      split(s, nj, K, B + j0 * brs, brs, bks, w->maxb + pm, sB, ldk, eB);
+      CUtensorMap ma, mb;
+      if (!make_slice_map(&ma, sA, mi, K, ldk, TM) || !make_slice_map(&mb, sB, nj, K, ldk, TN))
+        return EC_ERR_CUDA;
+      OzArgs args{};
+      args.M = (int)mi;
+      args.N = (int)nj;
+      args.tiles_m = (int)((mi + TM - 1) / TM);
+      args.tiles_n = (int)((nj + TN - 1) / TN);
+      args.alpha = alpha;
+      args.C = C + i0 + j0 * ldc;
+      args.ldc = ldc;
+      args.ea = eA;
+      args.eb = eB;
+      // a tri panel on the diagonal (i0 == j0) keeps rows >= columns; a panel below it
+      // is full
+      args.tri = (tri && i0 == j0) ? 1 : 0;
+      const int64_t tiles = (int64_t)args.tiles_m * args.tiles_n;
+      for (int64_t k0 = 0; k0 < K; k0 += OZ_KCHUNK) {
+        args.k0 = (int)k0;
+        args.klen = (int)std::min<int64_t>(OZ_KCHUNK, K - k0);
+        args.beta = k0 == 0 ? beta : 1.0;
+        oz_gemm_kernel<<<(unsigned)tiles, 128, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb, args, st);
+      }
+      if (cudaGetLastError() != cudaSuccess) return EC_ERR_CUDA;
+    }
+  }
+  return EC_OK;
+}
+
+}  // namespace ec
+
+extern "C" ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, int64_t K,
+                                          double alpha, const double* A, int64_t lda,
+                                          const double* B, int64_t ldb, double beta, double* C,
+                                          int64_t ldc, int lower, void* stream) {
+  using namespace ec;
+  if ((ta != 0 && ta != 1) || (tb != 0 && tb != 1) || M < 0 || N < 0 || K < 0) return EC_ERR_ARG;
+  if (M == 0 || N == 0) return EC_OK;
+  if (!A || !B || !C) return EC_ERR_ARG;
+  const int64_t arows = ta ? K : M, brows = tb ? N : K;
+  if (lda < (arows > 1 ? arows : 1) || ldb < (brows > 1 ? brows : 1) || ldc < M) return EC_ERR_ARG;
+  if (lower && M != N) return EC_ERR_SHAPE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStatus* st = nullptr;
+  if (device_alloc((void**)&st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return EC_ERR_OOM;
+  }
+  cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+  OzWork w;
+  ec_status rc = oz_gemm(s, ta ? T_ : N_, tb ? T_ : N_, M, N, K, alpha, A, lda, B, ldb, beta, C,
+                         ldc, lower ? 1 : 0, &w, st);
+  cudaError_t e = cudaStreamSynchronize(s);
+  DevStatus h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
+  oz_free(&w);
+  cudaFree(st);
+  if (rc != EC_OK) return rc;
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EC_ERR_OOM : EC_ERR_CUDA;
+  return h.code ? (ec_status)h.code : EC_OK;
+}

@@ -1,0 +1,39 @@
+// FP64-accurate dense products on the tensor cores (Ozaki-type integer slices in
+// BF16, tcgen05 MMAs, exact per-diagonal accumulation); see ec_oz.cu.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "ec_internal.h"
+
+namespace ec {
+
+// K handled by one launch (longer K runs as consecutive launches accumulating in C).
+constexpr int OZ_KCHUNK = 192;
+
+// Device workspace of the emulated products: the BF16 slices of one panel of each
+// operand, their power-of-two exponents, and a scratch of row maxima.  Grown on demand
+// (through device_alloc) and kept until oz_free; cap_elems bounds the slices (BF16
+// elements), which makes large operands go through in panels.
+struct OzWork {
+  __nv_bfloat16* slices = nullptr;
+  int64_t slices_cap = 0;
+  int* exps = nullptr;
+  unsigned long long* maxb = nullptr;
+  int64_t rows_cap = 0;
+  int64_t cap_elems = 2ll << 30;        // 4 GB of slices
+};
+
+int64_t oz_kchunk();
+void oz_free(OzWork* w);
+
+// C = alpha op(A) op(B) + beta C with FP64 inputs and output, column-major, computed
+// on the tensor cores from seven 8-bit slices per operand.  tri = 1 (M == N) updates
+// only the lower triangle of C.  Error: below 2^-53 max_k|a_ik| max_k|b_kj| sqrt(K)
+// per entry before the final FP64 rounding of each K chunk's contribution (the scales
+// are per row of op(A) and per column of op(B)).  Enqueued on s; needs w.
+ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                  double* C, int64_t ldc, int tri, OzWork* w, DevStatus* st);
+
+}  // namespace ec

@@ -259,6 +259,8 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t
 
 }  // namespace
 
+void* tensor_map_encode_fn() { return (void*)encode_fn(); }
+
 int64_t bf16_ld(int64_t K) { return (K + 7) / 8 * 8; }
 
 void to_bf16(cudaStream_t s, int64_t M, int64_t K, const double* src, int64_t lds, int trans,

@@ -8,6 +8,10 @@
 
 namespace ec {
 
+// cuTensorMapEncodeTiled, resolved once through the runtime's driver entry-point
+// query (nullptr when unavailable).
+void* tensor_map_encode_fn();
+
 // Leading dimension (elements) of a K-major bf16 operand: K rounded up to 8 (16 bytes).
 int64_t bf16_ld(int64_t K);
 // dst[i * ld + k] = bf16(src element (i, k)), zero for k >= K; src column-major (lds),

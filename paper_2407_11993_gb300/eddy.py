@@ -41,7 +41,8 @@ class ec_config(ctypes.Structure):
     _fields_ = [("form", c_int), ("theta", c_double), ("dt", c_double), ("stream", c_void_p),
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
                 ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int),
-                ("rhs_mode", c_int), ("refine_steps", c_int), ("tile_variant", c_int)]
+                ("rhs_mode", c_int), ("refine_steps", c_int), ("tile_variant", c_int),
+                ("setup_gemm", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -260,7 +261,7 @@ class ThetaMethod:
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
                  integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0,
-                 refine_steps: int = 0, log_path: str | None = None):
+                 refine_steps: int = 0, log_path: str | None = None, setup_gemm: str = "tensor"):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
@@ -271,18 +272,21 @@ class ThetaMethod:
             raise ValueError("rhs must be 'sum', 'independent' or 'paired'")
         if not 0 <= int(tile_variant) <= 3:
             raise ValueError("tile_variant must be 0 (autotune) or 1 .. 3")
+        if setup_gemm not in ("tensor", "fp64"):
+            raise ValueError("setup_gemm must be 'tensor' or 'fp64'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
                         _PREC[precision], 1 if integrator == "exact" else 0,
                         {"sum": 0, "independent": 1, "paired": 2}[rhs], int(refine_steps),
-                        int(tile_variant))
+                        int(tile_variant), 1 if setup_gemm == "fp64" else 0)
         self.rhs = rhs
         self.log_path = log_path
         self._desc = {"form": form, "theta": float(theta), "dt": float(dt), "solver": solver,
                       "precision": precision, "integrator": integrator, "rhs": rhs,
-                      "refine_steps": int(refine_steps), "device": int(device)}
+                      "refine_steps": int(refine_steps), "device": int(device),
+                      "setup_gemm": setup_gemm}
         h = c_void_p()
         check(lib().ec_create(ctypes.byref(h), ctypes.byref(cfg)), "ec_create")
         self._h = h
