@@ -92,6 +92,11 @@ typedef struct ec_config {
                              shape of the per-step products on the actual factor and keeps the
                              fastest; 1 .. 3 = use that shape.  No shape changes a result bit. */
   int setup_gemm;         /* EC_GEMM_TENSOR (default) or EC_GEMM_FP64, see below */
+  int release_inputs;     /* nonzero: when ec_setup succeeds, free the device copies of L and R
+                             (and, for the plain form with EC_SOLVE_INVERSE, of the Cholesky factor
+                             of Z) that stepping does not read -- 2-3 N^2 doubles, 69-103 GB at
+                             N = 65,536.  The plain form then refuses ec_set_step (EC_ERR_STATE):
+                             a new dt needs a new ec_setup.  Everything else is unaffected. */
 } ec_config;
 
 /* Arithmetic units of the setup's large dense products (both FP64-accurate): the
@@ -324,12 +329,12 @@ EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, 
  * counterpart):  C = alpha op(A) op(B) + beta C, op(X) = X (t = 0) or X^T (t = 1).
  * Device pointers, column-major FP64 with leading dimensions lda, ldb, ldc; op(A) is
  * M x K, op(B) is K x N.  lower = 1 (M = N) updates only the lower triangle of C.
- * Each row of op(A) and column of op(B) is scaled by a power of two and cut into seven
+ * Each row of op(A) and column of op(B) is scaled by a power of two and cut into eight
  * 8-bit integer slices held exactly in BF16; the slice products (tcgen05, FP32
  * accumulation kept exact per slice diagonal) are recombined in integer arithmetic.
- * Error per entry: below 2^-53 sqrt(K) max_k|op(A)_ik| max_k|op(B)_kj| plus one FP64
+ * Error per entry: below 2^-60 sqrt(K) max_k|op(A)_ik| max_k|op(B)_kj| plus one FP64
  * rounding per 192-long K chunk, comparable to an FP64 GEMM.  Allocates a temporary
- * workspace (about 14 (M + N) K bytes, in panels beyond 4 GB).  Synchronous. */
+ * workspace (about 16 (M + N) K bytes, in panels beyond 4 GB).  Synchronous. */
 EC_API ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, int64_t K,
                                       double alpha, const double* A, int64_t lda, const double* B,
                                       int64_t ldb, double beta, double* C, int64_t ldc, int lower,

@@ -10,6 +10,7 @@
 
 #include "ec_kernels.h"
 #include "ec_modal.h"
+#include "ec_oz.h"
 #include "ec_tiles.h"
 
 using namespace ec;
@@ -96,6 +97,7 @@ struct ec_ctx {
   ec_timing tim{};
   int64_t last_info = -1;
   ModalState* modal = nullptr;
+  OzWork oz;               // tensor-core product workspace of the plain setup (EC_GEMM_TENSOR)
 };
 
 namespace ec {
@@ -178,6 +180,7 @@ void free_setup(ec_ctx* c) {
   c->csr.nnz = 0;
   dfree(c->dFlags); dfree(c->dTickets); dfree(c->dEpoch);
   if (c->modal) { modal_free(c->modal); c->modal = nullptr; }
+  oz_free(&c->oz);
   c->ready = false;
 }
 
@@ -285,7 +288,8 @@ ec_status plain_factor(ec_ctx* c) {
   EventTimer t(c->stream);
   copy_matrix(c->stream, n0, n0, c->dL + m + m * n, n, c->dZ, n0);
   add_lower(c->stream, n0, c->dZ, n0, c->dR + m + m * n, n, c->cfg.theta * c->cfg.dt);
-  potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st);
+  OzWork* oz = c->cfg.setup_gemm == EC_GEMM_TENSOR ? &c->oz : nullptr;
+  potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st, oz);
   if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
     EC_TRY(alloc(&c->dW, (size_t)n0 * n0));
     EC_TRY(tile_plan_create(n0, &c->tiles));
@@ -294,7 +298,7 @@ ec_status plain_factor(ec_ctx* c) {
     EC_TRY(alloc(&c->dPart2, prow * npad));
     EC_TRY(alloc(&c->dYsol, npad));
     cudaMemsetAsync(c->dYsol, 0, sizeof(double) * npad, c->stream);
-    trtri_lower(c->stream, n0, c->dZ, n0, c->dDinv, c->dW, n0, c->st);
+    trtri_lower(c->stream, n0, c->dZ, n0, c->dDinv, c->dW, n0, c->st, oz);
     if (c->cfg.precision == EC_PREC_FP32) {
       // FP32 copy of C^{-1} for the solves; the lower half of L (= L_i, no electrodes)
       // in FP64 for the refinement residual.
@@ -321,6 +325,7 @@ ec_status plain_factor(ec_ctx* c) {
   }
   c->tim.factor_ms = t.stop_ms();
   ec_status rc = collect(c);
+  oz_free(&c->oz);   // the tensor-core workspace is needed during the factorisation only
   // The per-step products read the packed tiles; the square inverse is kept only
   // for the GEMMs of independent right-hand sides.
   if (rc == EC_OK && c->dW && c->cfg.rhs_mode == EC_RHS_SUM) dfree(c->dW);
@@ -403,6 +408,7 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
     return EC_ERR_UNSUPPORTED;
   if (cfg->integrator == EC_INTEG_EXACT && cfg->form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
   if (cfg->tile_variant < 0 || cfg->tile_variant > TILE_VARIANTS) return EC_ERR_ARG;
+  if (cfg->setup_gemm != EC_GEMM_TENSOR && cfg->setup_gemm != EC_GEMM_FP64) return EC_ERR_ARG;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
@@ -610,12 +616,19 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
     ma.precision = c->cfg.precision;
     ma.integ = c->cfg.integrator;
     ma.rhs_mode = c->cfg.rhs_mode;
+    ma.gemm = c->cfg.setup_gemm;
     ma.st = c->st;
     EC_TRY(modal_setup(c->stream, c->modal, ma, &c->tim));
     EC_TRY(collect(c));
   }
   c->tim.setup_ms = whole.stop_ms();
   c->ready = true;
+  if (c->cfg.release_inputs) {
+    // stepping reads the factors / modes and the sparse R only
+    dfree(c->dL);
+    dfree(c->dR);
+    if (c->cfg.form == EC_FORM_PLAIN && c->cfg.plain_solver == EC_SOLVE_INVERSE) dfree(c->dZ);
+  }
   return EC_OK;
 }
 
@@ -623,6 +636,7 @@ ec_status ec_set_step(ec_ctx* c, double theta, double dt) {
   if (!c) return EC_ERR_ARG;
   if (!(theta >= 0.0 && theta <= 1.0) || !(dt > 0.0)) return EC_ERR_ARG;
   if (!c->ready) return EC_ERR_STATE;
+  if (c->cfg.form == EC_FORM_PLAIN && (!c->dL || !c->dR)) return EC_ERR_STATE;  // released
   c->cfg.theta = theta;
   c->cfg.dt = dt;
   form_sources(c);

@@ -449,7 +449,8 @@ void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const d
       n, bs, Qin, Wm, Qout, ld, st);
 }
 
-void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st) {
+void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st,
+           OzWork* oz) {
   static std::atomic<unsigned long long> attr_set{0};
   const int smem = 2 * 64 * 65 * (int)sizeof(double);
   if (first_on_device(attr_set))
@@ -463,39 +464,40 @@ void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevS
     if (rest > 0) {
       double* P = A + (k + kb) + k * lda;
       // panel: P <- P Lkk^{-T}  (in place; each CTA owns whole rows of the panel)
-      dgemm(s, N_, T_, rest, kb, kb, 1.0, P, lda, Dk, NB, 0.0, P, lda, 0, st);
+      gemm_auto(s, oz, N_, T_, rest, kb, kb, 1.0, P, lda, Dk, NB, 0.0, P, lda, 0, st);
       // trailing lower update: A22 <- A22 - P P^T
-      dgemm(s, N_, T_, rest, rest, kb, -1.0, P, lda, P, lda, 1.0, A + (k + kb) + (k + kb) * lda,
-            lda, 1, st);
+      gemm_auto(s, oz, N_, T_, rest, rest, kb, -1.0, P, lda, P, lda, 1.0,
+                A + (k + kb) + (k + kb) * lda, lda, 1, st);
     }
   }
 }
 
 void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
-                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st, OzWork* oz) {
   for (int64_t k = 0; k < n; k += NB) {
     const int kb = (int)((n - k) < NB ? (n - k) : NB);
     const double* Dk = Dinv + (k / NB) * NB * NB;
     double* Bk = B + k;
-    dgemm(s, N_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+    gemm_auto(s, oz, N_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
     const int64_t rest = n - k - kb;
     if (rest > 0)
-      dgemm(s, N_, N_, rest, nrhs, kb, -1.0, Lf + (k + kb) + k * ldl, ldl, Bk, ldb, 1.0,
-            B + k + kb, ldb, 0, st);
+      gemm_auto(s, oz, N_, N_, rest, nrhs, kb, -1.0, Lf + (k + kb) + k * ldl, ldl, Bk, ldb, 1.0,
+                B + k + kb, ldb, 0, st);
   }
 }
 
 void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
-                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
+                       OzWork* oz) {
   const int64_t nblk = (n + NB - 1) / NB;
   for (int64_t b = nblk - 1; b >= 0; --b) {
     const int64_t k = b * NB;
     const int kb = (int)((n - k) < NB ? (n - k) : NB);
     const double* Dk = Dinv + b * NB * NB;
     double* Bk = B + k;
-    dgemm(s, T_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+    gemm_auto(s, oz, T_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
     if (k > 0)  // B[0:k] -= L[k:k+kb, 0:k]^T B_k
-      dgemm(s, T_, N_, k, nrhs, kb, -1.0, Lf + k, ldl, Bk, ldb, 1.0, B, ldb, 0, st);
+      gemm_auto(s, oz, T_, N_, k, nrhs, kb, -1.0, Lf + k, ldl, Bk, ldb, 1.0, B, ldb, 0, st);
   }
 }
 
@@ -504,16 +506,17 @@ void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf
 // trailing update only the lower triangle of the trailing block, a third of the
 // flops of the full solve.  The strict upper triangle is left stale.
 void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lf, int64_t ldl,
-                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st) {
+                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
+                            OzWork* oz) {
   for (int64_t k = 0; k < n; k += NB) {
     const int kb = (int)((n - k) < NB ? (n - k) : NB);
     const double* Dk = Dinv + (k / NB) * NB * NB;
     double* Bk = B + k * ldb;
-    dgemm(s, N_, T_, n - k, kb, kb, 1.0, Bk + k, ldb, Dk, NB, 0.0, Bk + k, ldb, 0, st);
+    gemm_auto(s, oz, N_, T_, n - k, kb, kb, 1.0, Bk + k, ldb, Dk, NB, 0.0, Bk + k, ldb, 0, st);
     const int64_t rest = n - k - kb;
     if (rest > 0)  // lower(B[k+kb:, k+kb:]) -= B[k+kb:, k:k+kb] L[k+kb:, k:k+kb]^T
-      dgemm(s, N_, T_, rest, rest, kb, -1.0, Bk + k + kb, ldb, Lf + (k + kb) + k * ldl, ldl, 1.0,
-            B + (k + kb) + (k + kb) * ldb, ldb, 1, st);
+      gemm_auto(s, oz, N_, T_, rest, rest, kb, -1.0, Bk + k + kb, ldb, Lf + (k + kb) + k * ldl,
+                ldl, 1.0, B + (k + kb) + (k + kb) * ldb, ldb, 1, st);
   }
 }
 

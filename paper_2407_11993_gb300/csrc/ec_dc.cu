@@ -438,7 +438,7 @@ void dc_free(DcWork* w) {
 }
 
 ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, double* lam,
-                   double* Q, double* Qtmp, double* W, DcWork* wk, DevStatus* st) {
+                   double* Q, double* Qtmp, double* W, DcWork* wk, DevStatus* st, OzWork* oz) {
   if (n <= 0) return EC_OK;
   cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * n, s);
   leaf_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(
@@ -459,7 +459,20 @@ ec_status dc_solve(cudaStream_t s, int64_t n, const double* d, const double* e, 
     rank_kernel<<<dim3((unsigned)groups, chunks), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, lam);
     vec_kernel<<<dim3((unsigned)bs, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, W);
     rot_kernel<<<dim3(chunks, (unsigned)groups), 256, 0, ::ec::counted(s)>>>(n, bs, *wk, W);
-    dgemm_halves(s, n, bs, groups, cur, W, nxt, n, st);
+    if (oz && bs >= DC_TC_MIN) {
+      // large merges: the two children's diagonal blocks times the matching rows of W,
+      // one product per half on the tensor-core path
+      for (int64_t z = 0; z < groups; ++z) {
+        const int64_t s0 = z * bs, nb = (n - s0) < bs ? (n - s0) : bs;
+        gemm_auto(s, oz, N_, N_, half, nb, half, 1.0, cur + s0 + s0 * n, n, W + s0 + s0 * n, n,
+                  0.0, nxt + s0 + s0 * n, n, 0, st);
+        const int64_t r0 = s0 + half, mb = nb - half;
+        gemm_auto(s, oz, N_, N_, mb, nb, mb, 1.0, cur + r0 + r0 * n, n, W + r0 + s0 * n, n, 0.0,
+                  nxt + r0 + s0 * n, n, 0, st);
+      }
+    } else {
+      dgemm_halves(s, n, bs, groups, cur, W, nxt, n, st);
+    }
     const int64_t done = groups * bs;
     if (done < n)   // a trailing block without a right half is carried over unmerged
       copy_matrix(s, n - done, n - done, cur + done + done * n, n, nxt + done + done * n, n);

@@ -25,6 +25,8 @@ constexpr int GEMM_KC = 16;         // K chunk staged through shared memory
 
 enum Op { N_ = 0, T_ = 1 };
 
+struct OzWork;   // workspace of the FP64-accurate tensor-core products (ec_oz.h)
+
 // ---- FP64 dense kernels (ec_blas.cu); all column-major -------------------
 // C[MxN] = alpha op(A) op(B) + beta C.  tri = 1 restricts work to the lower
 // triangle of C (tiles above the diagonal skipped, diagonal tiles masked).
@@ -34,6 +36,12 @@ enum Op { N_ = 0, T_ = 1 };
 void dgemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
            double* C, int64_t ldc, int tri, const DevStatus* st);
+
+// Same product, dispatched: with a tensor-core workspace `oz` and a product large enough
+// to gain from it, the FP64-accurate tensor-core path (ec_oz.cu); otherwise dgemm.
+void gemm_auto(cudaStream_t s, OzWork* oz, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, int tri, const DevStatus* st);
 
 // C (M x N, ld ldc) = A^T B for a short output (M <= 64) and long K, with K split
 // into `splits` slices whose partial products (ws: splits x M x N) are summed in
@@ -49,22 +57,30 @@ void dgemm_tn_split(cudaStream_t s, int64_t M, int64_t N, int64_t K, const doubl
 void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const double* Qin,
                   const double* Wm, double* Qout, int64_t ld, const DevStatus* st);
 
+// The blocked drivers below take an optional tensor-core workspace: with it, their
+// trailing updates and panel products run through gemm_auto's FP64-accurate
+// tensor-core path; without it, on the FP64 CUDA cores.
+//
 // Blocked right-looking Cholesky of the lower triangle of A (n x n, ld lda), in
 // place.  Dinv receives, per NB block, the inverse of the diagonal block of the
 // factor (NB x NB column-major, zero above the diagonal).  A non-positive pivot
 // sets st->code = EC_ERR_NOT_SPD and st->info = its global index.
-void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st);
+void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st,
+           OzWork* oz = nullptr);
 
 // B <- Lfac^{-1} B  (left, lower, no transpose); B is n x nrhs.
 void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac, int64_t ldl,
-                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+                     const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
+                     OzWork* oz = nullptr);
 // B <- Lfac^{-T} B  (left, lower factor, transposed = upper solve).
 void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lfac, int64_t ldl,
-                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+                       const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
+                       OzWork* oz = nullptr);
 // Lower triangle of B <- B Lfac^{-T} for square B whose result is symmetric
 // (n x n); the strict upper triangle is not written.
 void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lfac, int64_t ldl,
-                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st);
+                            const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
+                            OzWork* oz = nullptr);
 
 // Symmetrise: copy the lower triangle onto the upper one.
 void symmetrize_lower(cudaStream_t s, int64_t n, double* A, int64_t lda);
@@ -93,7 +109,8 @@ void trsv_begin(cudaStream_t s, const TrsvSync& sync);   // resets tickets, bump
 // W = C^{-1} for the lower Cholesky factor C (n x n); W's diagonal 64 x 64 blocks
 // hold zeros above the diagonal, blocks above the block diagonal are not written.
 void trtri_lower(cudaStream_t s, int64_t n, const double* C, int64_t ldc, const double* Dinv,
-                 double* W, int64_t ldw, const DevStatus* st);
+                 double* W, int64_t ldw, const DevStatus* st,
+                 OzWork* oz = nullptr);
 int trmv_chunks(int64_t n, int chunk);
 // y = W b (part1: trmv_chunks x n partials, summed into y), then x = W^T y as
 // trmv_chunks x n partials in part2 (the consumer sums them in order).

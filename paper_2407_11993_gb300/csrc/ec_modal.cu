@@ -27,6 +27,7 @@
 #include <cmath>
 
 #include "ec_modal.h"
+#include "ec_oz.h"
 #include "ec_sytrd.h"
 #include "ec_tc.h"
 
@@ -63,6 +64,10 @@ struct ModalState {
   __nv_bfloat16* Ubf_cm_lo = nullptr;
   __nv_bfloat16* Ybf = nullptr;      // right operand (N x ld), hi and lo halves
   size_t ybfCap = 0;
+  // FP64-accurate tensor-core products (EC_GEMM_TENSOR): workspace, kept for the run's
+  // snapshot reconstruction
+  int gemm = EC_GEMM_TENSOR;
+  OzWork oz;
   // setup scratch
   double* DinvR = nullptr;
   const double* CR = nullptr;
@@ -75,6 +80,7 @@ constexpr int MT = 256;            // modes per CTA
 constexpr int TS = 16;             // steps per shared-memory block of the probe contraction
 constexpr int64_t SUPER = 32768;   // steps per launch group (bounds the partial-sum buffer)
 constexpr int64_t CH_MIN = 1024;   // shortest time chunk; runs up to this length are one chunk
+constexpr int64_t ORM_GROUP = 1024;  // reflectors per compact-WY group of the tensor-core back-transform
 
 cudaError_t dalloc(void** p, size_t b) { return device_alloc(p, b); }
 
@@ -406,7 +412,8 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
   if (N <= 0) return EC_OK;
   if (K < 0) K = n0;
   if (ms->precision == EC_PREC_FP64) {
-    dgemm(s, trans_u ? T_ : N_, N_, n0, N, K, 1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
+    gemm_auto(s, ms->gemm == EC_GEMM_TENSOR ? &ms->oz : nullptr, trans_u ? T_ : N_, N_, n0, N, K,
+              1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
     return EC_OK;
   }
   const int64_t ld = bf16_ld(n0);
@@ -432,6 +439,7 @@ void modal_free(ModalState* ms) {
   __nv_bfloat16* bs[] = {ms->Ubf_rm, ms->Ubf_cm, ms->Ubf_rm_lo, ms->Ubf_cm_lo, ms->Ybf};
   for (__nv_bfloat16* p : bs)
     if (p) cudaFree(p);
+  oz_free(&ms->oz);
   delete ms;
 }
 
@@ -471,10 +479,12 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   cudaMemsetAsync(ms->x, 0, sizeof(double) * n0 * ms->ntraj, s);
   ms->CR = a.Ri;
   ms->ldCR = ld;
+  ms->gemm = a.gemm;
+  OzWork* oz = a.gemm == EC_GEMM_TENSOR ? &ms->oz : nullptr;
 
   Timer t(s);
   // a4: R_i = C_R C_R^T
-  potrf(s, n0, a.Ri, ld, ms->DinvR, a.st);
+  potrf(s, n0, a.Ri, ld, ms->DinvR, a.st, oz);
   tim->factor_ms = t.ms();
   {
     DevStatus h{};
@@ -482,8 +492,8 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
     if (h.code != 0) return EC_OK;   // reported by the caller's status collection
   }
   // a5: A = C_R^{-1} L_i C_R^{-T}
-  trsm_left_lower(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
-  trsm_right_lower_t_sym(s, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st);
+  trsm_left_lower(s, n0, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st, oz);
+  trsm_right_lower_t_sym(s, n0, a.Ri, ld, ms->DinvR, a.Li, ld, a.st, oz);
   symmetrize_lower(s, n0, a.Li, ld);
   tim->reduce_ms = t.ms();
   // a6: tridiagonalisation
@@ -506,14 +516,29 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
     cleanup();
     return EC_ERR_OOM;
   }
-  sytrd_lower(s, n0, a.Li, ld, d, e, th, v, w, part, pcap, a.st);
+  if (oz) {
+    // panels of 64 columns, their rank-128 trailing updates on the tensor cores
+    double *Vp = nullptr, *Wp = nullptr, *yp = nullptr, *pp = nullptr;
+    if (alloc_n(&Vp, (size_t)n0 * NB) || alloc_n(&Wp, (size_t)n0 * NB) || alloc_n(&yp, 128) ||
+        alloc_n(&pp, (size_t)sytrd_blocked_scratch(n0))) {
+      for (double* p : {Vp, Wp, yp, pp})
+        if (p) cudaFree(p);
+      cleanup();
+      return EC_ERR_OOM;
+    }
+    sytrd_lower_blocked(s, n0, a.Li, ld, d, e, th, Vp, Wp, yp, pp, oz, a.st);
+    cudaStreamSynchronize(s);
+    for (double* p : {Vp, Wp, yp, pp}) cudaFree(p);
+  } else {
+    sytrd_lower(s, n0, a.Li, ld, d, e, th, v, w, part, pcap, a.st);
+  }
   tim->tridiag_ms = t.ms();
   DcWork* dcw = dc_alloc(n0, dalloc);
   if (!dcw) {
     cleanup();
     return EC_ERR_OOM;
   }
-  rc = dc_solve(s, n0, d, e, lam, Q1, Q2, Wm, dcw, a.st);
+  rc = dc_solve(s, n0, d, e, lam, Q1, Q2, Wm, dcw, a.st, oz);
   tim->eig_ms = t.ms();
   dc_free(dcw);
   if (rc != EC_OK) {
@@ -526,7 +551,26 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
            (unsigned)(n0 < 65535 ? n0 : 65535));
     reverse_kernel<<<g, 256, 0, ::ec::counted(s)>>>(n0, lam, Q1, ms->tau, ms->U);
   }
-  {
+  if (oz) {
+    // compact-WY groups of up to ORM_GROUP reflectors, products on the tensor cores
+    const int64_t gsz = std::min<int64_t>(ORM_GROUP, (std::max<int64_t>(n0 - 2, 1) + NB - 1) / NB * NB);
+    double *Vg = nullptr, *Gg = nullptr, *Tg = nullptr, *Xg = nullptr, *Wg = nullptr, *W2g = nullptr;
+    auto gfree = [&]() {
+      for (double* p : {Vg, Gg, Tg, Xg, Wg, W2g})
+        if (p) cudaFree(p);
+    };
+    if (alloc_n(&Vg, (size_t)n0 * gsz) || alloc_n(&Gg, (size_t)gsz * gsz) ||
+        alloc_n(&Tg, (size_t)gsz * gsz) || alloc_n(&Xg, (size_t)gsz * NB) ||
+        alloc_n(&Wg, (size_t)gsz * n0) || alloc_n(&W2g, (size_t)gsz * n0)) {
+      gfree();
+      cleanup();
+      return EC_ERR_OOM;
+    }
+    ormtr_lower_grouped(s, n0, a.Li, ld, th, ms->U, n0, n0, gsz, Vg, Gg, Tg, Xg, Wg, W2g, oz,
+                        a.st);
+    cudaStreamSynchronize(s);
+    gfree();
+  } else {
     const int64_t ws_cap = std::max<int64_t>((int64_t)dgemm_tn_splits(NB, n0, n0) * NB * n0,
                                              (int64_t)dgemm_tn_splits(NB, NB, n0) * NB * NB);
     double* ws = nullptr;
@@ -537,7 +581,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
       cudaFree(ws);
     }
   }
-  trsm_left_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, ms->U, n0, a.st);
+  trsm_left_lower_t(s, n0, n0, a.Ri, ld, ms->DinvR, ms->U, n0, a.st, oz);
   tim->backtransform_ms = t.ms();
   cleanup();
   // a7: projections and per-mode coefficients

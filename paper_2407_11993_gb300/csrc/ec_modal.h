@@ -27,6 +27,7 @@ struct ModalSetupArgs {
   int precision;       // EC_PREC_*
   int integ;           // EC_INTEG_*
   int rhs_mode;        // EC_RHS_*
+  int gemm;            // EC_GEMM_*: the setup's dense products on the tensor cores or FP64 cores
   DevStatus* st;
 };
 

@@ -8,26 +8,28 @@
 // slices (the error-free splitting of Ozaki et al., 2012), restated here:
 //
 //   * every row i of op(A) is scaled by 2^-e_i with max_k |a_ik| < 2^(e_i - 1) and
-//     rounded to a 56-bit fixed-point integer F_ik (|F| < 2^55; an entry loses only
-//     the bits below 2^(e_i - 56), i.e. 2^-55 of its row's largest entry);
-//   * F is cut into seven balanced base-256 digits, F = sum_s d_s 256^(6-s),
+//     rounded to a 64-bit fixed-point integer F_ik (|F| < 2^63; an entry loses only
+//     the bits below 2^(e_i - 64), i.e. 2^-62 of its row's largest entry);
+//   * F is cut into eight balanced base-256 digits, F = sum_s d_s 256^(7-s),
 //     |d_s| <= 128, and slice s holds d_s 2^-8s in BF16 (exact: 8 significant bits);
 //   * columns of op(B) likewise (exponents f_j, slices t);
-//   * a_ik b_kj = 2^(e_i + f_j - 16) sum_{s,t} A_s B_t, and the pairs with s + t <= 6
-//     are kept (the rest lie below 2^-53 of the row / column scales).
+//   * a_ik b_kj = 2^(e_i + f_j - 16) sum_{s,t} A_s B_t, and the 36 pairs with
+//     s + t <= 7 are kept (the dropped ones lie below 2^-61 of the row / column scales,
+//     so the product keeps FP64 accuracy even where a row's entries span many decades).
 //
 // One CTA computes a 128 x 64 tile of C over a K range of at most 192:
-//   * warp 0 / lane 0 streams, per 32-wide K block, all seven A slices (one 3-D TMA
-//     box of 128 x 32 x 7) and all seven B slices (64 x 32 x 7) into a two-stage
+//   * warp 0 / lane 0 streams, per 32-wide K block, all eight A slices (one 3-D TMA
+//     box of 128 x 32 x 8) and all eight B slices (64 x 32 x 8) into a two-stage
 //     shared-memory ring (64-byte swizzle), guarded by mbarriers;
 //   * warp 1 / lane 0 issues one tcgen05.mma (kind::f16, BF16 in, FP32 accumulate,
 //     M = 128, N = 64, K = 16) per slice pair and 16-wide K step into six FP32
 //     accumulators in tensor memory: one per diagonal s + t = d for d <= 4, whose
 //     sums are exact (integers times 2^-8d below 2^24 in magnitude, because
-//     (d + 1) 2^14 K < 2^24 for K <= 192), and one shared by d = 5, 6, whose FP32
+//     (d + 1) 2^14 K < 2^24 for K <= 192), and one shared by d = 5, 6, 7, whose FP32
 //     rounding lies below 2^-60 of the leading diagonal;
-//   * all four warps then read the accumulators (warp w owns TMEM lanes 32w..32w+31,
-//     the tile's rows), rebuild each entry as an exact 64-bit integer at granularity
+//   * all eight warps then read the accumulators (warp w reads TMEM lanes
+//     32 (w % 4) .. + 31, the tile's rows, for half of the columns), rebuild each
+//     entry as an exact 64-bit integer at granularity
 //     2^-40, convert it to binary64 with integer instructions (one rounding), apply
 //     2^(e_i + f_j - 56) and alpha, and add beta C.
 // Longer K is done as consecutive launches that accumulate into C in FP64.
@@ -50,17 +52,17 @@ namespace ec {
 
 namespace {
 
-constexpr int OZ_S = 7;                 // slices per operand
-constexpr int OZ_DMAX = 6;              // slice pairs with s + t <= OZ_DMAX
+constexpr int OZ_S = 8;                 // slices per operand
+constexpr int OZ_DMAX = 7;              // slice pairs with s + t <= OZ_DMAX
 constexpr int OZ_EXACT = 5;             // diagonals 0 .. 4 have their own accumulator
-constexpr int NACC = OZ_EXACT + 1;      // + one shared by the diagonals 5 .. 6
+constexpr int NACC = OZ_EXACT + 1;      // + one shared by the diagonals 5 .. 7
 constexpr int TM = 128, TN = 64, TK = 32;
 constexpr int STAGES = 2;
 constexpr int A_SLICE = TM * TK * 2;    // 8 KB
 constexpr int B_SLICE = TN * TK * 2;    // 4 KB
 constexpr int A_BYTES = OZ_S * A_SLICE;
 constexpr int B_BYTES = OZ_S * B_SLICE;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 84 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;   // 96 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int TMEM_COLS = 512;
 constexpr int GROUP_M = 16;             // tile rows per raster group (L2 reuse of A)
@@ -147,7 +149,9 @@ __device__ __forceinline__ void tile_of(int t, int tiles_m, int tiles_n, int& bm
   bm = g * GROUP_M + (r - bn * gm);
 }
 
-__global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+constexpr int OZ_THREADS = 256;         // 8 warps: two per TMEM lane quarter in the epilogue
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                          const __grid_constant__ CUtensorMap mapB,
                                                          const OzArgs a, DevStatus* st) {
   int bm, bn;
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__
   const uint32_t tmem = tmem_base;
 
   if (warp == 0 && lane == 0) {
-    // producer: all seven slices of A and of B for each 32-wide K block
+    // producer: all eight slices of A and of B for each 32-wide K block
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t use = kb / STAGES;
@@ -254,38 +258,51 @@ __global__ void __launch_bounds__(128, 1) oz_gemm_kernel(const __grid_constant__
   const bool good = (abort_flag == 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (good) {
-    const int row = m0 + warp * 32 + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and half of the
+    // columns: [32 (w / 4), 32 (w / 4) + 32)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
     const bool row_ok = row < a.M;
-    const int erow = row_ok ? a.ea[row] : 0;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int erow = row_ok ? a.ea[row] - 56 : 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 16) {
+    for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
       uint32_t r[NACC][16];
 #pragma unroll
       for (int q = 0; q < NACC; ++q) tmem_ld16(lane_base + (uint32_t)(q * TN + c0), r[q]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (!row_ok) continue;
-#pragma unroll 4
+      // columns of this chunk all inside C (and, for lower-triangle products, all at or
+      // left of this row): no per-entry checks
+      const bool whole = (n0 + c0 + 16 <= a.N) && (!a.tri || n0 + c0 + 15 <= row);
+#pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int col = n0 + c0 + j;
-        if (col >= a.N || (a.tri && col > row)) continue;
-        // exact integer at granularity 2^-40 (diagonal d holds integers times 2^-8d)
-        int64_t X = 0;
-#pragma unroll
-        for (int q = 0; q < OZ_EXACT; ++q) {
-          const float v = __uint_as_float(r[q][j]) * __int_as_float((127 + 8 * q) << 23);
-          X += (int64_t)__float2int_rn(v) << (40 - 8 * q);
-        }
-        X += (int64_t)__float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);  // 2^40
-        const int sc = erow + a.eb[col] - 56;
+        if (!whole && (col >= a.N || (a.tri && col > row))) continue;
+        // exact integer at granularity 2^-40 (diagonal d holds integers times 2^-8d):
+        // the top two diagonals in 32 bits, the rest by wide multiply-adds, then the
+        // shared group of the small diagonals rounded at 2^-40
+        const int i0 = __float2int_rn(__uint_as_float(r[0][j]));
+        const int i1 = __float2int_rn(__uint_as_float(r[1][j]) * 256.0f);
+        const int i2 = __float2int_rn(__uint_as_float(r[2][j]) * 65536.0f);
+        const int i3 = __float2int_rn(__uint_as_float(r[3][j]) * 16777216.0f);
+        const int i4 = __float2int_rn(__uint_as_float(r[4][j]) * 4294967296.0f);
+        const int ig = __float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);
+        int64_t X = (int64_t)(i0 * 256 + i1) * 4294967296ll;
+        X += (int64_t)i2 * (1 << 24);
+        X += (int64_t)i3 * (1 << 16);
+        X += (int64_t)i4 * (1 << 8);
+        X += ig;
+        const int sc = erow + a.eb[col];
         uint64_t bits;
+        if (!oz::i64_scaled_to_f64_bits_fast(X, sc, &bits)) {
+          const double slow = X == 0 ? 0.0 : ldexp((double)X, sc);
+          bits = (uint64_t)__double_as_longlong(slow);
+        }
         double v;
-        if (oz::i64_scaled_to_f64_bits(X, sc, &bits))
-          v = __longlong_as_double((long long)bits);
-        else
-          v = ldexp((double)X, sc);
-        if (a.alpha == -1.0) v = -v;
-        else if (a.alpha != 1.0) v *= a.alpha;
+        if (a.alpha == -1.0) v = __longlong_as_double((long long)(bits ^ (1ull << 63)));
+        else if (a.alpha == 1.0) v = __longlong_as_double((long long)bits);
+        else v = a.alpha * __longlong_as_double((long long)bits);
         double* cp = a.C + (int64_t)row + (int64_t)col * a.ldc;
         if (a.beta == 0.0) *cp = v;
         else if (a.beta == 1.0) *cp += v;
@@ -362,10 +379,10 @@ __global__ void __launch_bounds__(256) oz_split_kernel(int64_t R, int64_t K, con
     const int64_t r = r0 + rr;
     const int64_t k = k0 + kp;
     if (r >= R || k >= K) continue;
-    int d0[7], d1[7];
-    oz::digits7(oz::f64_to_fixed56((uint64_t)__double_as_longlong(tile[rr][kp]), ex[rr]), d0);
+    int d0[OZ_S], d1[OZ_S];
+    oz::digits8(oz::f64_to_fixed64((uint64_t)__double_as_longlong(tile[rr][kp]), ex[rr]), d0);
     const bool two = (k + 1 < K);
-    oz::digits7(two ? oz::f64_to_fixed56((uint64_t)__double_as_longlong(tile[rr][kp + 1]), ex[rr])
+    oz::digits8(two ? oz::f64_to_fixed64((uint64_t)__double_as_longlong(tile[rr][kp + 1]), ex[rr])
                     : 0,
                 d1);
     __nv_bfloat16* o = out + r * ldk + k;
@@ -391,7 +408,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 7.
+// 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 8.
 bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
                     int64_t ldk, int box_rows) {
   EncodeTiledFn fn = (EncodeTiledFn)tensor_map_encode_fn();
@@ -551,7 +568,8 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
         args.k0 = (int)k0;
         args.klen = (int)std::min<int64_t>(OZ_KCHUNK, K - k0);
         args.beta = k0 == 0 ? beta : 1.0;
-        oz_gemm_kernel<<<(unsigned)tiles, 128, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb, args, st);
+        oz_gemm_kernel<<<(unsigned)tiles, OZ_THREADS, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb,
+                                                                                    args, st);
       }
       if (cudaGetLastError() != cudaSuccess) return EC_ERR_CUDA;
     }

@@ -28,10 +28,10 @@ int64_t oz_kchunk();
 void oz_free(OzWork* w);
 
 // C = alpha op(A) op(B) + beta C with FP64 inputs and output, column-major, computed
-// on the tensor cores from seven 8-bit slices per operand.  tri = 1 (M == N) updates
-// only the lower triangle of C.  Error: below 2^-53 max_k|a_ik| max_k|b_kj| sqrt(K)
-// per entry before the final FP64 rounding of each K chunk's contribution (the scales
-// are per row of op(A) and per column of op(B)).  Enqueued on s; needs w.
+// on the tensor cores from eight 8-bit slices per operand.  tri = 1 (M == N) updates
+// only the lower triangle of C.  Error: below 2^-60 max_k|a_ik| max_k|b_kj| sqrt(K)
+// per entry (the scales are per row of op(A) and per column of op(B)) plus one FP64
+// rounding of each 192-long K chunk's contribution.  Enqueued on s; needs w.
 ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                   double* C, int64_t ldc, int tri, OzWork* w, DevStatus* st);

@@ -60,10 +60,28 @@ OZ_HD bool i64_scaled_to_f64_bits(int64_t X, int sc, uint64_t* out) {
   return true;
 }
 
+// Same result without branches on the common path: normalise u = |X| so that its
+// leading one sits at bit 63, keep 53 bits, round to nearest even from the 11 bits
+// below, and add the biased exponent one below its final value so that a mantissa
+// that rounds up to 2^53 carries into the exponent.  Requires X != 0 and a normal
+// result; returns false otherwise (the caller then takes a slow path).
+OZ_HD bool i64_scaled_to_f64_bits_fast(int64_t X, int sc, uint64_t* out) {
+  const uint64_t sign = (uint64_t)X & (1ull << 63);
+  const uint64_t u = X < 0 ? (uint64_t)0 - (uint64_t)X : (uint64_t)X;
+  const int lz = clz64(u);
+  const uint64_t nu = u << (lz & 63);          // leading one at bit 63 (u != 0)
+  uint64_t mant = nu >> 11;                    // 53 bits, implicit one at bit 52
+  const uint32_t low = (uint32_t)(nu & 0x7FFull);
+  mant += (low > 0x400u || (low == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const int be = 63 - lz + 1023 + sc;          // biased exponent before a rounding carry
+  *out = sign | (((uint64_t)(be - 1) << 52) + mant);
+  return u != 0 && be > 0 && be < 2046;
+}
+
 // Fixed-point image of a binary64 value against a power-of-two scale: the integer
-// F = round(a * 2^(56 - e)) for |a| < 2^(e-1), so |F| < 2^55 (ties away from zero;
-// the value is exact whenever a carries no bits below 2^(e-56)).  Returns F.
-OZ_HD int64_t f64_to_fixed56(uint64_t bits, int e) {
+// F = round(a * 2^(64 - e)) for |a| < 2^(e-1), so |F| < 2^63 (ties away from zero;
+// exact whenever a carries no bits below 2^(e-64)).  Returns F.
+OZ_HD int64_t f64_to_fixed64(uint64_t bits, int e) {
   const int E = (int)((bits >> 52) & 0x7FF);
   uint64_t m = bits & ((1ull << 52) - 1);
   if (E == 0 && m == 0) return 0;
@@ -74,10 +92,10 @@ OZ_HD int64_t f64_to_fixed56(uint64_t bits, int e) {
     m |= (1ull << 52);
     ex = E - 1075;
   }
-  const int shift = ex + 56 - e;              // F = m * 2^shift
+  const int shift = ex + 64 - e;              // F = m * 2^shift
   uint64_t mag;
   if (shift >= 0) {
-    mag = shift >= 11 ? 0 : (m << shift);     // shift <= 2 for |a| < 2^(e-1); guard anyway
+    mag = shift > 10 ? 0 : (m << shift);      // shift <= 10 for |a| < 2^(e-1); guard anyway
   } else if (shift <= -64) {
     mag = 0;
   } else {
@@ -87,12 +105,12 @@ OZ_HD int64_t f64_to_fixed56(uint64_t bits, int e) {
   return (bits >> 63) ? -(int64_t)mag : (int64_t)mag;
 }
 
-// Balanced base-256 digits of a fixed-point value |F| < 2^55:
-//   F = sum_{s=0}^{6} d_s 256^(6-s),  d_s in [-127, 128]  (d_0 carries the top bits).
-OZ_HD void digits7(int64_t F, int* d) {
+// Balanced base-256 digits of a fixed-point value |F| < 2^63:
+//   F = sum_{s=0}^{7} d_s 256^(7-s),  |d_s| <= 128  (d_0 carries the top bits).
+OZ_HD void digits8(int64_t F, int* d) {
   const bool neg = F < 0;
   uint64_t u = neg ? (uint64_t)0 - (uint64_t)F : (uint64_t)F;
-  for (int s = 6; s >= 1; --s) {
+  for (int s = 7; s >= 1; --s) {
     const int low = (int)(u & 255u);
     u >>= 8;
     int v = low;

@@ -221,13 +221,15 @@ __global__ void form_v_kernel(int64_t n, const double* A, int64_t lda, int64_t b
   }
 }
 
-// T (kb x kb upper) of Q_b = H_b ... H_{b+kb-1} = I - V T V^T from G = V^T V.
-__global__ void form_t_kernel(int kb, const double* G, const double* tau, int64_t b, double* T) {
+// T (kb x kb upper, ld ldt) of Q_b = H_b ... H_{b+kb-1} = I - V T V^T from G = V^T V
+// (ld ldg).
+__global__ void form_t_kernel(int kb, const double* G, int64_t ldg, const double* tau, int64_t b,
+                              double* T, int64_t ldt) {
   __shared__ double Ts[64][65];
   __shared__ double g[64];
   const int a = threadIdx.x;
   for (int i = 0; i < kb; ++i) {
-    if (a < kb) g[a] = G[a + i * kb];
+    if (a < kb) g[a] = G[a + i * ldg];
     __syncthreads();
     const double ti = tau[b + i];
     if (a < i) {
@@ -242,7 +244,7 @@ __global__ void form_t_kernel(int kb, const double* G, const double* tau, int64_
     __syncthreads();
   }
   for (int i = 0; i < kb; ++i)
-    if (a < kb) T[a + i * kb] = Ts[a][i];
+    if (a < kb) T[a + i * ldt] = Ts[a][i];
 }
 
 }  // namespace
@@ -299,7 +301,7 @@ void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const 
     int spg = dgemm_tn_splits(kb, kb, len);
     while (spg > 1 && (int64_t)spg * kb * kb > ws_cap) --spg;
     dgemm_tn_split(s, kb, kb, len, V + r0, n, V + r0, n, G, kb, ws, spg, st);
-    form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G, tau, b, T);
+    form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G, kb, tau, b, T, kb);
     // W = V^T Y: a 64-row output with a long K, split over K to fill the GPU
     int sp = dgemm_tn_splits(kb, ncol, len);
     while (sp > 1 && (int64_t)sp * kb * ncol > ws_cap) --sp;
@@ -307,6 +309,308 @@ void ormtr_lower(cudaStream_t s, int64_t n, const double* A, int64_t lda, const 
     dgemm(s, N_, N_, kb, ncol, kb, 1.0, T, kb, W, kb, 0.0, W2, kb, 0, st);
     dgemm(s, N_, N_, len, ncol, kb, -1.0, V + r0, n, W2, kb, 1.0, Y + r0, ldy, 0, st);
   }
+}
+
+void ormtr_lower_grouped(cudaStream_t s, int64_t n, const double* A, int64_t lda,
+                         const double* tau, double* Y, int64_t ldy, int64_t ncol, int64_t gsize,
+                         double* V, double* G, double* T, double* X, double* W, double* W2,
+                         OzWork* oz, const DevStatus* st) {
+  const int64_t nref = n - 2;
+  if (nref <= 0) return;
+  const int64_t ngroups = (nref + gsize - 1) / gsize;
+  for (int64_t gi = ngroups - 1; gi >= 0; --gi) {
+    const int64_t b0 = gi * gsize;
+    const int64_t gb = (nref - b0) < gsize ? (nref - b0) : gsize;
+    const int64_t r0 = b0 + 1, len = n - r0;
+    // V: the group's reflectors, 64 columns at a time
+    for (int64_t c = 0; c < gb; c += NB) {
+      const int kb = (int)((gb - c) < NB ? (gb - c) : NB);
+      form_v_kernel<<<dim3(32, kb), 256, 0, ::ec::counted(s)>>>(n, A, lda, b0 + c, kb,
+                                                                V + c * n);
+    }
+    // G = V^T V, then T block by block: diagonal blocks from G's diagonal blocks, and
+    // T[0:c, c:c+kb] = -T[0:c, 0:c] G[0:c, c:c+kb] T[c:c+kb, c:c+kb]
+    gemm_auto(s, oz, T_, N_, gb, gb, len, 1.0, V + r0, n, V + r0, n, 0.0, G, gb, 0, st);
+    cudaMemsetAsync(T, 0, sizeof(double) * (size_t)gb * gb, s);
+    for (int64_t c = 0; c < gb; c += NB) {
+      const int kb = (int)((gb - c) < NB ? (gb - c) : NB);
+      form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G + c + c * gb, gb, tau, b0 + c,
+                                                    T + c + c * gb, gb);
+      if (c > 0) {
+        dgemm(s, N_, N_, c, kb, c, 1.0, T, gb, G + c * gb, gb, 0.0, X, gb, 0, st);
+        dgemm(s, N_, N_, c, kb, kb, -1.0, X, gb, T + c + c * gb, gb, 0.0, T + c * gb, gb, 0, st);
+      }
+    }
+    // Y[r0:, :] <- (I - V T V^T) Y[r0:, :]
+    gemm_auto(s, oz, T_, N_, gb, ncol, len, 1.0, V + r0, n, Y + r0, ldy, 0.0, W, gb, 0, st);
+    gemm_auto(s, oz, N_, N_, gb, ncol, gb, 1.0, T, gb, W, gb, 0.0, W2, gb, 0, st);
+    gemm_auto(s, oz, N_, N_, len, ncol, gb, -1.0, V + r0, n, W2, gb, 1.0, Y + r0, ldy, 0, st);
+  }
+}
+
+namespace {
+
+// Blocked tridiagonalisation, column j = b + i of a panel starting at column b:
+// A[j:, j] -= V[j:, 0:i] W[j, 0:i]^T + W[j:, 0:i] V[j, 0:i]^T  (the panel's earlier
+// reflectors, not yet applied to the trailing matrix).
+__global__ void __launch_bounds__(256) latrd_col_kernel(int64_t n, double* A, int64_t lda,
+                                                        int64_t j, const double* V,
+                                                        const double* W, int64_t ldv, int i) {
+  __shared__ double wj[64], vj[64];
+  if (threadIdx.x < i) {
+    wj[threadIdx.x] = W[j + threadIdx.x * ldv];
+    vj[threadIdx.x] = V[j + threadIdx.x * ldv];
+  }
+  __syncthreads();
+  const int64_t r = j + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double a0 = A[r + j * lda], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = 0;
+  for (; c + 1 < i; c += 2) {
+    a0 = fma(-V[r + c * ldv], wj[c], a0);
+    a1 = fma(-W[r + c * ldv], vj[c], a1);
+    a2 = fma(-V[r + (c + 1) * ldv], wj[c + 1], a2);
+    a3 = fma(-W[r + (c + 1) * ldv], vj[c + 1], a3);
+  }
+  if (c < i) {
+    a0 = fma(-V[r + c * ldv], wj[c], a0);
+    a1 = fma(-W[r + c * ldv], vj[c], a1);
+  }
+  A[r + j * lda] = (a0 + a1) + (a2 + a3);
+}
+
+// y1[c] = W[j+1:, c] . v[j+1:],  y2[c] = V[j+1:, c] . v[j+1:]  for c < i (one CTA per c).
+__global__ void __launch_bounds__(256) latrd_dots_kernel(int64_t n, int64_t j, const double* V,
+                                                         const double* W, int64_t ldv,
+                                                         const double* v, double* y) {
+  __shared__ double sh[2][8];
+  const int c = blockIdx.x;
+  double a1 = 0.0, a2 = 0.0;
+  for (int64_t r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+    const double vr = v[r];
+    a1 = fma(W[r + c * ldv], vr, a1);
+    a2 = fma(V[r + c * ldv], vr, a2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = a1;
+    sh[1][w] = a2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      s1 += sh[0][q];
+      s2 += sh[1][q];
+    }
+    y[c] = s1;
+    y[64 + c] = s2;
+  }
+}
+
+// Symmetric product over the trailing lower triangle, one CTA per 64 x 64 tile (I, J),
+// I >= J, of A22 = A[s0:, s0:] (s0 = j + 1, m = n - s0):
+//   prow[J][r] = sum_{c in J} A[r, c] v[c]   for r in block I  (diagonal tile: c <= r)
+//   pcol[I][c] = sum_{r in I} A[r, c] v[r]   for c in block J  (diagonal tile: r > c)
+// (partials indexed by block, stride mp), so that for a row r of block I
+//   (A22 v)[r] = sum_{J <= I} prow[J][r] + sum_{I' >= I} pcol[I'][r],
+// summed in that fixed order by p_latrd_kernel.  Each element is read once and used
+// for both of its contributions.
+__global__ void __launch_bounds__(256) symv_tile_kernel(int64_t n, const double* A, int64_t lda,
+                                                        int64_t j, const double* v, double* prow,
+                                                        double* pcol, int64_t mp) {
+  __shared__ double As[64][65];     // As[c][r] = A[row0 + r, col0 + c]
+  __shared__ double vr[64], vc[64];
+  __shared__ double red[4][64];
+  int64_t I, J;
+  {
+    const int64_t t = blockIdx.x;
+    int64_t q = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (q * (q + 1) / 2 > t) --q;
+    while ((q + 1) * (q + 2) / 2 <= t) ++q;
+    I = q;
+    J = t - q * (q + 1) / 2;
+  }
+  const int64_t s0 = j + 1, m = n - s0;
+  const int64_t r0 = I * 64, c0 = J * 64;      // offsets inside A22
+  const int tid = threadIdx.x;
+  for (int q = tid; q < 64 * 64; q += 256) {
+    const int rr = q & 63, cc = q >> 6;
+    const int64_t r = r0 + rr, c = c0 + cc;
+    double a = 0.0;
+    if (r < m && c < m && (I != J || rr >= cc)) a = A[(s0 + r) + (s0 + c) * lda];
+    As[cc][rr] = a;
+  }
+  if (tid < 64) {
+    vr[tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
+    vc[tid] = (c0 + tid < m) ? v[s0 + c0 + tid] : 0.0;
+  }
+  __syncthreads();
+  const int lo = tid & 63, qt = tid >> 6;
+  // row part: thread (row lo, quarter qt of the columns)
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+  for (int cc = 0; cc < 16; cc += 2) {
+    a0 = fma(As[qt * 16 + cc][lo], vc[qt * 16 + cc], a0);
+    a1 = fma(As[qt * 16 + cc + 1][lo], vc[qt * 16 + cc + 1], a1);
+  }
+  red[qt][lo] = a0 + a1;
+  __syncthreads();
+  if (tid < 64 && r0 + tid < m)
+    prow[J * mp + r0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+  __syncthreads();
+  // column part: thread (column lo, quarter qt of the rows); the diagonal tile's
+  // diagonal is counted once (in the row part)
+  double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < 16; rr += 2) {
+    const int ra = qt * 16 + rr, rb = ra + 1;
+    const double xa = (I != J || ra > lo) ? As[lo][ra] : 0.0;
+    const double xb = (I != J || rb > lo) ? As[lo][rb] : 0.0;
+    b0 = fma(xa, vr[ra], b0);
+    b1 = fma(xb, vr[rb], b1);
+  }
+  red[qt][lo] = b0 + b1;
+  __syncthreads();
+  if (tid < 64 && c0 + tid < m)
+    pcol[I * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+}
+
+// As p_kernel, with the panel's corrections: for rows r > j,
+//   p_r = tau ( (A22 v)_r - V[r, 0:i] y1 - W[r, 0:i] y2 ),
+// then w = p - (tau/2)(p^T v) v by the last CTA.
+__global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, const double* v,
+                                                      const double* tau, const double* prow,
+                                                      const double* pcol, int64_t mp,
+                                                      const double* V, const double* W,
+                                                      int64_t ldv, int i, const double* y,
+                                                      double* p, double* dots, unsigned* counter) {
+  __shared__ double sh[9];
+  __shared__ double ys[128];
+  __shared__ bool last;
+  if (threadIdx.x < 2 * i) ys[threadIdx.x < i ? threadIdx.x : 64 + threadIdx.x - i] =
+      y[threadIdx.x < i ? threadIdx.x : 64 + threadIdx.x - i];
+  __syncthreads();
+  const double t = tau[j];
+  const int64_t len = n - j - 1;
+  double dot = 0.0;
+  const int64_t nbk = (len + 63) / 64;
+  // one thread per row (the grid covers the rows once); the partials of the row are
+  // added in block order, two independent chains each
+  for (int64_t r = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rl = r - (j + 1), blk = rl >> 6;
+    double q0 = 0.0, q1 = 0.0, c0 = 0.0, c1 = 0.0;
+    int64_t b = 0;
+    for (; b + 1 <= blk; b += 2) {
+      q0 += prow[b * mp + rl];
+      q1 += prow[(b + 1) * mp + rl];
+    }
+    if (b <= blk) q0 += prow[b * mp + rl];
+    b = blk;
+    for (; b + 1 < nbk; b += 2) {
+      c0 += pcol[b * mp + rl];
+      c1 += pcol[(b + 1) * mp + rl];
+    }
+    if (b < nbk) c0 += pcol[b * mp + rl];
+    double q = (q0 + q1) + (c0 + c1);
+    double e0 = 0.0, e1 = 0.0;
+    for (int c = 0; c < i; ++c) {
+      e0 = fma(V[r + c * ldv], ys[c], e0);
+      e1 = fma(W[r + c * ldv], ys[64 + c], e1);
+    }
+    q = (q - e0) - e1;
+    q *= t;
+    p[r] = q;
+    dot = fma(q, v[r], dot);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+  if (lane == 0) sh[w] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) b += sh[q];
+    dots[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    double b = 0.0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) b += __ldcg(dots + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (threadIdx.x == 0) {
+      sh[8] = 0.5 * t * b;
+      *counter = 0u;
+    }
+  }
+  __syncthreads();
+  const double f = sh[8];
+  for (int64_t r = j + 1 + threadIdx.x; r < n; r += blockDim.x) p[r] = fma(-f, v[r], p[r]);
+  // rows above j + 1 of the panel's w column are zero (v is zero there)
+  for (int64_t r = threadIdx.x; r <= j; r += blockDim.x) p[r] = 0.0;
+}
+
+}  // namespace
+
+int64_t sytrd_blocked_scratch(int64_t n) {
+  const int64_t nbk = (n + 63) / 64;
+  return 2 * nbk * n + 2 * (int64_t)num_sms() + 8;
+}
+
+void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, double* e,
+                         double* tau, double* V, double* W, double* y, double* partial,
+                         OzWork* oz, const DevStatus* st) {
+  const int sms = num_sms();
+  const int pgrid = 2 * sms;
+  const int64_t mp = n;                            // stride of the per-block partials
+  const int64_t nbk_max = (n + 63) / 64;
+  double* prow = partial;
+  double* pcol = partial + nbk_max * mp;
+  double* dots = pcol + nbk_max * mp;
+  unsigned* counter = reinterpret_cast<unsigned*>(dots + pgrid);
+  cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  const int64_t jend = n - 2;                      // columns 0 .. n-3 carry a reflector
+  for (int64_t b = 0; b < jend; b += NB) {
+    const int nb = (int)((jend - b) < NB ? (jend - b) : NB);
+    for (int i = 0; i < nb; ++i) {
+      const int64_t j = b + i;
+      const int64_t len = n - j - 1;
+      double* vj = V + (int64_t)i * n;
+      double* wj = W + (int64_t)i * n;
+      if (i > 0)
+        latrd_col_kernel<<<(unsigned)((n - j + 255) / 256), 256, 0, ::ec::counted(s)>>>(
+            n, A, lda, j, V, W, n, i);
+      house_col_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, A, lda, j, vj, d, e, tau, st);
+      const int64_t nbk = (len + 63) / 64;
+      symv_tile_kernel<<<(unsigned)(nbk * (nbk + 1) / 2), 256, 0, ::ec::counted(s)>>>(
+          n, A, lda, j, vj, prow, pcol, mp);
+      if (i > 0)
+        latrd_dots_kernel<<<(unsigned)i, 256, 0, ::ec::counted(s)>>>(n, j, V, W, n, vj, y);
+      const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;
+      p_latrd_kernel<<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(
+          n, j, vj, tau, prow, pcol, mp, V, W, n, i, y, wj, dots, counter);
+    }
+    // the panel's rank-2nb update of the trailing lower triangle
+    const int64_t t0 = b + nb, m = n - t0;
+    if (m > 0) {
+      gemm_auto(s, oz, N_, T_, m, m, nb, -1.0, V + t0, n, W + t0, n, 1.0, A + t0 + t0 * lda, lda,
+                1, st);
+      gemm_auto(s, oz, N_, T_, m, m, nb, -1.0, W + t0, n, V + t0, n, 1.0, A + t0 + t0 * lda, lda,
+                1, st);
+    }
+  }
+  tail_kernel<<<1, 1, 0, ::ec::counted(s)>>>(n, A, lda, d, e);
 }
 
 }  // namespace ec

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) trmv_lower_t_kernel(int64_t n, const doub
 }  // namespace
 
 void trtri_lower(cudaStream_t s, int64_t n, const double* C, int64_t ldc, const double* Dinv,
-                 double* W, int64_t ldw, const DevStatus* st) {
+                 double* W, int64_t ldw, const DevStatus* st, OzWork* oz) {
   // W = C^{-1}: forward block substitution on the identity, touching only the
   // columns that can be non-zero (W is lower triangular).
   cudaMemsetAsync(W, 0, sizeof(double) * (size_t)ldw * n, s);
@@ -134,11 +134,11 @@ void trtri_lower(cudaStream_t s, int64_t n, const double* C, int64_t ldc, const 
     const int64_t ncols = k + kb;
     const double* Dk = Dinv + (k / NB) * NB * NB;
     double* Wk = W + k;
-    dgemm(s, N_, N_, kb, ncols, kb, 1.0, Dk, NB, Wk, ldw, 0.0, Wk, ldw, 0, st);
+    gemm_auto(s, oz, N_, N_, kb, ncols, kb, 1.0, Dk, NB, Wk, ldw, 0.0, Wk, ldw, 0, st);
     const int64_t rest = n - k - kb;
     if (rest > 0)
-      dgemm(s, N_, N_, rest, ncols, kb, -1.0, C + (k + kb) + k * ldc, ldc, Wk, ldw, 1.0,
-            W + k + kb, ldw, 0, st);
+      gemm_auto(s, oz, N_, N_, rest, ncols, kb, -1.0, C + (k + kb) + k * ldc, ldc, Wk, ldw, 1.0,
+                W + k + kb, ldw, 0, st);
   }
 }
 

@@ -42,7 +42,7 @@ class ec_config(ctypes.Structure):
                 ("device", c_int), ("spin_limit", c_longlong), ("profile", c_int),
                 ("plain_solver", c_int), ("precision", c_int), ("integrator", c_int),
                 ("rhs_mode", c_int), ("refine_steps", c_int), ("tile_variant", c_int),
-                ("setup_gemm", c_int)]
+                ("setup_gemm", c_int), ("release_inputs", c_int)]
 
 
 class ec_timing(ctypes.Structure):
@@ -261,7 +261,8 @@ class ThetaMethod:
                  device: int = 0, stream: int | None = None, spin_limit: int = 0,
                  profile: bool = False, solver: str = "inverse", precision: str = "fp64",
                  integrator: str = "theta", rhs: str = "sum", tile_variant: int = 0,
-                 refine_steps: int = 0, log_path: str | None = None, setup_gemm: str = "tensor"):
+                 refine_steps: int = 0, log_path: str | None = None, setup_gemm: str = "tensor",
+                 release_inputs: bool = False):
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
@@ -280,7 +281,8 @@ class ThetaMethod:
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
                         _PREC[precision], 1 if integrator == "exact" else 0,
                         {"sum": 0, "independent": 1, "paired": 2}[rhs], int(refine_steps),
-                        int(tile_variant), 1 if setup_gemm == "fp64" else 0)
+                        int(tile_variant), 1 if setup_gemm == "fp64" else 0,
+                        int(bool(release_inputs)))
         self.rhs = rhs
         self.log_path = log_path
         self._desc = {"form": form, "theta": float(theta), "dt": float(dt), "solver": solver,

@@ -96,6 +96,88 @@ def coil_scan_case(args) -> dict:
     return out
 
 
+def dt_sweep_case(args) -> dict:
+    """Sec. 5: the eigenmode analysis does not depend on dt, the Cholesky factor does.
+    One modal setup followed by k runs at k different dt (ec_set_step: O(N) per dt)
+    against the plain form, which re-forms and re-factors Z for every dt (ec_set_step
+    re-factors); T steps per run.  Reports the cumulative seconds after each dt."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2407_11993_gb300 import eddy
+    from workloads import synth
+
+    p = synth.config4(T=args.T, n=args.n) if args.config4 else synth.small(
+        args.n, T=args.T, seed=1, electrodes=False, coil=True, probes=4, dt=1e-7)
+    dts = [p.dt * (1.0 + 0.5 * i) for i in range(args.dt_sweep)]
+    out = {"n": args.n, "T": args.T, "dts": dts}
+    for form in ("modal", "plain"):
+        tm = eddy.ThetaMethod(form, p.theta, dts[0], setup_gemm=args.setup_gemm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tm.setup(p.L, p.R, None, p.M, None, p.C)
+        cum = []
+        for i, dt in enumerate(dts):
+            if i > 0:
+                tm.set_step(p.theta, dt)
+            tm.set_state(np.zeros(tm.state_size()))
+            tm.run(args.T, p.src, None, 0)
+            cum.append(time.perf_counter() - t0)
+        tm.close()
+        out[form] = {"cumulative_s": cum}
+    out["plain_over_modal_after_k"] = [a / b for a, b in zip(out["plain"]["cumulative_s"],
+                                                            out["modal"]["cumulative_s"])]
+    return out
+
+
+def grad_config5_case(args) -> dict:
+    """The differentiation workload: N = 4096, T = 5000, checkpoints every 250 steps,
+    targets from a 3x3x2 block at twice the resistivity plus seeded 1 % noise; the GPU
+    adjoint gradient (ec_grad) timed, and compared with the FP64 oracle's gradient
+    (all states kept, no checkpoints), timed on the host cores."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from oracle import adjoint as adj
+    from paper_2407_11993_gb300 import eddy
+    from workloads import synth
+
+    n, T, ck = args.n, args.T, 250
+    p = synth.small(n, T=T, seed=0, electrodes=False, coil=True, probes=16, dt=1e-6)
+    g2 = synth.geometry(n, 0)
+    nx, ny, nz = g2.grid
+    ijk = g2.ijk
+    block = ((ijk[:, 0] >= nx // 2 - 1) & (ijk[:, 0] <= nx // 2 + 1) &
+             (ijk[:, 1] >= ny // 2 - 1) & (ijk[:, 1] <= ny // 2 + 1) & (ijk[:, 2] <= 1))
+    g2.rho = g2.rho.copy()
+    g2.rho[block] *= 2.0
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm.setup(p.L, synth.resistance(g2), None, p.M, None, p.C)
+    v, _ = tm.run(T, p.src, None, 0)
+    tm.close()
+    v = v + 1e-2 * np.std(v) * np.random.default_rng(1000).standard_normal(v.shape)
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt)
+    tm.setup(p.L, p.R, None, p.M, None, p.C)
+    tm.grad(50, p.src[:, :51], v[:, :50], 25)               # warm-up
+    tm.set_state(np.zeros(tm.state_size()))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, gR, gs = tm.grad(T, p.src, v, ck)
+    t_gpu = time.perf_counter() - t0
+    tm.close()
+    t0 = time.perf_counter()
+    ref = adj.misfit_and_gradient(p.L, p.R, p.M, p.C, p.theta, p.dt, p.src, v)
+    t_cpu = time.perf_counter() - t0
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"n": n, "T": T, "ckpt_every": ck, "gpu_grad_s": t_gpu, "oracle_grad_s": t_cpu,
+            "J_rel_err": abs(J - ref.J) / ref.J, "dJ_dR_rel_err": rel(gR, ref.dJ_dRdiag),
+            "dJ_dsrc_rel_err": rel(gs, ref.dJ_dsrc), "host_cores": __import__("os").cpu_count()}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--form", choices=["plain", "modal"], default="plain")
@@ -105,6 +187,8 @@ def main() -> None:
     ap.add_argument("--no-electrodes", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "bf16x3"])
     ap.add_argument("--refine", type=int, default=0, help="plain fp32: refinement sweeps per step")
+    ap.add_argument("--setup-gemm", default="tensor", choices=["tensor", "fp64"],
+                    help="arithmetic units of the setup's large dense products")
     ap.add_argument("--config4", action="store_true",
                     help="the N=65,536 headline recipe (one coil, 4 pickups, dt = 0.1 us, no "
                          "electrodes, snapshots every 1000 steps) at size --n")
@@ -118,6 +202,11 @@ def main() -> None:
     ap.add_argument("--plain-T", type=int, default=20)
     ap.add_argument("--nmin", type=int, default=1024)
     ap.add_argument("--nmax", type=int, default=12288)
+    ap.add_argument("--dt-sweep", type=int, default=0,
+                    help="k runs at k different dt on one setup (modal) vs k re-factorisations "
+                         "(plain)")
+    ap.add_argument("--grad-config5", action="store_true",
+                    help="the differentiation workload (N=4096, T=5000, checkpoints every 250)")
     args = ap.parse_args()
 
     from paper_2407_11993_gb300 import build, eddy
@@ -130,6 +219,12 @@ def main() -> None:
     if args.coil_scan:
         print(json.dumps(coil_scan_case(args)))
         return
+    if args.dt_sweep:
+        print(json.dumps(dt_sweep_case(args)))
+        return
+    if args.grad_config5:
+        print(json.dumps(grad_config5_case(args)))
+        return
     if args.config4:
         p = synth.config4(T=args.T, n=args.n)
     elif args.config2:
@@ -138,7 +233,8 @@ def main() -> None:
         p = synth.small(args.n, T=args.T, seed=1, electrodes=not args.no_electrodes, coil=True,
                         probes=16, dt=0.5e-6)
     tm = eddy.ThetaMethod(args.form, p.theta, p.dt, solver=args.solver, profile=True,
-                          precision=args.precision, refine_steps=args.refine)
+                          precision=args.precision, refine_steps=args.refine,
+                          setup_gemm=args.setup_gemm)
     m = p.E.shape[0]
     import time
     t0 = time.perf_counter()
@@ -153,7 +249,8 @@ def main() -> None:
     out.update(setup_wall_s=t1 - t0, run_wall_s=t2 - t1,
                steps_per_s=p.T / (out["run_ms"] / 1e3) if out["run_ms"] > 0 else None)
     out.update(form=args.form, n=args.n, T=args.T, precision=args.precision, refine=args.refine,
-               setup_launches=setup_launches, launches=eddy.launch_count())
+               setup_gemm=args.setup_gemm, setup_launches=setup_launches,
+               launches=eddy.launch_count())
     print(json.dumps(out))
 
 

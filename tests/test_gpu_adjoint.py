@@ -122,3 +122,34 @@ def test_config5_shape_n4096(eddy):
     assert abs(J - ref.J) <= TOL * ref.J
     assert rel(gR, ref.dJ_dRdiag) < TOL
     assert rel(gs, ref.dJ_dsrc) < TOL
+
+
+def test_resistivity_gradient_fd_32_coordinates_h1e6(eddy):
+    """Central differences of the GPU's own misfit, relative step h = 1e-6 (and 1e-4) in
+    rho on 32 random coordinates, against the GPU adjoint gradient (dJ/drho_e =
+    g dJ/dR_ee).  Same bars as the oracle's check: aggregate relative error over the 32
+    coordinates 1e-2 at h = 1e-6 (FP64 rounding of the small misfit difference) and 1e-4
+    at h = 1e-4."""
+    n, T = 1024, 300
+    p, v = inversion_case(n, T, seed=3)
+    J, gR, _ = gpu_grad(eddy, p, v, T, 100)
+    rho = p.geom.rho
+    coords = np.random.default_rng(32).choice(n, size=32, replace=False)
+    grad = synth.G_FACTOR * gR[coords]
+
+    def misfit(R):
+        tm = eddy.ThetaMethod("plain", p.theta, p.dt)
+        tm.setup(p.L, R, None, p.M, None, p.C)
+        probes, _ = tm.run(T, p.src, None, 0)
+        tm.close()
+        return float(np.sum((probes - v) ** 2))
+
+    for hr, bar in ((1e-6, 1e-2), (1e-4, 1e-4)):
+        f = []
+        for e in coords:
+            h = hr * rho[e]
+            Rp = p.R.copy(); Rp[e, e] += h * synth.G_FACTOR
+            Rm = p.R.copy(); Rm[e, e] -= h * synth.G_FACTOR
+            f.append((misfit(Rp) - misfit(Rm)) / (2 * h))
+        f = np.array(f)
+        assert np.linalg.norm(f - grad) <= bar * np.linalg.norm(grad), hr

@@ -89,3 +89,29 @@ def test_batch_rejects_modal_and_duplicates(eddy):
         eddy.batch_run([a, a], 5, [p.src, p.src], None)
     a.close()
     mod.close()
+
+
+def test_batch_of_twenty_uneven_instances(eddy):
+    """20 instances with N drawn uniformly from [200, 3000] (fixed seed, half of them with
+    the electrode constraint): every instance bitwise equal to its own ec_run, and equal
+    to the oracle per trace."""
+    rng = np.random.default_rng(2024)
+    sizes = [int(x) for x in rng.integers(200, 3001, size=20)]
+    T, stride = 24, 8
+    ps = [synth.small(n, T=T, seed=100 + i, electrodes=(i % 2 == 0), coil=True, snap_stride=stride)
+          for i, n in enumerate(sizes)]
+    single = []
+    for p in ps:
+        tm = make(eddy, p)
+        single.append(tm.run(T, p.src, p.iD if p.E.shape[0] else None, stride))
+        tm.close()
+    models = [make(eddy, p) for p in ps]
+    batched = eddy.batch_run(models, T, [p.src for p in ps], [p.iD for p in ps], stride)
+    for (pa, sa), (pb, sb) in zip(single, batched):
+        assert np.array_equal(pa, pb) and np.array_equal(sa, sb)
+    for i in (0, 7, 19):
+        ref = orc.run_problem(ps[i], form="plain", T=T)
+        assert rel_traces(batched[i][0], ref.probes) < TOL
+        assert rel_snaps(batched[i][1], ref.snaps) < TOL
+    for m in models:
+        m.close()

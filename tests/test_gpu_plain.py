@@ -198,3 +198,29 @@ def test_tile_launch_shapes_are_bitwise_identical(eddy):
     for v in range(1, 4):
         assert np.array_equal(xs[v], xs[0])
         assert np.array_equal(probes[v], probes[0])
+
+
+@pytest.mark.parametrize("form", ["plain", "modal"])
+def test_release_inputs_after_setup(eddy, form):
+    """release_inputs frees the dense copies of L, R (and Z) that stepping does not read:
+    the run is unchanged; the plain form then refuses a new dt (EC_ERR_STATE), the modal
+    form still takes one (its per-mode coefficients only) and still sets a current."""
+    p = synth.small(300, T=30, seed=51, electrodes=True, coil=True, snap_stride=10)
+    ref = orc.run_problem(p, "plain")
+    tm = eddy.ThetaMethod(form, p.theta, p.dt, release_inputs=True)
+    tm.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
+    probes, snaps = tm.run(p.T, p.src, p.iD, p.snap_stride)
+    assert rel_traces(probes, ref.probes) < TOL and rel_snaps(snaps, ref.snaps) < TOL
+    if form == "plain":
+        with pytest.raises(eddy.EcError) as e:
+            tm.set_step(p.theta, 2 * p.dt)
+        assert e.value.code == 8
+    else:
+        q = synth.small(300, T=30, seed=51, electrodes=True, coil=True, snap_stride=10,
+                        dt=2 * p.dt)
+        tm.set_step(q.theta, q.dt)
+        tm.set_state(np.zeros(tm.state_size()))
+        probes, snaps = tm.run(q.T, q.src, q.iD, q.snap_stride)
+        refq = orc.run_problem(q, "plain")
+        assert rel_traces(probes, refq.probes) < TOL and rel_snaps(snaps, refq.snaps) < TOL
+    tm.close()
