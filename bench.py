@@ -314,6 +314,36 @@ def our_arm(args) -> None:
     modal, modal_setup_wall, tms = setup("modal")       # largest footprint first
     plain, plain_setup_wall, tps = setup("plain")
 
+    # ---- plain-step precision variant (FP32 hi/lo pair inverse factor), run before
+    # the timed loop so that its setup's transient memory comes before the modal
+    # form's kept slices of U; its errors are filled in after the FP64 runs below
+    px_out, px_err = None, None
+    if rank == 0 and not args.no_variants:
+        try:
+            px = eddy.ThetaMethod("plain", p.theta, p.dt, device=local,
+                                  stream=stream.cuda_stream, profile=True,
+                                  precision="fp32x2", release_inputs=True)
+            t0 = time.perf_counter()
+            px.setup(p.L, p.R, E, M, MD, p.C)
+            setup_x = time.perf_counter() - t0
+            Te = w["err_steps"]
+            prx, snx = px.run(Te, p.src[:, :Te + 1] if S else None,
+                              p.iD[:, :Te + 1] if m else None, 500 if Te % 500 == 0 else Te // 2)
+            tx = px.timings()
+            px.close()
+            fx = tx["fwd_ms"] / max(1.0, tx["fwd_launches"])
+            bytes_fx = 8.0 * n0 * (n0 + 1) / 2.0
+            pk_, _ = peaks()
+            gbs = bytes_fx / (fx * 1e-3) / 1e9
+            px_out = (np.asarray(prx), np.asarray(snx), {
+                "steps_per_s": Te / (tx["run_ms"] / 1e3), "setup_s": setup_x,
+                "fwd_product_ms": fx, "fwd_product_gbs": gbs,
+                "fwd_product_hbm_frac": gbs / float(pk_.get("hbm_gbs", 6800.0)),
+                "note": "inverse factor as FP32 hi/lo pairs (8 B per entry), compensated FP32 "
+                        "products; errors against the FP64 plain form over the same first steps"})
+        except Exception as ex:  # noqa: BLE001 - the main line must still be printed
+            px_err = str(ex)[:300]
+
     probes_p = torch.empty((cp, P), dtype=torch.float64, device=dev)
     probes_m = torch.empty((cm, P), dtype=torch.float64, device=dev)
     nsn = cm // stride if stride else 0
@@ -430,10 +460,10 @@ def our_arm(args) -> None:
 
     # ---- stated errors (outside the timed region) ------------------------------
     err = {}
+    outs = {}
     if rank == 0:
         Te = w["err_steps"]
         se = 500 if (Te % 500 == 0 and Te >= 500) else max(1, Te // 2)
-        outs = {}
         for name, tm in (("plain", plain), ("modal", modal)):
             tm.set_state(np.zeros(tm.state_size()))
             pr, sn = tm.run(Te, p.src[:, :Te + 1] if S else None, p.iD[:, :Te + 1] if m else None,
@@ -489,6 +519,54 @@ def our_arm(args) -> None:
             err["vs_oracle_first_steps"] = {"steps": To,
                                             "plain_probe_rel_per_trace": _per_trace(pp[:, :To], ref.probes),
                                             "modal_probe_rel_per_trace": _per_trace(pm[:, :To], ref.probes)}
+
+    # ---- precision variants ----------------------------------------------------
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        if px_out is not None:
+            prx, snx, stats = px_out
+            pp_, sp_ = outs.get("plain", (None, None))
+            stats["probe_rel_per_trace_vs_fp64_plain"] = (_per_trace(prx, pp_)
+                                                          if pp_ is not None else None)
+            stats["snapshot_rel_vs_fp64_plain"] = (_per_snapshot(snx, sp_)
+                                                   if sp_ is not None else None)
+            variants["plain_fp32x2"] = stats
+        elif px_err is not None:
+            variants["plain_fp32x2"] = {"error": px_err}
+        # modal form: the same modes with the products by U in reduced arithmetic
+        pm_, sm_ = outs.get("modal", (None, None))
+        Te = w["err_steps"]
+        se = 500 if (Te % 500 == 0 and Te >= 500) else max(1, Te // 2)
+        for prec in ("fp32x2", "fp32", "bf16x3", "bf16"):
+            key = "modal_" + prec
+            try:
+                t0 = time.perf_counter()
+                modal.set_precision(prec)
+                switch_s = time.perf_counter() - t0
+                modal.set_state(np.zeros(modal.state_size()))
+                prv, snv = modal.run(Te, p.src[:, :Te + 1] if S else None,
+                                     p.iD[:, :Te + 1] if m else None, se)
+                prv, snv = np.asarray(prv), np.asarray(snv)
+                rates = []
+                for i in range(3):                 # one warm-up chunk, two timed
+                    s_, d_ = window(i * cm, cm)
+                    modal.run(cm, s_, d_, stride if nsn else 0, mem=eddy.EC_MEM_DEVICE,
+                              probes_out=probes_m, snaps_out=snaps_m if nsn else None)
+                    if i:
+                        rates.append(cm / (modal.timings()["run_ms"] / 1e3))
+                variants[key] = {
+                    "steps_per_s": statistics.mean(rates), "switch_s": switch_s,
+                    "probe_rel_per_trace_vs_fp64_modal": _per_trace(prv, pm_),
+                    "probe_rel_functional_vs_fp64_modal": _functional(prv, pm_, p.C, sm_),
+                    "snapshot_rel_vs_fp64_modal": _per_snapshot(snv, sm_),
+                    "note": "same modes (one eigensolve), products by U in " + prec +
+                            "; errors against the FP64 modal run over the same first steps"}
+            except Exception as ex:  # noqa: BLE001
+                variants[key] = {"error": str(ex)[:300]}
+        try:
+            modal.set_precision("fp64")
+        except Exception:  # noqa: BLE001
+            pass
 
     # ---- end to end through the public API with host buffers (modal form) --------
     e2e = None
@@ -555,6 +633,7 @@ def our_arm(args) -> None:
                            "fp64_mma_tflops": fp["fp64_mma_tflops"],
                            "fp32_fma_tflops": fp["fp32_fma_tflops"],
                            "hbm_gbs": hbm, "bf16_tflops": pk.get("bf16_tflops")},
+        "precision_variants": variants,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -580,6 +659,8 @@ def main():
     ap.add_argument("--oracle-check", action="store_true",
                     help="also run the oracle's first steps at the full size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the plain step's FP32-pair precision variant")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -82,8 +82,8 @@ typedef struct ec_config {
   long long spin_limit;   /* polls before a kernel-side wait gives up (EC_ERR_TIMEOUT); 0 = default */
   int profile;            /* nonzero: ec_run times its dominant kernels with CUDA events (see ec_timing) */
   int plain_solver;       /* plain form only: EC_SOLVE_INVERSE (default) or EC_SOLVE_SUBSTITUTION */
-  int precision;          /* EC_PREC_FP64 (default); modal form: EC_PREC_BF16 / EC_PREC_BF16X3;
-                             plain form: EC_PREC_FP32; see below */
+  int precision;          /* EC_PREC_FP64 (default); modal form: EC_PREC_BF16 / _BF16X3 /
+                             _FP32 / _FP32X2; plain form: EC_PREC_FP32 / _FP32X2; see below */
   int integrator;         /* modal form: EC_INTEG_THETA (default) or EC_INTEG_EXACT, see below */
   int rhs_mode;           /* EC_RHS_SUM (default), EC_RHS_INDEPENDENT or EC_RHS_PAIRED, see below */
   int refine_steps;       /* plain form with EC_PREC_FP32: FP64 iterative-refinement sweeps per
@@ -142,8 +142,21 @@ enum { EC_INTEG_THETA = 0, EC_INTEG_EXACT = 1 };
  *                 can amplify (see ec_gemm_bf16 and the documented error tables).
  *   EC_PREC_BF16X3  split BF16: each operand is stored as hi + lo BF16 parts and each
  *                 product is hi*hi + hi*lo + lo*hi on the tensor cores, summed in
- *                 FP64 (about 2^-16 relative per entry, three times the tensor work). */
-enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2, EC_PREC_FP32 = 3 };
+ *                 FP64 (about 2^-16 relative per entry, three times the tensor work).
+ *   EC_PREC_FP32  the same three products with U and the right-hand columns rounded to
+ *                 FP32 (each under a power-of-two scale), FP32 multiply-adds and FP32
+ *                 sums within K segments of at least 512, the segments added in FP64
+ *                 (2^-24 relative per entry plus the FP32 sum's rounding).  With a few
+ *                 right-hand columns the products stream U once: half the bytes of FP64
+ *                 and arithmetic on the FP32 pipe.
+ *   EC_PREC_FP32X2  U as FP32 hi/lo pairs (8 bytes, about 48 significant bits) and
+ *                 compensated FP32 arithmetic (exact hi*hi products by FMA, the cross
+ *                 terms, float-float sums, FP64 sums every 64 products): about 2^-46
+ *                 relative per entry.
+ *   FP32 / FP32X2 keep the FP64 U (ec_modes) and add a copy of 4 / 8 bytes per entry.
+ *   ec_batch_run and ec_grad, which serve the plain form, are unaffected. */
+enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2, EC_PREC_FP32 = 3,
+       EC_PREC_FP32X2 = 4 };
 
 /* Arithmetic of the plain form's per-step solve (EC_SOLVE_INVERSE, EC_RHS_SUM, no
  * electrodes).  The Cholesky factor and its inverse are computed in FP64 in every case.
@@ -153,7 +166,14 @@ enum { EC_PREC_FP64 = 0, EC_PREC_BF16 = 1, EC_PREC_BF16X3 = 2, EC_PREC_FP32 = 3 
  *                 sweeps then forms the residual b - Z x in FP64 (L from its packed FP64
  *                 lower half, R from its sparse form) and adds the FP32 solve of it.
  *                 ec_grad, ec_get_inverse_factor and ec_batch_run need EC_PREC_FP64
- *                 (EC_ERR_UNSUPPORTED); electrodes (m > 0) are EC_ERR_UNSUPPORTED. */
+ *                 (EC_ERR_UNSUPPORTED); electrodes (m > 0) are EC_ERR_UNSUPPORTED.
+ *   EC_PREC_FP32X2  the inverse factor is stored as FP32 hi/lo pairs (hi = fp32(w),
+ *                 lo = fp32(w - hi): about 48 significant bits in the same 8 bytes as
+ *                 FP64) and the products run in compensated FP32 arithmetic (exact
+ *                 hi*hi products by FMA, float-float sums, FP64 partial rows): on GB300
+ *                 the products then move from the FP64 pipe's limit to HBM bandwidth.
+ *                 Error about 2^-46 relative per product entry; electrodes allowed; the
+ *                 same calls as EC_PREC_FP32 need EC_PREC_FP64. */
 
 /* How the plain form applies its Cholesky factor C each step (Sec. 3.3.1).
  *   EC_SOLVE_INVERSE       C^{-1} is formed once at setup (N^3/3 extra flops); each
@@ -213,6 +233,16 @@ EC_API ec_status ec_setup(ec_ctx* ctx, int64_t n, const double* L, const double*
  * Modal form: recomputes the per-mode coefficients only (O(N)); the modes do not
  * depend on dt (Sec. 5). */
 EC_API ec_status ec_set_step(ec_ctx* ctx, double theta, double dt);
+
+/* Modal form only: switch the arithmetic of the products with the mode matrix U
+ * (EC_PREC_FP64 / _BF16 / _BF16X3 / _FP32 / _FP32X2, see above) on a set-up context.
+ * The modes (Sec. 3.2) are kept: the reduced copy of U is rebuilt from the FP64 U and
+ * the projections B = U^T [R_D | L_D | M_0], G^T = U^T (C K)^T are recomputed with the
+ * new arithmetic; the current modal state is kept.  Works after release_inputs.
+ * EC_ERR_STATE before ec_setup, EC_ERR_UNSUPPORTED for the plain form, EC_ERR_ARG for
+ * an unknown value, EC_ERR_OOM when the copy does not fit (the context then keeps
+ * FP64 products). */
+EC_API ec_status ec_set_precision(ec_ctx* ctx, int precision);
 
 /* Advance T steps of Eq. time_integration (plain) or its modal image (modal).
  *   src     s x (T+1) coil currents i_0 at t_k = k dt, k = 0..T (row-major; NULL if s = 0)

@@ -45,6 +45,8 @@ struct ec_ctx {
   double* dT1 = nullptr;     // EC_PREC_FP32: halves of L x
   double* dT2 = nullptr;
   float* dV32 = nullptr;     // EC_PREC_FP32: FP32 copy of the product input (npad, zero tail)
+  float2* dWpx2 = nullptr;   // EC_PREC_FP32X2: C^{-1} as packed FP32 hi/lo pair tiles
+  float2* dVx2 = nullptr;    // EC_PREC_FP32X2: pair copy of the product input (npad, zero tail)
   double* dPart1 = nullptr;  // unit partials of C^{-1} b
   double* dPart2 = nullptr;  // unit partials of C^{-T} y
   double* dYsol = nullptr;   // C^{-1} b (npad, zero tail)
@@ -171,6 +173,7 @@ void free_setup(ec_ctx* c) {
   dfree(c->dL); dfree(c->dR); dfree(c->dZ); dfree(c->dDinv); dfree(c->dE); dfree(c->dV);
   dfree(c->dW); dfree(c->dWp); tile_plan_free(&c->tiles); dfree(c->dPart1);
   dfree(c->dWp32); dfree(c->dLh); dfree(c->dDelta); dfree(c->dRes); dfree(c->dT1); dfree(c->dT2); dfree(c->dV32); dfree(c->dPart2); dfree(c->dYsol);
+  dfree(c->dWpx2); dfree(c->dVx2);
   dfree(c->dRhsM); dfree(c->dYM); dfree(c->dXM);
   dfree(c->dWR); dfree(c->dT); dfree(c->dVtWR); dfree(c->dRrinvT); dfree(c->dPE);
   dfree(c->dCPE); dfree(c->dRD); dfree(c->dLD); dfree(c->dM); dfree(c->dMD); dfree(c->dC);
@@ -314,6 +317,14 @@ ec_status plain_factor(ec_ctx* c) {
       tile_pack_lower(c->stream, c->tiles, c->dL, c->n, c->dLh, 0.5);
       EC_TRY(tile_autotune_f32(c->stream, &c->tiles, c->dWp32, c->dWork, c->dV32, c->dPart1,
                                c->dYsol, c->dPart2, c->st, c->cfg.tile_variant));
+    } else if (c->cfg.precision == EC_PREC_FP32X2) {
+      // FP32 hi/lo pairs: as many bytes as FP64, arithmetic on the FP32 pipe
+      EC_TRY(alloc(&c->dWpx2, tile_packed_doubles(c->tiles)));
+      EC_TRY(alloc(&c->dVx2, npad));
+      cudaMemsetAsync(c->dVx2, 0, sizeof(float2) * npad, c->stream);
+      tile_pack_lower_x2(c->stream, c->tiles, c->dW, n0, c->dWpx2);
+      EC_TRY(tile_autotune_x2(c->stream, &c->tiles, c->dWpx2, c->dWork, c->dVx2, c->dPart1,
+                              c->dYsol, c->dPart2, c->st, c->cfg.tile_variant));
     } else {
       EC_TRY(alloc(&c->dWp, tile_packed_doubles(c->tiles)));
       tile_pack_lower(c->stream, c->tiles, c->dW, n0, c->dWp);
@@ -343,6 +354,11 @@ double* plain_solve(ec_ctx* c, const StepArgs& a, double* b, cudaEvent_t* e3) {
     TrsvSync sy{c->dFlags, c->dFlags + (c->n0 + NB - 1) / NB, c->dTickets, c->dEpoch};
     trsv_pair(c->stream, c->n0, c->dZ, c->n0, c->dDinv, b, b, b, sy, c->trsv_grid, c->spin_limit,
               c->st, e3);
+    return b;
+  }
+  if (c->cfg.precision == EC_PREC_FP32X2) {
+    tile_trmv_pair_x2(c->stream, c->tiles, c->dWpx2, b, c->dVx2, c->dPart1, c->dYsol, c->dPart2,
+                      b, c->st, e3);
     return b;
   }
   if (c->cfg.precision != EC_PREC_FP32) {
@@ -389,14 +405,17 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
   if (cfg->plain_solver != EC_SOLVE_INVERSE && cfg->plain_solver != EC_SOLVE_SUBSTITUTION)
     return EC_ERR_ARG;
   if (cfg->precision != EC_PREC_FP64 && cfg->precision != EC_PREC_BF16 &&
-      cfg->precision != EC_PREC_BF16X3 && cfg->precision != EC_PREC_FP32)
+      cfg->precision != EC_PREC_BF16X3 && cfg->precision != EC_PREC_FP32 &&
+      cfg->precision != EC_PREC_FP32X2)
     return EC_ERR_ARG;
   if ((cfg->precision == EC_PREC_BF16 || cfg->precision == EC_PREC_BF16X3) &&
       cfg->form != EC_FORM_MODAL)
     return EC_ERR_UNSUPPORTED;
-  if (cfg->precision == EC_PREC_FP32 &&
-      (cfg->form != EC_FORM_PLAIN || cfg->plain_solver != EC_SOLVE_INVERSE ||
-       cfg->rhs_mode != EC_RHS_SUM))
+  // plain form: the reduced-precision inverse factor serves the inverse solver of one
+  // summed right-hand side; modal form: the products with U, any right-hand-side mode
+  if ((cfg->precision == EC_PREC_FP32 || cfg->precision == EC_PREC_FP32X2) &&
+      cfg->form == EC_FORM_PLAIN &&
+      (cfg->plain_solver != EC_SOLVE_INVERSE || cfg->rhs_mode != EC_RHS_SUM))
     return EC_ERR_UNSUPPORTED;
   if (cfg->refine_steps < 0 || cfg->refine_steps > 8) return EC_ERR_ARG;
   if (cfg->integrator != EC_INTEG_THETA && cfg->integrator != EC_INTEG_EXACT) return EC_ERR_ARG;
@@ -463,7 +482,8 @@ ec_status ec_setup(ec_ctx* c, int64_t n, const double* L, const double* R, int64
   if ((m > 0 && !E) || (s > 0 && !M) || (p > 0 && !C)) return EC_ERR_ARG;
   if (mem != EC_MEM_HOST && mem != EC_MEM_DEVICE) return EC_ERR_ARG;
   if (m >= n) return EC_ERR_SHAPE;
-  if (c->cfg.precision == EC_PREC_FP32 && m > 0) return EC_ERR_UNSUPPORTED;
+  if (c->cfg.form == EC_FORM_PLAIN && c->cfg.precision == EC_PREC_FP32 && m > 0)
+    return EC_ERR_UNSUPPORTED;
   const bool indep = c->cfg.rhs_mode != EC_RHS_SUM;
   const bool paired = c->cfg.rhs_mode == EC_RHS_PAIRED;
   // (paired read-out computes each trajectory's own probe directly: no per-step dot
@@ -643,6 +663,30 @@ ec_status ec_set_step(ec_ctx* c, double theta, double dt) {
   if (c->cfg.form == EC_FORM_PLAIN) return plain_factor(c);
   EC_TRY(modal_set_step(c->stream, c->modal, theta, dt));
   return collect(c);
+}
+
+ec_status ec_set_precision(ec_ctx* c, int precision) {
+  if (!c) return EC_ERR_ARG;
+  if (precision != EC_PREC_FP64 && precision != EC_PREC_BF16 && precision != EC_PREC_BF16X3 &&
+      precision != EC_PREC_FP32 && precision != EC_PREC_FP32X2)
+    return EC_ERR_ARG;
+  if (!c->ready) return EC_ERR_STATE;
+  if (c->cfg.form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
+  cudaSetDevice(c->cfg.device);
+  const int64_t n = c->n;
+  ec_status rc = modal_set_precision(c->stream, c->modal, precision, c->dRD, c->dLD, c->dM + c->m,
+                                     n, c->dC + c->m, n, c->st);
+  if (rc == EC_OK) rc = collect(c);
+  if (rc != EC_OK) {
+    // keep a usable context: FP64 products from the same modes
+    c->cfg.precision = EC_PREC_FP64;
+    modal_set_precision(c->stream, c->modal, EC_PREC_FP64, c->dRD, c->dLD, c->dM + c->m, n,
+                        c->dC + c->m, n, c->st);
+    cudaStreamSynchronize(c->stream);
+    return rc;
+  }
+  c->cfg.precision = precision;
+  return EC_OK;
 }
 
 ec_status ec_run(ec_ctx* c, int64_t T, const double* src, const double* iD, double* probes,

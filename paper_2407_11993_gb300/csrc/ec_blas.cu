@@ -160,12 +160,13 @@ __global__ void split_sum_kernel(int64_t M, int64_t N, int splits, const double*
 // children's blocks [s, s + bs/2) and [s + bs/2, s + nb) of the block-diagonal Qin;
 //   Qout[top rows, s : s + nb]    = Qin[top, top]       Wm[top rows, s : s + nb]
 //   Qout[bottom rows, s : s + nb] = Qin[bottom, bottom] Wm[bottom rows, s : s + nb]
-// blockIdx.z = 2 z + (0: top, 1: bottom).
-__global__ void __launch_bounds__(256) dgemm_halves_kernel(int64_t n, int64_t bs, const double* Qin,
-                                                           const double* Wm, double* Qout,
-                                                           int64_t ld, const DevStatus* st) {
+// blockIdx.z = 2 (z - z0) + (0: top, 1: bottom) for merges z0, z0 + 1, ...
+__global__ void __launch_bounds__(256) dgemm_halves_kernel(int64_t n, int64_t bs, int64_t z0,
+                                                           const double* Qin, const double* Wm,
+                                                           double* Qout, int64_t ld,
+                                                           const DevStatus* st) {
   if (failed(st)) return;
-  const int64_t s0 = (int64_t)(blockIdx.z >> 1) * bs;
+  const int64_t s0 = (z0 + (int64_t)(blockIdx.z >> 1)) * bs;
   const int64_t nb = (n - s0) < bs ? (n - s0) : bs;
   const int64_t half = bs / 2;
   const int64_t off = (blockIdx.z & 1) ? half : 0;
@@ -445,8 +446,13 @@ void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const d
   const int64_t half = bs / 2;
   const unsigned tm = (unsigned)((half + GEMM_TILE - 1) / GEMM_TILE);
   const unsigned tn = (unsigned)((bs + GEMM_TILE - 1) / GEMM_TILE);
-  dgemm_halves_kernel<<<dim3(tm, tn, (unsigned)(2 * groups)), 256, 0, ::ec::counted(s)>>>(
-      n, bs, Qin, Wm, Qout, ld, st);
+  // gridDim.z is limited to 65535: at most 32767 merges (two halves each) per launch
+  constexpr int64_t ZMAX = 32767;
+  for (int64_t z0 = 0; z0 < groups; z0 += ZMAX) {
+    const int64_t g = (groups - z0) < ZMAX ? (groups - z0) : ZMAX;
+    dgemm_halves_kernel<<<dim3(tm, tn, (unsigned)(2 * g)), 256, 0, ::ec::counted(s)>>>(
+        n, bs, z0, Qin, Wm, Qout, ld, st);
+  }
 }
 
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st,

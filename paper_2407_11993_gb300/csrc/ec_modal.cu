@@ -28,6 +28,7 @@
 
 #include "ec_modal.h"
 #include "ec_oz.h"
+#include "ec_skinny32.h"
 #include "ec_sytrd.h"
 #include "ec_tc.h"
 
@@ -64,10 +65,17 @@ struct ModalState {
   __nv_bfloat16* Ubf_cm_lo = nullptr;
   __nv_bfloat16* Ybf = nullptr;      // right operand (N x ld), hi and lo halves
   size_t ybfCap = 0;
+  // FP32 / FP32-pair copy of U and the scratch of its products (EC_PREC_FP32, _FP32X2)
+  U32 u32;
+  Skinny32Work sk;
   // FP64-accurate tensor-core products (EC_GEMM_TENSOR): workspace, kept for the run's
   // snapshot reconstruction
   int gemm = EC_GEMM_TENSOR;
   OzWork oz;
+  // U's slices, cut on the first FP64 reconstruction and kept (16 bytes per entry): each
+  // later U x then streams them once instead of running U x on the FP64 pipe
+  OzSplit usplit;
+  bool usplit_tried = false;
   // setup scratch
   double* DinvR = nullptr;
   const double* CR = nullptr;
@@ -81,6 +89,9 @@ constexpr int TS = 16;             // steps per shared-memory block of the probe
 constexpr int64_t SUPER = 32768;   // steps per launch group (bounds the partial-sum buffer)
 constexpr int64_t CH_MIN = 1024;   // shortest time chunk; runs up to this length are one chunk
 constexpr int64_t ORM_GROUP = 1024;  // reflectors per compact-WY group of the tensor-core back-transform
+// from this size on, FP64 snapshot reconstructions use U's kept slices (below it the
+// FP64 cores finish U x in about the time of the tensor path's launches)
+constexpr int64_t PRESPLIT_MIN = 4096;
 
 cudaError_t dalloc(void** p, size_t b) { return device_alloc(p, b); }
 
@@ -411,7 +422,21 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
   const int64_t n0 = ms->n0;
   if (N <= 0) return EC_OK;
   if (K < 0) K = n0;
+  if (ms->precision == EC_PREC_FP32 || ms->precision == EC_PREC_FP32X2)
+    return skinny32_product(s, ms->u32, n0, trans_u, N, K, Y, lds, C, ldc, &ms->sk, st);
   if (ms->precision == EC_PREC_FP64) {
+    if (ms->gemm == EC_GEMM_TENSOR && !trans_u && n0 >= PRESPLIT_MIN) {
+      if (!ms->usplit.slices && !ms->usplit_tried) {
+        ms->usplit_tried = true;
+        if (oz_presplit(s, N_, n0, n0, ms->U, n0, &ms->usplit) != EC_OK)
+          oz_split_free(&ms->usplit);               // no room: the per-call paths below
+      }
+      if (ms->usplit.slices) {
+        const ec_status rc = oz_gemm_presplit(s, ms->usplit, K, N_, N, Y, lds, 0.0, C, ldc,
+                                              &ms->oz, st);
+        if (rc != EC_ERR_OOM) return rc;
+      }
+    }
     gemm_auto(s, ms->gemm == EC_GEMM_TENSOR ? &ms->oz : nullptr, trans_u ? T_ : N_, N_, n0, N, K,
               1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
     return EC_OK;
@@ -440,6 +465,9 @@ void modal_free(ModalState* ms) {
   for (__nv_bfloat16* p : bs)
     if (p) cudaFree(p);
   oz_free(&ms->oz);
+  oz_split_free(&ms->usplit);
+  u32_free(&ms->u32);
+  skinny32_free(&ms->sk);
   delete ms;
 }
 
@@ -458,6 +486,55 @@ int64_t modal_state_size(const ModalState* ms) { return ms->n0 * ms->ntraj; }
 const double* modal_tau(ModalState* ms) { return ms->tau; }
 const double* modal_U(ModalState* ms) { return ms->U; }
 
+
+// Reduced-precision copy of U for the chosen arithmetic (dropping any other), then the
+// projections B = U^T [R_D | L_D | M_0] and G^T = U^T (C K)^T with that arithmetic.
+ec_status modal_products_prepare(cudaStream_t s, ModalState* ms, int precision, const double* RD,
+                                 const double* LD, const double* Msrc, int64_t ldM,
+                                 const double* CK, int64_t ldC, DevStatus* st) {
+  const int64_t n0 = ms->n0;
+  ms->precision = precision;
+  u32_free(&ms->u32);
+  for (__nv_bfloat16** p : {&ms->Ubf_rm, &ms->Ubf_cm, &ms->Ubf_rm_lo, &ms->Ubf_cm_lo}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (precision == EC_PREC_FP32 || precision == EC_PREC_FP32X2)
+    MS_TRY(u32_build(s, n0, ms->U, n0, precision == EC_PREC_FP32X2 ? 1 : 0, &ms->u32));
+  if (precision == EC_PREC_BF16 || precision == EC_PREC_BF16X3) {
+    const int64_t ld = bf16_ld(n0);
+    const bool x3 = precision == EC_PREC_BF16X3;
+    MS_TRY(alloc_n(&ms->Ubf_rm, (size_t)n0 * ld));
+    MS_TRY(alloc_n(&ms->Ubf_cm, (size_t)n0 * ld));
+    if (x3) {
+      MS_TRY(alloc_n(&ms->Ubf_rm_lo, (size_t)n0 * ld));
+      MS_TRY(alloc_n(&ms->Ubf_cm_lo, (size_t)n0 * ld));
+    }
+    to_bf16(s, n0, n0, ms->U, n0, 0, ms->Ubf_rm, ld, x3 ? ms->Ubf_rm_lo : nullptr);
+    to_bf16(s, n0, n0, ms->U, n0, 1, ms->Ubf_cm, ld, x3 ? ms->Ubf_cm_lo : nullptr);
+  }
+  if (ms->ncoef > 0) {
+    double* Gm = nullptr;
+    if (alloc_n(&Gm, (size_t)n0 * ms->ncoef)) return EC_ERR_OOM;
+    if (ms->m > 0) {
+      copy_matrix(s, n0, ms->m, RD, n0, Gm, n0);
+      copy_matrix(s, n0, ms->m, LD, n0, Gm + n0 * ms->m, n0);
+    }
+    if (ms->S > 0) copy_matrix(s, n0, ms->S, Msrc, ldM, Gm + n0 * 2 * ms->m, n0);
+    ec_status rc2 = modal_product(s, ms, 1, ms->ncoef, Gm, n0, ms->B, n0, st);
+    cudaStreamSynchronize(s);
+    cudaFree(Gm);
+    if (rc2 != EC_OK) return rc2;
+  }
+  if (ms->P > 0) MS_TRY(modal_product(s, ms, 1, ms->P, CK, ldC, ms->Gt, n0, st));
+  return EC_OK;
+}
+
+ec_status modal_set_precision(cudaStream_t s, ModalState* ms, int precision, const double* RD,
+                              const double* LD, const double* Msrc, int64_t ldM,
+                              const double* CK, int64_t ldC, DevStatus* st) {
+  return modal_products_prepare(s, ms, precision, RD, LD, Msrc, ldM, CK, ldC, st);
+}
 
 ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, ec_timing* tim) {
   const int64_t n0 = a.n0, ld = a.ld;
@@ -585,33 +662,8 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   tim->backtransform_ms = t.ms();
   cleanup();
   // a7: projections and per-mode coefficients
-  ms->precision = a.precision;
-  if (a.precision != EC_PREC_FP64) {
-    const int64_t ld = bf16_ld(n0);
-    const bool x3 = a.precision == EC_PREC_BF16X3;
-    MS_TRY(alloc_n(&ms->Ubf_rm, (size_t)n0 * ld));
-    MS_TRY(alloc_n(&ms->Ubf_cm, (size_t)n0 * ld));
-    if (x3) {
-      MS_TRY(alloc_n(&ms->Ubf_rm_lo, (size_t)n0 * ld));
-      MS_TRY(alloc_n(&ms->Ubf_cm_lo, (size_t)n0 * ld));
-    }
-    to_bf16(s, n0, n0, ms->U, n0, 0, ms->Ubf_rm, ld, x3 ? ms->Ubf_rm_lo : nullptr);
-    to_bf16(s, n0, n0, ms->U, n0, 1, ms->Ubf_cm, ld, x3 ? ms->Ubf_cm_lo : nullptr);
-  }
-  if (ms->ncoef > 0) {
-    double* Gm = nullptr;
-    if (alloc_n(&Gm, (size_t)n0 * ms->ncoef)) return EC_ERR_OOM;
-    if (a.m > 0) {
-      copy_matrix(s, n0, a.m, a.RD, n0, Gm, n0);
-      copy_matrix(s, n0, a.m, a.LD, n0, Gm + n0 * a.m, n0);
-    }
-    if (a.S > 0) copy_matrix(s, n0, a.S, a.Msrc, a.ldM, Gm + n0 * 2 * a.m, n0);
-    ec_status rc2 = modal_product(s, ms, 1, ms->ncoef, Gm, n0, ms->B, n0, a.st);
-    cudaStreamSynchronize(s);
-    cudaFree(Gm);
-    if (rc2 != EC_OK) return rc2;
-  }
-  if (a.P > 0) MS_TRY(modal_product(s, ms, 1, a.P, a.CK, a.ldC, ms->Gt, n0, a.st));
+  MS_TRY(modal_products_prepare(s, ms, a.precision, a.RD, a.LD, a.Msrc, a.ldM, a.CK, a.ldC,
+                                a.st));
   ms->integ = a.integ;
   ms->nkeep = n0;
   coef_kernel<<<(unsigned)((n0 + 255) / 256 < 1024 ? (n0 + 255) / 256 : 1024), 256, 0, ::ec::counted(s)>>>(

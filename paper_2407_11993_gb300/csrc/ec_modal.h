@@ -35,6 +35,11 @@ ModalState* modal_create();
 void modal_free(ModalState* ms);
 ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, ec_timing* tim);
 ec_status modal_set_step(cudaStream_t s, ModalState* ms, double theta, double dt);
+// Switch the arithmetic of the products with U (EC_PREC_*): rebuilds the reduced copy
+// of U and the projections from the same modes; the modal state is kept.
+ec_status modal_set_precision(cudaStream_t s, ModalState* ms, int precision, const double* RD,
+                              const double* LD, const double* Msrc, int64_t ldM,
+                              const double* CK, int64_t ldC, DevStatus* st);
 // ev (optional): receives an event pair around every scan launch.
 ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& a,
                     std::vector<cudaEvent_t>* ev = nullptr);

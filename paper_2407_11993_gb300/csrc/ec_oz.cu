@@ -17,7 +17,7 @@
 //     s + t <= 7 are kept (the dropped ones lie below 2^-61 of the row / column scales,
 //     so the product keeps FP64 accuracy even where a row's entries span many decades).
 //
-// One CTA computes a 128 x 64 tile of C over a K range of at most 192:
+// One CTA per SM (persistent) computes 128 x 64 tiles of C over a K range of at most 192:
 //   * warp 0 / lane 0 streams, per 32-wide K block, all eight A slices (one 3-D TMA
 //     box of 128 x 32 x 8) and all eight B slices (64 x 32 x 8) into a two-stage
 //     shared-memory ring (64-byte swizzle), guarded by mbarriers;
@@ -27,9 +27,10 @@
 //     sums are exact (integers times 2^-8d below 2^24 in magnitude, because
 //     (d + 1) 2^14 K < 2^24 for K <= 192), and one shared by d = 5, 6, 7, whose FP32
 //     rounding lies below 2^-60 of the leading diagonal;
-//   * all eight warps then read the accumulators (warp w reads TMEM lanes
+//   * eight epilogue warps read the accumulators (warp w reads TMEM lanes
 //     32 (w % 4) .. + 31, the tile's rows, for half of the columns), rebuild each
-//     entry as an exact 64-bit integer at granularity
+//     entry as an exact 64-bit integer (staged in tensor memory, which releases the
+//     accumulators to the next tile's MMAs) at granularity
 //     2^-40, convert it to binary64 with integer instructions (one rounding), apply
 //     2^(e_i + f_j - 56) and alpha, and add beta C.
 // Longer K is done as consecutive launches that accumulate into C in FP64.
@@ -131,6 +132,7 @@ struct OzArgs {
   int k0, klen;            // K range of this launch
   int tiles_m, tiles_n;
   int tri;                 // keep only rows >= columns (of the C block)
+  int amode, bmode;        // alpha: 0 = 1, 1 = -1, 2 = other; beta: 0 = 0, 1 = 1, 2 = other
   double alpha, beta;
   double* C;
   int64_t ldc;
@@ -149,25 +151,70 @@ __device__ __forceinline__ void tile_of(int t, int tiles_m, int tiles_n, int& bm
   bm = g * GROUP_M + (r - bn * gm);
 }
 
-constexpr int OZ_THREADS = 256;         // 8 warps: two per TMEM lane quarter in the epilogue
+constexpr int EPI_WARPS = 8;                       // two per TMEM lane quarter
+constexpr int OZ_THREADS = (2 + EPI_WARPS) * 32;   // producer, MMA issuer, epilogue
+constexpr int STAGE_COL = NACC * TN;               // TMEM columns 384..511: the exact integers
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Tiles of this launch handled by a CTA: t = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// lower-triangle products skip the tiles entirely above the diagonal.  Every warp
+// role walks the same sequence.
+__device__ __forceinline__ bool next_tile(const OzArgs& a, int& t, int& m0, int& n0) {
+  const int ntiles = a.tiles_m * a.tiles_n;
+  for (; t < ntiles; t += gridDim.x) {
+    int bm, bn;
+    tile_of(t, a.tiles_m, a.tiles_n, bm, bn);
+    m0 = bm * TM;
+    n0 = bn * TN;
+    if (!(a.tri && n0 > m0 + TM - 1)) return true;
+  }
+  return false;
+}
+
+// Persistent: one CTA per SM walks its tiles.  Warp 0 (one lane) streams the slices of
+// every tile's K blocks through the shared-memory ring without stopping at tile
+// boundaries; warp 1 (one lane) issues the MMAs of a tile once the epilogue has
+// released the accumulators; warps 2..9 first fold the six accumulators of each entry
+// into its exact 64-bit integer (kept in TMEM columns 384..511), release the
+// accumulators -- the next tile's MMAs start -- and then convert and store while those
+// run.
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                          const __grid_constant__ CUtensorMap mapB,
                                                          const OzArgs a, DevStatus* st) {
-  int bm, bn;
-  tile_of(blockIdx.x, a.tiles_m, a.tiles_n, bm, bn);
-  const int m0 = bm * TM, n0 = bn * TN;
-  // lower-triangle products: tiles entirely above the diagonal have nothing to do
-  if (a.tri && n0 > m0 + TM - 1) return;
-
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full, acc_empty,
+      done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued, consumed, skip;
-  // an earlier failure in the pipeline: the whole CTA leaves together
   if (threadIdx.x == 0) skip = *(volatile int*)&st->code;
   __syncthreads();
-  if (skip) return;
+  if (skip) return;                                  // an earlier failure: leave together
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (a.klen + TK - 1) / TK;
@@ -184,6 +231,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, EPI_WARPS);
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     issued = 0;
@@ -195,120 +244,173 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // producer: all eight slices of A and of B for each 32-wide K block
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t use = kb / STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty_bar[s], (use - 1) & 1, st, 41)) {
-        abort_flag = 1;
-        break;
-      }
-      uint8_t* sa = smem + s * STAGE_BYTES;
-      uint8_t* sb = sa + A_BYTES;
-      mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-      tma_load_3d(sa, &mapA, &full_bar[s], a.k0 + kb * TK, m0, 0);
-      tma_load_3d(sb, &mapB, &full_bar[s], a.k0 + kb * TK, n0, 0);
-      *(volatile int*)&issued = kb + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer: one MMA per slice pair and 16-wide K step
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1, st, 42)) {
-        abort_flag = 1;
-        break;
-      }
-      *(volatile int*)&consumed = kb + 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-      for (int d = 0; d <= OZ_DMAX; ++d) {
-        const int acc = d < OZ_EXACT ? d : OZ_EXACT;
-        const uint32_t tacc = tmem + (uint32_t)(acc * TN);
-#pragma unroll
-        for (int si = 0; si <= d; ++si) {
-          const int ti = d - si;
-          if (si >= OZ_S || ti >= OZ_S) continue;
-          const uint64_t da = smem_desc(sa + si * A_SLICE);
-          const uint64_t db = smem_desc(sb + ti * B_SLICE);
-#pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk) {
-            // the first product into each accumulator overwrites it
-            const bool first = kb == 0 && kk == 0 && si == 0 && (d < OZ_EXACT || d == OZ_EXACT);
-            mma_bf16(tacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: all eight slices of A and of B for each 32-wide K block, tile after tile
+      uint32_t it = 0;
+      int t = blockIdx.x, m0 = 0, n0 = 0;
+      for (; next_tile(a, t, m0, n0) && !*(volatile int*)&abort_flag; t += gridDim.x) {
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t use = it / STAGES;
+          if (it >= STAGES && !mbar_wait(&empty_bar[s], (use - 1) & 1, st, 41)) {
+            *(volatile int*)&abort_flag = 1;
+            break;
           }
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          uint8_t* sb = sa + A_BYTES;
+          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+          tma_load_3d(sa, &mapA, &full_bar[s], a.k0 + kb * TK, m0, 0);
+          tma_load_3d(sb, &mapB, &full_bar[s], a.k0 + kb * TK, n0, 0);
+          *(volatile int*)&issued = (int)(it + 1);
         }
       }
-      mma_commit(&empty_bar[s]);
     }
-    // always committed: arrives once every MMA this thread issued has completed
-    mma_commit(&done_bar);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: one MMA per slice pair and 16-wide K step
+      uint32_t it = 0, tc = 0;
+      int t = blockIdx.x, m0 = 0, n0 = 0;
+      bool ok = true;
+      for (; ok && next_tile(a, t, m0, n0) && !*(volatile int*)&abort_flag; t += gridDim.x, ++tc) {
+        // the epilogue must have taken the previous tile's accumulators
+        if (tc > 0 && !mbar_wait(&acc_empty, (tc - 1) & 1, st, 46)) {
+          *(volatile int*)&abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, st, 42)) {
+            *(volatile int*)&abort_flag = 1;
+            ok = false;
+            break;
+          }
+          *(volatile int*)&consumed = (int)(it + 1);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int d = 0; d <= OZ_DMAX; ++d) {
+            const int acc = d < OZ_EXACT ? d : OZ_EXACT;
+            const uint32_t tacc = tmem + (uint32_t)(acc * TN);
+#pragma unroll
+            for (int si = 0; si <= d; ++si) {
+              const int ti = d - si;
+              if (si >= OZ_S || ti >= OZ_S) continue;
+              const uint64_t da = smem_desc(sa + si * A_SLICE);
+              const uint64_t db = smem_desc(sb + ti * B_SLICE);
+#pragma unroll
+              for (int kk = 0; kk < TK / 16; ++kk) {
+                // the first product into each accumulator overwrites it
+                const bool first = kb == 0 && kk == 0 && si == 0 && d <= OZ_EXACT;
+                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+              }
+            }
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        // arrives once this tile's MMAs have completed (also after a failure, so the
+        // epilogue's wait ends)
+        mma_commit(&acc_full);
+      }
+      // arrives once every MMA this thread issued has completed
+      mma_commit(&done_bar);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and half of
+    // the columns, [32 h, 32 h + 32) with h = (w - 2) / 4
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    uint32_t tc = 0;
+    int t = blockIdx.x, m0 = 0, n0 = 0;
+    for (; next_tile(a, t, m0, n0); t += gridDim.x, ++tc) {
+      if (!mbar_wait(&acc_full, tc & 1, st, 47)) {
+        *(volatile int*)&abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (*(volatile int*)&abort_flag) break;
+      const int row = m0 + quarter * 32 + lane;
+      const bool row_ok = row < a.M;
+      // phase 1: the exact integer of each entry at granularity 2^-40 (diagonal d holds
+      // integers times 2^-8d): the top two diagonals in 32 bits, the rest by wide
+      // multiply-adds, then the shared group of the small diagonals rounded at 2^-40
+#pragma unroll 1
+      for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
+        uint32_t r[NACC][16];
+#pragma unroll
+        for (int q = 0; q < NACC; ++q) tmem_ld16(lane_base + (uint32_t)(q * TN + c0), r[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t xs[32];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int i0 = __float2int_rn(__uint_as_float(r[0][j]));
+          const int i1 = __float2int_rn(__uint_as_float(r[1][j]) * 256.0f);
+          const int i2 = __float2int_rn(__uint_as_float(r[2][j]) * 65536.0f);
+          const int i3 = __float2int_rn(__uint_as_float(r[3][j]) * 16777216.0f);
+          const int i4 = __float2int_rn(__uint_as_float(r[4][j]) * 4294967296.0f);
+          const int ig = __float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);
+          int64_t X = (int64_t)(i0 * 256 + i1) * 4294967296ll;
+          X += (int64_t)i2 * (1 << 24);
+          X += (int64_t)i3 * (1 << 16);
+          X += (int64_t)i4 * (1 << 8);
+          X += ig;
+          xs[2 * j] = (uint32_t)(uint64_t)X;
+          xs[2 * j + 1] = (uint32_t)((uint64_t)X >> 32);
+        }
+        tmem_st32(lane_base + (uint32_t)(STAGE_COL + 2 * c0), xs);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) dev::mbar_arrive(&acc_empty);
+      // phase 2 (overlaps the next tile's MMAs): binary64 conversion, scaling, C update
+      const int erow = row_ok ? a.ea[row] - 56 : 0;
+#pragma unroll 1
+      for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
+        uint32_t xs[32];
+        tmem_ld32(lane_base + (uint32_t)(STAGE_COL + 2 * c0), xs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!row_ok) continue;
+        // columns of this chunk all inside C (and, for lower-triangle products, all at
+        // or left of this row): no per-entry checks
+        const bool whole = (n0 + c0 + 16 <= a.N) && (!a.tri || n0 + c0 + 15 <= row);
+        int ebc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ebc[j] = (n0 + c0 + j < a.N) ? a.eb[n0 + c0 + j] : 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (!whole && (col >= a.N || (a.tri && col > row))) continue;
+          const int64_t X = (int64_t)(((uint64_t)xs[2 * j + 1] << 32) | xs[2 * j]);
+          const int sc = erow + ebc[j];
+          uint64_t bits;
+          if (!oz::i64_scaled_to_f64_bits_fast(X, sc, &bits)) {
+            const double slow = X == 0 ? 0.0 : ldexp((double)X, sc);
+            bits = (uint64_t)__double_as_longlong(slow);
+          }
+          // alpha and beta arrive classified, so no FP64 compare runs per entry
+          if (a.amode == 1) bits ^= (1ull << 63);
+          double v = __longlong_as_double((long long)bits);
+          if (a.amode == 2) v *= a.alpha;
+          double* cp = a.C + (int64_t)row + (int64_t)col * a.ldc;
+          if (a.bmode == 0) *cp = v;
+          else if (a.bmode == 1) *cp += v;
+          else *cp = fma(a.beta, *cp, v);
+        }
+      }
+    }
   }
   __syncwarp();
   __syncthreads();
   if (threadIdx.x == 0) {
+    // no MMA may still write tensor memory when it is freed
     if (!mbar_wait(&done_bar, 0, st, 43)) abort_flag = 1;
+    // a failed pipeline: let the copies already issued land before shared memory is released
     if (abort_flag)
-      for (int kb = consumed; kb < issued; ++kb)
-        mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1, st, 44);
-  }
-  __syncthreads();
-  const bool good = (abort_flag == 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (good) {
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and half of the
-    // columns: [32 (w / 4), 32 (w / 4) + 32)
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = m0 + quarter * 32 + lane;
-    const bool row_ok = row < a.M;
-    const int erow = row_ok ? a.ea[row] - 56 : 0;
-    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-    for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
-      uint32_t r[NACC][16];
-#pragma unroll
-      for (int q = 0; q < NACC; ++q) tmem_ld16(lane_base + (uint32_t)(q * TN + c0), r[q]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!row_ok) continue;
-      // columns of this chunk all inside C (and, for lower-triangle products, all at or
-      // left of this row): no per-entry checks
-      const bool whole = (n0 + c0 + 16 <= a.N) && (!a.tri || n0 + c0 + 15 <= row);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c0 + j;
-        if (!whole && (col >= a.N || (a.tri && col > row))) continue;
-        // exact integer at granularity 2^-40 (diagonal d holds integers times 2^-8d):
-        // the top two diagonals in 32 bits, the rest by wide multiply-adds, then the
-        // shared group of the small diagonals rounded at 2^-40
-        const int i0 = __float2int_rn(__uint_as_float(r[0][j]));
-        const int i1 = __float2int_rn(__uint_as_float(r[1][j]) * 256.0f);
-        const int i2 = __float2int_rn(__uint_as_float(r[2][j]) * 65536.0f);
-        const int i3 = __float2int_rn(__uint_as_float(r[3][j]) * 16777216.0f);
-        const int i4 = __float2int_rn(__uint_as_float(r[4][j]) * 4294967296.0f);
-        const int ig = __float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);
-        int64_t X = (int64_t)(i0 * 256 + i1) * 4294967296ll;
-        X += (int64_t)i2 * (1 << 24);
-        X += (int64_t)i3 * (1 << 16);
-        X += (int64_t)i4 * (1 << 8);
-        X += ig;
-        const int sc = erow + a.eb[col];
-        uint64_t bits;
-        if (!oz::i64_scaled_to_f64_bits_fast(X, sc, &bits)) {
-          const double slow = X == 0 ? 0.0 : ldexp((double)X, sc);
-          bits = (uint64_t)__double_as_longlong(slow);
-        }
-        double v;
-        if (a.alpha == -1.0) v = __longlong_as_double((long long)(bits ^ (1ull << 63)));
-        else if (a.alpha == 1.0) v = __longlong_as_double((long long)bits);
-        else v = a.alpha * __longlong_as_double((long long)bits);
-        double* cp = a.C + (int64_t)row + (int64_t)col * a.ldc;
-        if (a.beta == 0.0) *cp = v;
-        else if (a.beta == 1.0) *cp += v;
-        else *cp = fma(a.beta, *cp, v);
-      }
-    }
+      for (int it = consumed; it < issued; ++it)
+        mbar_wait(&full_bar[it % STAGES], (it / STAGES) & 1, st, 44);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -408,18 +510,24 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 8.
-bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
-                    int64_t ldk, int box_rows) {
+// 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 8;
+// consecutive slices lie Rs * ldk elements apart (Rs >= R).
+bool make_slice_map_ld(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
+                       int64_t ldk, int64_t Rs, int box_rows) {
   EncodeTiledFn fn = (EncodeTiledFn)tensor_map_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)OZ_S};
-  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(R * ldk) * 2};
+  cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(Rs * ldk) * 2};
   cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
   cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
+                    int64_t ldk, int box_rows) {
+  return make_slice_map_ld(map, base, R, K, ldk, R, box_rows);
 }
 
 ec_status grow_ws(OzWork* w, int64_t slice_elems, int64_t rows) {
@@ -496,6 +604,110 @@ void oz_free(OzWork* w) {
   *w = OzWork{};
 }
 
+namespace {
+
+// One mi x nj panel of C = alpha A B + beta C from the slices behind maps ma, mb: K in
+// chunks of OZ_KCHUNK, the first with beta, the rest accumulating.
+ec_status launch_panel(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int64_t mi,
+                       int64_t nj, int64_t K, double alpha, double beta, double* C, int64_t ldc,
+                       const int* eA, const int* eB, int tri, DevStatus* st) {
+  OzArgs args{};
+  args.M = (int)mi;
+  args.N = (int)nj;
+  args.tiles_m = (int)((mi + TM - 1) / TM);
+  args.tiles_n = (int)((nj + TN - 1) / TN);
+  args.alpha = alpha;
+  args.C = C;
+  args.ldc = ldc;
+  args.ea = eA;
+  args.eb = eB;
+  args.tri = tri;
+  const int64_t tiles = (int64_t)args.tiles_m * args.tiles_n;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms());
+  for (int64_t k0 = 0; k0 < K; k0 += OZ_KCHUNK) {
+    args.k0 = (int)k0;
+    args.klen = (int)std::min<int64_t>(OZ_KCHUNK, K - k0);
+    args.beta = k0 == 0 ? beta : 1.0;
+    args.amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
+    args.bmode = args.beta == 0.0 ? 0 : args.beta == 1.0 ? 1 : 2;
+    oz_gemm_kernel<<<grid, OZ_THREADS, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb, args, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+
+void set_kernel_attributes() {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set))
+    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+}  // namespace
+
+ec_status oz_presplit(cudaStream_t s, Op ta, int64_t R, int64_t K, const double* A, int64_t lda,
+                      OzSplit* out) {
+  oz_split_free(out);
+  if (R <= 0 || K <= 0) return EC_ERR_ARG;
+  if (R > (1ll << 30)) return EC_ERR_UNSUPPORTED;
+  const int64_t ldk = (K + 7) / 8 * 8;
+  unsigned long long* maxb = nullptr;
+  if (device_alloc((void**)&out->slices, sizeof(__nv_bfloat16) * (size_t)OZ_S * R * ldk) !=
+          cudaSuccess ||
+      device_alloc((void**)&out->exps, sizeof(int) * (size_t)R) != cudaSuccess ||
+      device_alloc((void**)&maxb, sizeof(unsigned long long) * (size_t)R) != cudaSuccess) {
+    cudaGetLastError();
+    if (maxb) cudaFree(maxb);
+    oz_split_free(out);
+    return EC_ERR_OOM;
+  }
+  const int64_t ars = ta == N_ ? 1 : lda, aks = ta == N_ ? lda : 1;
+  split(s, R, K, A, ars, aks, maxb, out->slices, ldk, out->exps);
+  cudaStreamSynchronize(s);
+  cudaFree(maxb);
+  out->R = R;
+  out->K = K;
+  out->ldk = ldk;
+  return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+
+void oz_split_free(OzSplit* a) {
+  if (a->slices) cudaFree(a->slices);
+  if (a->exps) cudaFree(a->exps);
+  *a = OzSplit{};
+}
+
+ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb, int64_t N,
+                           const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                           OzWork* w, DevStatus* st) {
+  if (N <= 0 || a.R <= 0) return EC_OK;
+  if (!w || !a.slices || kuse <= 0 || kuse > a.K) return EC_ERR_ARG;
+  if (N > (1ll << 30)) return EC_ERR_UNSUPPORTED;
+  if (!tensor_map_encode_fn()) return EC_ERR_UNSUPPORTED;
+  set_kernel_attributes();
+  const int64_t ldk = a.ldk;                 // B's slices share A's K layout
+  const int64_t per_row = (int64_t)OZ_S * ldk;
+  int64_t pn = w->cap_elems / per_row / TN * TN;
+  if (pn < TN) pn = TN;
+  if (pn > N) pn = N;
+  {
+    const ec_status g = grow_ws(w, per_row * pn, pn);
+    if (g != EC_OK) return g;
+  }
+  CUtensorMap ma;
+  // the map covers kuse columns of the slices (ldk stays a.ldk): reads past kuse are zero
+  if (!make_slice_map_ld(&ma, a.slices, a.R, kuse, ldk, a.R, TM)) return EC_ERR_CUDA;
+  const int64_t brs = tb == N_ ? ldb : 1, bks = tb == N_ ? 1 : ldb;
+  for (int64_t j0 = 0; j0 < N; j0 += pn) {
+    const int64_t nj = std::min(pn, N - j0);
+    split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
+    CUtensorMap mb;
+    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, TN)) return EC_ERR_CUDA;
+    const ec_status rc = launch_panel(s, ma, mb, a.R, nj, kuse, 1.0, beta, C + j0 * ldc, ldc,
+                                      a.exps, w->exps, 0, st);
+    if (rc != EC_OK) return rc;
+  }
+  return EC_OK;
+}
+
 ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                   double* C, int64_t ldc, int tri, OzWork* w, DevStatus* st) {
@@ -511,9 +723,7 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
   if (tri && M != N) return EC_ERR_ARG;
   if (M > (1ll << 30) || N > (1ll << 30)) return EC_ERR_UNSUPPORTED;
   if (!tensor_map_encode_fn()) return EC_ERR_UNSUPPORTED;
-  static std::atomic<unsigned long long> attr_set{0};
-  if (first_on_device(attr_set))
-    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  set_kernel_attributes();
   const int64_t ldk = (K + 7) / 8 * 8;
   // panels so that the slices of one A panel and one B panel fit the workspace cap
   const int64_t per_row = (int64_t)OZ_S * ldk;
@@ -550,28 +760,11 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
       CUtensorMap ma, mb;
       if (!make_slice_map(&ma, sA, mi, K, ldk, TM) || !make_slice_map(&mb, sB, nj, K, ldk, TN))
         return EC_ERR_CUDA;
-      OzArgs args{};
-      args.M = (int)mi;
-      args.N = (int)nj;
-      args.tiles_m = (int)((mi + TM - 1) / TM);
-      args.tiles_n = (int)((nj + TN - 1) / TN);
-      args.alpha = alpha;
-      args.C = C + i0 + j0 * ldc;
-      args.ldc = ldc;
-      args.ea = eA;
-      args.eb = eB;
       // a tri panel on the diagonal (i0 == j0) keeps rows >= columns; a panel below it
       // is full
-      args.tri = (tri && i0 == j0) ? 1 : 0;
-      const int64_t tiles = (int64_t)args.tiles_m * args.tiles_n;
-      for (int64_t k0 = 0; k0 < K; k0 += OZ_KCHUNK) {
-        args.k0 = (int)k0;
-        args.klen = (int)std::min<int64_t>(OZ_KCHUNK, K - k0);
-        args.beta = k0 == 0 ? beta : 1.0;
-        oz_gemm_kernel<<<(unsigned)tiles, OZ_THREADS, SMEM_BYTES, ::ec::counted(s)>>>(ma, mb,
-                                                                                    args, st);
-      }
-      if (cudaGetLastError() != cudaSuccess) return EC_ERR_CUDA;
+      const ec_status rc = launch_panel(s, ma, mb, mi, nj, K, alpha, beta, C + i0 + j0 * ldc,
+                                        ldc, eA, eB, (tri && i0 == j0) ? 1 : 0, st);
+      if (rc != EC_OK) return rc;
     }
   }
   return EC_OK;

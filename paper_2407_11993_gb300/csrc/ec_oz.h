@@ -36,4 +36,22 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                   double* C, int64_t ldc, int tri, OzWork* w, DevStatus* st);
 
+// The slices of a fixed left operand op(A) (R x K, rows scaled by their own powers of
+// two), cut once and reused by every later product with it: a product with few right
+// columns then reads 16 bytes per entry of A instead of splitting A again (24 bytes of
+// traffic per entry on top).  Memory: 16 R ldk bytes.
+struct OzSplit {
+  __nv_bfloat16* slices = nullptr;      // [8][R][ldk]
+  int* exps = nullptr;                  // R
+  int64_t R = 0, K = 0, ldk = 0;
+};
+// EC_ERR_OOM when the slices do not fit (out stays empty).
+ec_status oz_presplit(cudaStream_t s, Op ta, int64_t R, int64_t K, const double* A, int64_t lda,
+                      OzSplit* out);
+void oz_split_free(OzSplit* a);
+// C = op(A)[:, :kuse] op(B) + beta C with op(A) from `a` (kuse <= a.K), op(B) kuse x N.
+ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb, int64_t N,
+                           const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                           OzWork* w, DevStatus* st);
+
 }  // namespace ec

@@ -337,8 +337,9 @@ void ormtr_lower_grouped(cudaStream_t s, int64_t n, const double* A, int64_t lda
       form_t_kernel<<<1, 64, 0, ::ec::counted(s)>>>(kb, G + c + c * gb, gb, tau, b0 + c,
                                                     T + c + c * gb, gb);
       if (c > 0) {
-        dgemm(s, N_, N_, c, kb, c, 1.0, T, gb, G + c * gb, gb, 0.0, X, gb, 0, st);
-        dgemm(s, N_, N_, c, kb, kb, -1.0, X, gb, T + c + c * gb, gb, 0.0, T + c * gb, gb, 0, st);
+        gemm_auto(s, oz, N_, N_, c, kb, c, 1.0, T, gb, G + c * gb, gb, 0.0, X, gb, 0, st);
+        gemm_auto(s, oz, N_, N_, c, kb, kb, -1.0, X, gb, T + c + c * gb, gb, 0.0, T + c * gb, gb,
+                  0, st);
       }
     }
     // Y[r0:, :] <- (I - V T V^T) Y[r0:, :]
@@ -481,6 +482,94 @@ __global__ void __launch_bounds__(256) symv_tile_kernel(int64_t n, const double*
     pcol[I * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
 }
 
+// Column-strip form of the same product: CTA (k, J) takes the tiles (I, J) with
+// I in [J + k SEG, J + (k+1) SEG) of the 64-column strip J, loads each tile with
+// asynchronous 8-byte copies while the previous one is used, writes the row part of
+// every tile (prow[J][rows of I]) and keeps the column part of its whole segment in
+// registers, written once (pcol[k][columns of J]).  For a row r of block B:
+//   (A22 v)[r] = sum_{J <= B} prow[J][r] + sum_{k < nseg(B)} pcol[k][r],
+// nseg(B) = ceil((nbk - B) / SEG), summed in that order by p_latrd_kernel.
+constexpr int SEG = 16;
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double* A, int64_t lda,
+                                                         int64_t j, const double* v, double* prow,
+                                                         double* pcol, int64_t mp) {
+  extern __shared__ double sbuf[];                  // two tiles, As[b][c][r] stride 65
+  __shared__ double vr[2][64], vc[64];
+  __shared__ double red[4][64];
+  const int64_t s0 = j + 1, m = n - s0;
+  const int64_t nbk = (m + 63) / 64;
+  const int64_t J = blockIdx.y, k = blockIdx.x;
+  const int64_t I0 = J + k * SEG;
+  if (I0 >= nbk) return;
+  const int64_t I1 = (I0 + SEG < nbk) ? I0 + SEG : nbk;
+  const int tid = threadIdx.x, lo = tid & 63, qt = tid >> 6;
+  const int64_t c0 = J * 64;
+  if (tid < 64) vc[tid] = (c0 + tid < m) ? v[s0 + c0 + tid] : 0.0;
+  auto load = [&](int64_t I, int b) {
+    double* As = sbuf + b * 64 * 65;
+    const int64_t r0 = I * 64;
+    for (int q = tid; q < 64 * 64; q += 256) {
+      const int rr = q & 63, cc = q >> 6;
+      const int64_t r = r0 + rr, c = c0 + cc;
+      const bool ok = r < m && c < m && (I != J || rr >= cc);
+      cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + r) + (s0 + c) * lda)
+                                      : (const void*)A, ok);
+    }
+    if (tid < 64) vr[b][tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  double colacc = 0.0;     // column part of (lo, qt) over the segment
+  load(I0, 0);
+  for (int64_t I = I0; I < I1; ++I) {
+    const int b = (int)((I - I0) & 1);
+    if (I + 1 < I1) {
+      load(I + 1, b ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const double* As = sbuf + b * 64 * 65;
+    // row part: thread (row lo, quarter qt of the columns)
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 16; cc += 2) {
+      a0 = fma(As[(qt * 16 + cc) * 65 + lo], vc[qt * 16 + cc], a0);
+      a1 = fma(As[(qt * 16 + cc + 1) * 65 + lo], vc[qt * 16 + cc + 1], a1);
+    }
+    // column part: thread (column lo, quarter qt of the rows); the diagonal tile's
+    // diagonal is counted once (in the row part)
+    double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+    for (int rr = 0; rr < 16; rr += 2) {
+      const int ra = qt * 16 + rr, rb = ra + 1;
+      const double xa = (I != J || ra > lo) ? As[lo * 65 + ra] : 0.0;
+      const double xb = (I != J || rb > lo) ? As[lo * 65 + rb] : 0.0;
+      b0 = fma(xa, vr[b][ra], b0);
+      b1 = fma(xb, vr[b][rb], b1);
+    }
+    colacc += b0 + b1;
+    red[qt][lo] = a0 + a1;
+    __syncthreads();
+    const int64_t r0 = I * 64;
+    if (tid < 64 && r0 + tid < m)
+      prow[J * mp + r0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+    __syncthreads();                               // red and the buffer are reused
+  }
+  red[qt][lo] = colacc;
+  __syncthreads();
+  if (tid < 64 && c0 + tid < m)
+    pcol[k * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+}
+
 // As p_kernel, with the panel's corrections: for rows r > j,
 //   p_r = tau ( (A22 v)_r - V[r, 0:i] y1 - W[r, 0:i] y2 ),
 // then w = p - (tau/2)(p^T v) v by the last CTA.
@@ -501,7 +590,7 @@ __global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, cons
   double dot = 0.0;
   const int64_t nbk = (len + 63) / 64;
   // one thread per row (the grid covers the rows once); the partials of the row are
-  // added in block order, two independent chains each
+  // added in block / segment order, two independent chains each
   for (int64_t r = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t rl = r - (j + 1), blk = rl >> 6;
@@ -512,12 +601,13 @@ __global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, cons
       q1 += prow[(b + 1) * mp + rl];
     }
     if (b <= blk) q0 += prow[b * mp + rl];
-    b = blk;
-    for (; b + 1 < nbk; b += 2) {
+    const int64_t nseg = (nbk - blk + SEG - 1) / SEG;
+    b = 0;
+    for (; b + 1 < nseg; b += 2) {
       c0 += pcol[b * mp + rl];
       c1 += pcol[(b + 1) * mp + rl];
     }
-    if (b < nbk) c0 += pcol[b * mp + rl];
+    if (b < nseg) c0 += pcol[b * mp + rl];
     double q = (q0 + q1) + (c0 + c1);
     double e0 = 0.0, e1 = 0.0;
     for (int c = 0; c < i; ++c) {
@@ -568,9 +658,15 @@ int64_t sytrd_blocked_scratch(int64_t n) {
   return 2 * nbk * n + 2 * (int64_t)num_sms() + 8;
 }
 
+constexpr int STRIP_SMEM = 2 * 64 * 65 * (int)sizeof(double);
+
 void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, double* e,
                          double* tau, double* V, double* W, double* y, double* partial,
                          OzWork* oz, const DevStatus* st) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(attr_set))
+    cudaFuncSetAttribute(symv_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         STRIP_SMEM);
   const int sms = num_sms();
   const int pgrid = 2 * sms;
   const int64_t mp = n;                            // stride of the per-block partials
@@ -593,8 +689,8 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
             n, A, lda, j, V, W, n, i);
       house_col_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, A, lda, j, vj, d, e, tau, st);
       const int64_t nbk = (len + 63) / 64;
-      symv_tile_kernel<<<(unsigned)(nbk * (nbk + 1) / 2), 256, 0, ::ec::counted(s)>>>(
-          n, A, lda, j, vj, prow, pcol, mp);
+      symv_strip_kernel<<<dim3((unsigned)((nbk + SEG - 1) / SEG), (unsigned)nbk), 256,
+                          STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj, prow, pcol, mp);
       if (i > 0)
         latrd_dots_kernel<<<(unsigned)i, 256, 0, ::ec::counted(s)>>>(n, j, V, W, n, vj, y);
       const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;

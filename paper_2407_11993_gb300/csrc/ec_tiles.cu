@@ -184,6 +184,49 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
   // Two accumulators: the unit's closing add is then one DADD per lane (each DADD costs
   // the FP64 pipe a DFMA slot); two chains per lane and two warps per SMSP already
   // cover the DFMA latency at GB300's FP64 issue rate.
+  if constexpr (std::is_same<WT, float2>::value) {
+    // FP32 hi/lo pair factor: each product w v = (w_hi + w_lo)(v_hi + v_lo) as an
+    // exact w_hi v_hi (TwoProd by FMA) plus the two cross terms, accumulated in an
+    // unnormalised float-float sum (TwoSum of the high parts, low parts added); the
+    // unit's sum is formed in FP64 once at its end.  About 2^-46 relative per entry.
+    float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+    for (int64_t it = 0;; ++it) {
+      const int s = (int)(it % ST);
+      const uint32_t ph = (uint32_t)((it / ST) & 1);
+      if (!warp_wait(&sm.full[s], ph, a.st, 42)) break;
+      const Meta m = sm.meta[s];
+      if (m.flags & F_END) break;
+      if (m.flags & F_FIRST) {
+        sh[0] = sh[1] = sl[0] = sl[1] = 0.f;
+      }
+      const float2* Wt = reinterpret_cast<const float2*>(sm.W[s]);
+      const float2* vv = reinterpret_cast<const float2*>(sm.v[s]) + q * 16;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int i0 = q * 16 + k;
+        const float2 w = !TRANS ? Wt[i0 * TB + (o ^ i0)] : Wt[o * TB + (i0 ^ o)];
+        const float2 v = vv[k];                 // broadcast
+        const int c = k & 1;
+        // rounded intrinsics: no contraction of the TwoSum's operations into FMAs
+        const float p = __fmul_rn(w.x, v.x);
+        float e = fmaf(w.x, v.x, -p);
+        e = fmaf(w.x, v.y, e);
+        e = fmaf(w.y, v.x, e);
+        const float t = __fadd_rn(sh[c], p);
+        const float bp = __fsub_rn(t, sh[c]);
+        const float err = __fadd_rn(__fsub_rn(sh[c], __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        sl[c] = __fadd_rn(sl[c], __fadd_rn(err, e));
+        sh[c] = t;
+      }
+      __syncwarp();
+      if (lane == 0) dev::mbar_arrive(&sm.empty[s]);
+      if (m.flags & F_LAST) {
+        m.out[q * m.npad + o] =
+            ((double)sh[0] + (double)sh[1]) + ((double)sl[0] + (double)sl[1]);
+      }
+    }
+    return;
+  } else {
   WT acc[2] = {WT(0), WT(0)};
   for (int64_t it = 0;; ++it) {
     const int s = (int)(it % ST);
@@ -218,6 +261,7 @@ __global__ void __launch_bounds__(CW * 32 + 32, MINB) tile_trmv_kernel(const __g
       m.out[q * m.npad + o] = double(acc[0] + acc[1]);
     }
   }
+  }
 }
 
 __device__ __forceinline__ int64_t tile_row_of(int64_t t) {
@@ -231,6 +275,17 @@ __device__ __forceinline__ int64_t tile_row_of(int64_t t) {
 // WT; the diagonal is multiplied by diag_scale (0.5 stores the half of a symmetric
 // matrix whose product with its transpose-sum gives the full product).
 template <typename WT>
+__device__ __forceinline__ WT to_entry(double v) {
+  return WT(v);
+}
+// FP32 pair: hi = fp32(v), lo = fp32(v - hi) (about 48 significant bits together)
+template <>
+__device__ __forceinline__ float2 to_entry<float2>(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+template <typename WT>
 __global__ void pack_kernel(int64_t n, int64_t ntiles, const double* W, int64_t ldw, WT* Wp,
                             double diag_scale) {
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -241,7 +296,7 @@ __global__ void pack_kernel(int64_t n, int64_t ntiles, const double* W, int64_t 
       const bool in = row < n && col < n && (I != J || r >= c);
       double v = in ? W[row + col * ldw] : 0.0;
       if (row == col) v *= diag_scale;
-      Wp[t * TILE_DBL + e] = WT(v);
+      Wp[t * TILE_DBL + e] = to_entry<WT>(v);
     }
   }
 }
@@ -271,6 +326,7 @@ struct SumDesc {
   int64_t n, nblk, npad;
   int chunk;
   float* out32;        // optional FP32 copy of out (input of an FP32-factor product)
+  float2* outx2;       // optional FP32 pair copy of out (input of a pair-factor product)
 };
 
 template <int NI>
@@ -309,6 +365,18 @@ __global__ void __launch_bounds__(TB * SUM_G) tile_sum_kernel(const __grid_const
     const double v = a.accumulate ? d.out[i] + red[0][tx] : red[0][tx];
     d.out[i] = v;
     if (d.out32) d.out32[i] = (float)v;
+    if (d.outx2) {
+      const float hi = (float)v;
+      d.outx2[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+  }
+}
+
+__global__ void to_x2_kernel(int64_t n, const double* x, float2* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float hi = (float)x[i];
+    y[i] = make_float2(hi, (float)(x[i] - (double)hi));
   }
 }
 
@@ -362,6 +430,7 @@ void tile_prepare_launches() {
   if (dev < 0 || dev >= 64 || g_attr_done[dev]) return;
   set_attributes<1>();
   set_attributes<1, float>();
+  set_attributes<1, float2>();
   set_attributes<TILE_BATCH_MAX>();
   g_attr_done[dev] = true;
 }
@@ -476,9 +545,9 @@ void tile_unpack_lower(cudaStream_t s, const TilePlan& p, const double* Wp, doub
 namespace {
 
 void sum_launch(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out,
-                int accumulate, float* out32 = nullptr) {
+                int accumulate, float* out32 = nullptr, float2* outx2 = nullptr) {
   SumArgs<1> a{};
-  a.d[0] = SumDesc{part, out, p.n, p.nblk, p.npad, p.chunk, out32};
+  a.d[0] = SumDesc{part, out, p.n, p.nblk, p.npad, p.chunk, out32, outx2};
   a.trans = trans;
   a.accumulate = accumulate;
   tile_sum_kernel<1><<<(unsigned)p.nblk, TB * SUM_G, 0, ::ec::counted(s)>>>(a);
@@ -489,7 +558,7 @@ void sum_launch(cudaStream_t s, const TilePlan& p, int trans, const double* part
 template <typename WT>
 void pair_launch(cudaStream_t s, const TilePlan& p, const WT* Wp, const void* b_in,
                  double* part1, double* y, float* y32, double* part2, double* x, int accumulate,
-                 DevStatus* st, cudaEvent_t* ev) {
+                 DevStatus* st, cudaEvent_t* ev, float2* yx2 = nullptr) {
   tile_prepare_launches();
   const Variant<1>& v = variants<1, WT>()[p.variant];
   const int grid = p.grids[p.variant];
@@ -501,8 +570,9 @@ void pair_launch(cudaStream_t s, const TilePlan& p, const WT* Wp, const void* b_
   if (ev) cudaEventRecord(ev[0], s);
   v.fwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[1], s);
-  sum_launch(s, p, 0, part1, y, 0, y32);
-  a.d[0] = TileDesc{Wp, y32 ? (const void*)y32 : (const void*)y, part2, p.nblk, p.npad, p.chunk};
+  sum_launch(s, p, 0, part1, y, 0, y32, yx2);
+  const void* y_in = y32 ? (const void*)y32 : yx2 ? (const void*)yx2 : (const void*)y;
+  a.d[0] = TileDesc{Wp, y_in, part2, p.nblk, p.npad, p.chunk};
   a.units = p.units_bwd;
   v.bwd<<<grid, v.threads, v.smem, ::ec::counted(s)>>>(a);
   if (ev) cudaEventRecord(ev[2], s);
@@ -527,6 +597,20 @@ void tile_trmv_pair_f32(cudaStream_t s, const TilePlan& p, const float* Wp, cons
   const int64_t g = std::min<int64_t>((p.n + 255) / 256, 1024);
   to_f32_kernel<<<(unsigned)(g < 1 ? 1 : g), 256, 0, ::ec::counted(s)>>>(p.n, b, v32);
   pair_launch<float>(s, p, Wp, v32, part1, y, v32, part2, x, accumulate, st, ev);
+}
+
+void tile_pack_lower_x2(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
+                        float2* Wp) {
+  const int64_t g = std::min<int64_t>(p.ntiles, (int64_t)num_sms() * 16);
+  pack_kernel<float2><<<(unsigned)g, 256, 0, ::ec::counted(s)>>>(p.n, p.ntiles, W, ldw, Wp, 1.0);
+}
+
+void tile_trmv_pair_x2(cudaStream_t s, const TilePlan& p, const float2* Wp, const double* b,
+                       float2* vx2, double* part1, double* y, double* part2, double* x,
+                       DevStatus* st, cudaEvent_t* ev) {
+  const int64_t g = std::min<int64_t>((p.n + 255) / 256, 1024);
+  to_x2_kernel<<<(unsigned)(g < 1 ? 1 : g), 256, 0, ::ec::counted(s)>>>(p.n, b, vx2);
+  pair_launch<float2>(s, p, Wp, vx2, part1, y, nullptr, part2, x, 0, st, ev, vx2);
 }
 
 void tile_sym_product(cudaStream_t s, const TilePlan& p, const double* Hp, const double* x,
@@ -620,6 +704,25 @@ ec_status tile_autotune_f32(cudaStream_t s, TilePlan* p, const float* Wp, const 
   return rc;
 }
 
+ec_status tile_autotune_x2(cudaStream_t s, TilePlan* p, const float2* Wp, const double* b,
+                           float2* vx2, double* part1, double* y, double* part2, DevStatus* st,
+                           int forced) {
+  if (forced >= 1 && forced <= TILE_VARIANTS) {
+    p->variant = forced - 1;
+    return EC_OK;
+  }
+  int best = 0;
+  ec_status rc = autotune_shapes(
+      s,
+      [&](int v) {
+        p->variant = v;
+        tile_trmv_pair_x2(s, *p, Wp, b, vx2, part1, y, part2, y, st);
+      },
+      &best, p->tune_ms);
+  p->variant = best;
+  return rc;
+}
+
 // ---- batches of instances ---------------------------------------------------
 
 ec_status tile_batch_create(const TileInst* inst, int count, TileBatch* B) {
@@ -663,7 +766,7 @@ void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, D
   for (int i = 0; i < B.count; ++i) {
     const TilePlan& p = *inst[i].plan;
     a.d[i] = TileDesc{inst[i].Wp, inst[i].b, inst[i].part1, p.nblk, p.npad, p.chunk};
-    sa.d[i] = SumDesc{inst[i].part1, inst[i].y, p.n, p.nblk, p.npad, p.chunk, nullptr};
+    sa.d[i] = SumDesc{inst[i].part1, inst[i].y, p.n, p.nblk, p.npad, p.chunk, nullptr, nullptr};
   }
   a.units = B.units_fwd;
   a.nunits = B.nunits_fwd;
@@ -675,7 +778,7 @@ void tile_batch_pair(cudaStream_t s, const TileBatch& B, const TileInst* inst, D
   for (int i = 0; i < B.count; ++i) {
     const TilePlan& p = *inst[i].plan;
     a.d[i] = TileDesc{inst[i].Wp, inst[i].y, inst[i].part2, p.nblk, p.npad, p.chunk};
-    sa.d[i] = SumDesc{inst[i].part2, inst[i].x, p.n, p.nblk, p.npad, p.chunk, nullptr};
+    sa.d[i] = SumDesc{inst[i].part2, inst[i].x, p.n, p.nblk, p.npad, p.chunk, nullptr, nullptr};
   }
   a.units = B.units_bwd;
   a.nunits = B.nunits_bwd;

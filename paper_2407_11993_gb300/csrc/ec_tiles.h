@@ -80,6 +80,18 @@ ec_status tile_autotune_f32(cudaStream_t s, TilePlan* p, const float* Wp, const 
                             float* v32, double* part1, double* y, double* part2, DevStatus* st,
                             int forced);
 
+// FP32 hi/lo pair factor (EC_PREC_FP32X2): packed tiles of {fp32(w), fp32(w - hi)} (8 bytes
+// per entry, as FP64), products in compensated FP32 arithmetic with FP64 partial rows.
+// vx2: pair copy of the product input (npad entries, zero tail).
+void tile_pack_lower_x2(cudaStream_t s, const TilePlan& p, const double* W, int64_t ldw,
+                        float2* Wp);
+void tile_trmv_pair_x2(cudaStream_t s, const TilePlan& p, const float2* Wp, const double* b,
+                       float2* vx2, double* part1, double* y, double* part2, double* x,
+                       DevStatus* st, cudaEvent_t* ev = nullptr);
+ec_status tile_autotune_x2(cudaStream_t s, TilePlan* p, const float2* Wp, const double* b,
+                           float2* vx2, double* part1, double* y, double* part2, DevStatus* st,
+                           int forced);
+
 // out[i] = sum over the partial rows unit products wrote for row i, in row order
 // (trans = 0: partials of W b; trans = 1: partials of W^T y).
 void tile_sum(cudaStream_t s, const TilePlan& p, int trans, const double* part, double* out);

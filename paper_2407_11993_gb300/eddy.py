@@ -20,7 +20,9 @@ EC_MEM_HOST, EC_MEM_DEVICE = 0, 1
 EC_SOLVE_INVERSE, EC_SOLVE_SUBSTITUTION = 0, 1
 EC_PREC_FP64, EC_PREC_BF16, EC_PREC_BF16X3 = 0, 1, 2
 EC_PREC_FP32 = 3
-_PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3, "fp32": EC_PREC_FP32}
+EC_PREC_FP32X2 = 4
+_PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3, "fp32": EC_PREC_FP32,
+         "fp32x2": EC_PREC_FP32X2}
 
 STATUS = {
     0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_SHAPE", 3: "EC_ERR_NOT_SPD", 4: "EC_ERR_RANK",
@@ -33,7 +35,7 @@ EXPORTS = ("ec_create", "ec_setup", "ec_set_step", "ec_run", "ec_set_current", "
            "ec_last_info", "ec_error_string", "ec_destroy", "ec_selftest_wait_timeout",
            "ec_launch_count", "ec_solve_z", "ec_get_inverse_factor", "ec_solve_inverse_noalloc",
            "ec_grad", "ec_gemm_bf16", "ec_set_mode_count", "ec_phasors", "ec_batch_run",
-           "ec_selftest_fail_alloc", "ec_gemm_f64_emulated")
+           "ec_selftest_fail_alloc", "ec_gemm_f64_emulated", "ec_set_precision")
 NOALLOC_MAX_N = 8192
 
 
@@ -83,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "ec_create": (c_int, [POINTER(c_void_p), POINTER(ec_config)]),
             "ec_setup": (c_int, [P, c_int64, P, P, c_int64, P, c_int64, P, P, c_int64, P, c_int]),
             "ec_set_step": (c_int, [P, c_double, c_double]),
+            "ec_set_precision": (c_int, [P, c_int]),
             "ec_run": (c_int, [P, c_int64, P, P, P, c_int64, P, c_int]),
             "ec_set_current": (c_int, [P, P, c_int]),
             "ec_state_size": (c_int64, [P]),
@@ -266,7 +269,7 @@ class ThetaMethod:
         if solver not in ("inverse", "substitution"):
             raise ValueError("solver must be 'inverse' or 'substitution'")
         if precision not in _PREC:
-            raise ValueError("precision must be 'fp64', 'bf16', 'bf16x3' or 'fp32'")
+            raise ValueError("precision must be 'fp64', 'bf16', 'bf16x3', 'fp32' or 'fp32x2'")
         if integrator not in ("theta", "exact"):
             raise ValueError("integrator must be 'theta' or 'exact'")
         if rhs not in ("sum", "independent", "paired"):
@@ -321,6 +324,14 @@ class ThetaMethod:
 
     def set_step(self, theta: float, dt: float) -> None:
         check(lib().ec_set_step(self._h, float(theta), float(dt)), "ec_set_step", self._h)
+
+    def set_precision(self, precision: str) -> None:
+        """Modal form: switch the arithmetic of the products with U ('fp64', 'bf16',
+        'bf16x3', 'fp32', 'fp32x2') without repeating the eigensolve."""
+        if precision not in _PREC:
+            raise ValueError("precision must be 'fp64', 'bf16', 'bf16x3', 'fp32' or 'fp32x2'")
+        check(lib().ec_set_precision(self._h, _PREC[precision]), "ec_set_precision", self._h)
+        self._desc["precision"] = precision
 
     def run(self, T: int, src=None, iD=None, snap_stride: int = 0, mem: int = EC_MEM_HOST,
             probes_out=None, snaps_out=None):

@@ -178,6 +178,45 @@ def grad_config5_case(args) -> dict:
             "dJ_dsrc_rel_err": rel(gs, ref.dJ_dsrc), "host_cores": __import__("os").cpu_count()}
 
 
+def gemm_case(args) -> dict:
+    """One FP64-accurate tensor-core product C = A B (M x K times K x N, seeded normal
+    entries) through ec_gemm_f64_emulated: wall time of the call (split, products,
+    workspace) over `reps` calls after one warm-up, FP64-equivalent TFLOP/s, and the
+    largest error relative to |A||B| against torch's FP64 product."""
+    import time
+    from ctypes import c_void_p
+
+    import torch
+
+    from paper_2407_11993_gb300 import eddy
+
+    M, N, K = args.gemm
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(K, M, dtype=torch.float64, device="cuda", generator=g)   # column-major M x K
+    B = torch.randn(N, K, dtype=torch.float64, device="cuda", generator=g)   # column-major K x N
+    C = torch.zeros(N, M, dtype=torch.float64, device="cuda")
+
+    def call():
+        rc = eddy.lib().ec_gemm_f64_emulated(0, 0, M, N, K, 1.0, c_void_p(A.data_ptr()), M,
+                                             c_void_p(B.data_ptr()), K, 0.0,
+                                             c_void_p(C.data_ptr()), M, 0, None)
+        if rc != 0:
+            raise RuntimeError(f"ec_gemm_f64_emulated: {rc}")
+
+    call()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(max(1, args.reps)):
+        t0 = time.perf_counter()
+        call()
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    ref = A.t() @ B.t()
+    err = float(((C.t() - ref).abs() / (A.t().abs() @ B.t().abs())).max())
+    return {"M": M, "N": N, "K": K, "best_call_s": best,
+            "fp64_equiv_tflops": 2.0 * M * N * K / best / 1e12, "max_err_rel_absAB": err}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--form", choices=["plain", "modal"], default="plain")
@@ -185,7 +224,7 @@ def main() -> None:
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--T", type=int, default=10)
     ap.add_argument("--no-electrodes", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32x2", "bf16", "bf16x3"])
     ap.add_argument("--refine", type=int, default=0, help="plain fp32: refinement sweeps per step")
     ap.add_argument("--setup-gemm", default="tensor", choices=["tensor", "fp64"],
                     help="arithmetic units of the setup's large dense products")
@@ -205,6 +244,9 @@ def main() -> None:
     ap.add_argument("--dt-sweep", type=int, default=0,
                     help="k runs at k different dt on one setup (modal) vs k re-factorisations "
                          "(plain)")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"),
+                    help="one FP64-accurate tensor-core product of this shape")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--grad-config5", action="store_true",
                     help="the differentiation workload (N=4096, T=5000, checkpoints every 250)")
     args = ap.parse_args()
@@ -224,6 +266,9 @@ def main() -> None:
         return
     if args.grad_config5:
         print(json.dumps(grad_config5_case(args)))
+        return
+    if args.gemm:
+        print(json.dumps(gemm_case(args)))
         return
     if args.config4:
         p = synth.config4(T=args.T, n=args.n)

@@ -53,7 +53,8 @@ def test_binding_rejects_bad_config_without_gpu():
 
 @pytest.mark.parametrize("kwargs,code", [
     (dict(form="plain", precision="bf16"), 10),                    # BF16 variants: modal only
-    (dict(form="modal", precision="fp32"), 10),                    # FP32 factor: plain only
+    (dict(form="plain", precision="bf16x3"), 10),
+    (dict(form="plain", precision="fp32x2", solver="substitution"), 10),
     (dict(form="plain", precision="fp32", solver="substitution"), 10),
     (dict(form="plain", precision="fp32", rhs="independent"), 10),
     (dict(form="plain", integrator="exact"), 10),                  # exact integrator: modal only
@@ -89,6 +90,7 @@ def test_entry_points_check_arguments_without_gpu():
     assert so.ec_solve_inverse_noalloc(0, dummy, 1, dummy, dummy, None) == 1
     # null context
     assert so.ec_run(None, 1, None, None, None, 0, None, 0) == 1
+    assert so.ec_set_precision(None, 0) == 1
     assert so.ec_state_size(None) == 0
 
 

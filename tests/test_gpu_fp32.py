@@ -62,3 +62,32 @@ def test_fp32_unsupported_combinations(eddy):
         tm.setup(p.L, p.R, p.E, p.M, p.MD, p.C)
     with pytest.raises(eddy.EcError):
         eddy.ThetaMethod("modal", p.theta, p.dt, precision="fp32")
+
+
+@pytest.mark.parametrize("n,el", [(65, True), (2100, False), (1029, True)])
+def test_fp32_pair_factor(eddy, n, el):
+    """EC_PREC_FP32X2: the inverse factor as FP32 hi/lo pairs and compensated FP32
+    products (about 2^-46 per product entry).  Stated error: 1e-10 per probe trace and
+    per snapshot against the FP64 oracle (measured values printed); electrodes allowed."""
+    from parity import rel_snaps, rel_traces
+    p = synth.small(n, T=60, seed=n, electrodes=el, coil=True, snap_stride=20)
+    ref = orc.run_problem(p, form="plain")
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt, precision="fp32x2")
+    tm.setup(p.L, p.R, p.E if el else None, p.M, p.MD if el else None, p.C)
+    probes, snaps = tm.run(p.T, p.src, p.iD if el else None, p.snap_stride)
+    tm.close()
+    e_p, e_s = rel_traces(probes, ref.probes), rel_snaps(snaps, ref.snaps)
+    print(f"fp32x2 n={n}: probes {e_p:.3e} snapshots {e_s:.3e}")
+    assert e_p < 1e-10 and e_s < 1e-10
+
+
+def test_fp32_pair_solve_z(eddy):
+    p = synth.small(1500, T=1, seed=22, electrodes=False, coil=True)
+    b = np.random.default_rng(8).standard_normal(1500)
+    Z = p.L + p.dt * p.theta * p.R
+    tm = eddy.ThetaMethod("plain", p.theta, p.dt, precision="fp32x2")
+    tm.setup(p.L, p.R, None, p.M, None, p.C)
+    err = rel(tm.solve_z(b), np.linalg.solve(Z, b))
+    tm.close()
+    print(f"fp32x2 solve_z error {err:.3e}")
+    assert err < 1e-12
