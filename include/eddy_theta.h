@@ -91,7 +91,7 @@ typedef struct ec_config {
   int tile_variant;       /* plain form, EC_SOLVE_INVERSE: 0 (default) = ec_setup times every launch
                              shape of the per-step products on the actual factor and keeps the
                              fastest; 1 .. 3 = use that shape.  No shape changes a result bit. */
-  int setup_gemm;         /* EC_GEMM_TENSOR (default) or EC_GEMM_FP64, see below */
+  int setup_gemm;         /* EC_GEMM_TENSOR (default), EC_GEMM_FP64 or EC_GEMM_TENSOR_PAIRSYMV */
   int release_inputs;     /* nonzero: when ec_setup succeeds, free the device copies of L and R
                              (and, for the plain form with EC_SOLVE_INVERSE, of the Cholesky factor
                              of Z) that stepping does not read -- 2-3 N^2 doubles, 69-103 GB at
@@ -106,8 +106,15 @@ typedef struct ec_config {
  *   EC_GEMM_TENSOR  FP64 operands cut into 8-bit integer slices and multiplied on the
  *                   tensor cores with exact accumulation (see ec_gemm_f64_emulated).
  *   EC_GEMM_FP64    the FP64 CUDA cores (about 1.1 TFLOP/s on GB300).
+ *   EC_GEMM_TENSOR_PAIRSYMV  as EC_GEMM_TENSOR, and the tridiagonalisation's symmetric
+ *                   products (one pass over the trailing matrix per column, bound by
+ *                   the FP64 pipe) in compensated FP32: each FP64 entry split into an
+ *                   FP32 hi/lo pair, float-float sums, about 2^-46 relative per product
+ *                   instead of 2^-53.  Reflectors, updates and everything else as
+ *                   EC_GEMM_TENSOR.  Modal form only (the plain form treats it as
+ *                   EC_GEMM_TENSOR).
  * The two differ by rounding only. */
-enum { EC_GEMM_TENSOR = 0, EC_GEMM_FP64 = 1 };
+enum { EC_GEMM_TENSOR = 0, EC_GEMM_FP64 = 1, EC_GEMM_TENSOR_PAIRSYMV = 2 };
 
 /* How the s coil columns of M drive the system (batched right-hand sides).
  *   EC_RHS_SUM          all coils act on one trajectory (their voltages add).

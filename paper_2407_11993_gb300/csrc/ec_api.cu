@@ -291,7 +291,7 @@ ec_status plain_factor(ec_ctx* c) {
   EventTimer t(c->stream);
   copy_matrix(c->stream, n0, n0, c->dL + m + m * n, n, c->dZ, n0);
   add_lower(c->stream, n0, c->dZ, n0, c->dR + m + m * n, n, c->cfg.theta * c->cfg.dt);
-  OzWork* oz = c->cfg.setup_gemm == EC_GEMM_TENSOR ? &c->oz : nullptr;
+  OzWork* oz = c->cfg.setup_gemm != EC_GEMM_FP64 ? &c->oz : nullptr;
   potrf(c->stream, n0, c->dZ, n0, c->dDinv, c->st, oz);
   if (c->cfg.plain_solver == EC_SOLVE_INVERSE) {
     EC_TRY(alloc(&c->dW, (size_t)n0 * n0));
@@ -427,7 +427,9 @@ ec_status ec_create(ec_ctx** out, const ec_config* cfg) {
     return EC_ERR_UNSUPPORTED;
   if (cfg->integrator == EC_INTEG_EXACT && cfg->form != EC_FORM_MODAL) return EC_ERR_UNSUPPORTED;
   if (cfg->tile_variant < 0 || cfg->tile_variant > TILE_VARIANTS) return EC_ERR_ARG;
-  if (cfg->setup_gemm != EC_GEMM_TENSOR && cfg->setup_gemm != EC_GEMM_FP64) return EC_ERR_ARG;
+  if (cfg->setup_gemm != EC_GEMM_TENSOR && cfg->setup_gemm != EC_GEMM_FP64 &&
+      cfg->setup_gemm != EC_GEMM_TENSOR_PAIRSYMV)
+    return EC_ERR_ARG;
   if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0) || !(cfg->dt > 0.0)) return EC_ERR_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();

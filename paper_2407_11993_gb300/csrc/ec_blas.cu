@@ -455,55 +455,96 @@ void dgemm_halves(cudaStream_t s, int64_t n, int64_t bs, int64_t groups, const d
   }
 }
 
+// Two-level blocking: the 64-wide diagonal steps of each PW-wide panel update only the
+// panel's own columns (rows) with rank-64 products; the trailing part of the matrix is
+// then updated once per panel with a rank-PW product.  PW = 192 is one K chunk of the
+// tensor-core path, whose rank-64 updates would be bound by the read-modify-write of C
+// rather than by the tensor work.
+constexpr int64_t PW = 192;
+static_assert(PW % NB == 0, "panel width must be a multiple of the block size");
+
+// Lower-triangle update of an m x w column panel, rows r0.. of C (the first w rows
+// form the diagonal square): C -= X Y^T with X (m x kb), Y (w x kb).
+void panel_update_lower(cudaStream_t s, OzWork* oz, int64_t m, int64_t w, int kb, const double* X,
+                        int64_t ldx, const double* Y, int64_t ldy, double* C, int64_t ldc,
+                        const DevStatus* st) {
+  if (m <= 0 || w <= 0) return;
+  gemm_auto(s, oz, N_, T_, w, w, kb, -1.0, X, ldx, Y, ldy, 1.0, C, ldc, 1, st);
+  if (m > w)
+    gemm_auto(s, oz, N_, T_, m - w, w, kb, -1.0, X + w, ldx, Y, ldy, 1.0, C + w, ldc, 0, st);
+}
+
 void potrf(cudaStream_t s, int64_t n, double* A, int64_t lda, double* Dinv, DevStatus* st,
            OzWork* oz) {
   static std::atomic<unsigned long long> attr_set{0};
   const int smem = 2 * 64 * 65 * (int)sizeof(double);
   if (first_on_device(attr_set))
     cudaFuncSetAttribute(potf2_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  for (int64_t k = 0; k < n; k += NB) {
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    double* Akk = A + k + k * lda;
-    double* Dk = Dinv + (k / NB) * NB * NB;
-    potf2_diag_kernel<<<1, 256, smem, ::ec::counted(s)>>>(Akk, lda, kb, Dk, st, k);
-    const int64_t rest = n - k - kb;
-    if (rest > 0) {
-      double* P = A + (k + kb) + k * lda;
-      // panel: P <- P Lkk^{-T}  (in place; each CTA owns whole rows of the panel)
-      gemm_auto(s, oz, N_, T_, rest, kb, kb, 1.0, P, lda, Dk, NB, 0.0, P, lda, 0, st);
-      // trailing lower update: A22 <- A22 - P P^T
-      gemm_auto(s, oz, N_, T_, rest, rest, kb, -1.0, P, lda, P, lda, 1.0,
-                A + (k + kb) + (k + kb) * lda, lda, 1, st);
+  for (int64_t k0 = 0; k0 < n; k0 += PW) {
+    const int64_t pe = (k0 + PW) < n ? (k0 + PW) : n;     // panel columns [k0, pe)
+    for (int64_t k = k0; k < pe; k += NB) {
+      const int kb = (int)((n - k) < NB ? (n - k) : NB);
+      double* Akk = A + k + k * lda;
+      double* Dk = Dinv + (k / NB) * NB * NB;
+      potf2_diag_kernel<<<1, 256, smem, ::ec::counted(s)>>>(Akk, lda, kb, Dk, st, k);
+      const int64_t rest = n - k - kb;
+      if (rest > 0) {
+        double* P = A + (k + kb) + k * lda;
+        // panel: P <- P Lkk^{-T}  (in place; each CTA owns whole rows of the panel)
+        gemm_auto(s, oz, N_, T_, rest, kb, kb, 1.0, P, lda, Dk, NB, 0.0, P, lda, 0, st);
+        // the panel's remaining columns [k + kb, pe), lower part
+        panel_update_lower(s, oz, rest, pe - k - kb, kb, P, lda, P, lda,
+                           A + (k + kb) + (k + kb) * lda, lda, st);
+      }
+    }
+    const int64_t rest = n - pe;
+    if (rest > 0) {   // trailing lower update: A22 <- A22 - P P^T, rank pe - k0
+      const double* P = A + pe + k0 * lda;
+      gemm_auto(s, oz, N_, T_, rest, rest, pe - k0, -1.0, P, lda, P, lda, 1.0, A + pe + pe * lda,
+                lda, 1, st);
     }
   }
 }
 
 void trsm_left_lower(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
                      const double* Dinv, double* B, int64_t ldb, const DevStatus* st, OzWork* oz) {
-  for (int64_t k = 0; k < n; k += NB) {
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    const double* Dk = Dinv + (k / NB) * NB * NB;
-    double* Bk = B + k;
-    gemm_auto(s, oz, N_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
-    const int64_t rest = n - k - kb;
+  for (int64_t k0 = 0; k0 < n; k0 += PW) {
+    const int64_t pe = (k0 + PW) < n ? (k0 + PW) : n;
+    for (int64_t k = k0; k < pe; k += NB) {
+      const int kb = (int)((n - k) < NB ? (n - k) : NB);
+      const double* Dk = Dinv + (k / NB) * NB * NB;
+      double* Bk = B + k;
+      gemm_auto(s, oz, N_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+      const int64_t inner = pe - k - kb;
+      if (inner > 0)
+        gemm_auto(s, oz, N_, N_, inner, nrhs, kb, -1.0, Lf + (k + kb) + k * ldl, ldl, Bk, ldb,
+                  1.0, B + k + kb, ldb, 0, st);
+    }
+    const int64_t rest = n - pe;
     if (rest > 0)
-      gemm_auto(s, oz, N_, N_, rest, nrhs, kb, -1.0, Lf + (k + kb) + k * ldl, ldl, Bk, ldb, 1.0,
-                B + k + kb, ldb, 0, st);
+      gemm_auto(s, oz, N_, N_, rest, nrhs, pe - k0, -1.0, Lf + pe + k0 * ldl, ldl, B + k0, ldb,
+                1.0, B + pe, ldb, 0, st);
   }
 }
 
 void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf, int64_t ldl,
                        const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
                        OzWork* oz) {
-  const int64_t nblk = (n + NB - 1) / NB;
-  for (int64_t b = nblk - 1; b >= 0; --b) {
-    const int64_t k = b * NB;
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    const double* Dk = Dinv + b * NB * NB;
-    double* Bk = B + k;
-    gemm_auto(s, oz, T_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
-    if (k > 0)  // B[0:k] -= L[k:k+kb, 0:k]^T B_k
-      gemm_auto(s, oz, T_, N_, k, nrhs, kb, -1.0, Lf + k, ldl, Bk, ldb, 1.0, B, ldb, 0, st);
+  if (n <= 0) return;
+  for (int64_t k0 = (n - 1) / PW * PW; k0 >= 0; k0 -= PW) {
+    const int64_t pe = (k0 + PW) < n ? (k0 + PW) : n;     // panel rows [k0, pe)
+    for (int64_t k = (pe - 1) / NB * NB; k >= k0; k -= NB) {
+      const int kb = (int)((n - k) < NB ? (n - k) : NB);
+      const double* Dk = Dinv + (k / NB) * NB * NB;
+      double* Bk = B + k;
+      gemm_auto(s, oz, T_, N_, kb, nrhs, kb, 1.0, Dk, NB, Bk, ldb, 0.0, Bk, ldb, 0, st);
+      if (k > k0)  // B[k0:k] -= L[k:k+kb, k0:k]^T B_k
+        gemm_auto(s, oz, T_, N_, k - k0, nrhs, kb, -1.0, Lf + k + k0 * ldl, ldl, Bk, ldb, 1.0,
+                  B + k0, ldb, 0, st);
+    }
+    if (k0 > 0)  // B[0:k0] -= L[k0:pe, 0:k0]^T B[k0:pe]
+      gemm_auto(s, oz, T_, N_, k0, nrhs, pe - k0, -1.0, Lf + k0, ldl, B + k0, ldb, 1.0, B, ldb, 0,
+                st);
   }
 }
 
@@ -514,15 +555,22 @@ void trsm_left_lower_t(cudaStream_t s, int64_t n, int64_t nrhs, const double* Lf
 void trsm_right_lower_t_sym(cudaStream_t s, int64_t n, const double* Lf, int64_t ldl,
                             const double* Dinv, double* B, int64_t ldb, const DevStatus* st,
                             OzWork* oz) {
-  for (int64_t k = 0; k < n; k += NB) {
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    const double* Dk = Dinv + (k / NB) * NB * NB;
-    double* Bk = B + k * ldb;
-    gemm_auto(s, oz, N_, T_, n - k, kb, kb, 1.0, Bk + k, ldb, Dk, NB, 0.0, Bk + k, ldb, 0, st);
-    const int64_t rest = n - k - kb;
-    if (rest > 0)  // lower(B[k+kb:, k+kb:]) -= B[k+kb:, k:k+kb] L[k+kb:, k:k+kb]^T
-      gemm_auto(s, oz, N_, T_, rest, rest, kb, -1.0, Bk + k + kb, ldb, Lf + (k + kb) + k * ldl,
-                ldl, 1.0, B + (k + kb) + (k + kb) * ldb, ldb, 1, st);
+  for (int64_t k0 = 0; k0 < n; k0 += PW) {
+    const int64_t pe = (k0 + PW) < n ? (k0 + PW) : n;
+    for (int64_t k = k0; k < pe; k += NB) {
+      const int kb = (int)((n - k) < NB ? (n - k) : NB);
+      const double* Dk = Dinv + (k / NB) * NB * NB;
+      double* Bk = B + k * ldb;
+      gemm_auto(s, oz, N_, T_, n - k, kb, kb, 1.0, Bk + k, ldb, Dk, NB, 0.0, Bk + k, ldb, 0, st);
+      // the panel's remaining columns [k + kb, pe), rows below their diagonal:
+      // B[k+kb:, k+kb:pe] -= B[k+kb:, k:k+kb] L[k+kb:pe, k:k+kb]^T
+      panel_update_lower(s, oz, n - k - kb, pe - k - kb, kb, Bk + k + kb, ldb,
+                         Lf + (k + kb) + k * ldl, ldl, B + (k + kb) + (k + kb) * ldb, ldb, st);
+    }
+    const int64_t rest = n - pe;
+    if (rest > 0)  // lower(B[pe:, pe:]) -= B[pe:, k0:pe] L[pe:, k0:pe]^T
+      gemm_auto(s, oz, N_, T_, rest, rest, pe - k0, -1.0, B + pe + k0 * ldb, ldb,
+                Lf + pe + k0 * ldl, ldl, 1.0, B + pe + pe * ldb, ldb, 1, st);
   }
 }
 

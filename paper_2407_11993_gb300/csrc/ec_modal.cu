@@ -87,7 +87,7 @@ namespace {
 constexpr int MT = 256;            // modes per CTA
 constexpr int TS = 16;             // steps per shared-memory block of the probe contraction
 constexpr int64_t SUPER = 32768;   // steps per launch group (bounds the partial-sum buffer)
-constexpr int64_t CH_MIN = 1024;   // shortest time chunk; runs up to this length are one chunk
+constexpr int64_t CH_MIN = 256;    // shortest time chunk
 constexpr int64_t ORM_GROUP = 1024;  // reflectors per compact-WY group of the tensor-core back-transform
 // from this size on, FP64 snapshot reconstructions use U's kept slices (below it the
 // FP64 cores finish U x in about the time of the tensor path's launches)
@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
     q0 = a.ac[a.n0 + nmode];
     q1 = a.ac[2 * a.n0 + nmode];
     for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)bcol(a, c, r) * a.n0];
+    if (!two)
+      for (int c = 0; c < nc; ++c) b[c] *= q0;   // theta step: x <- a x + sum_c (q0 b_c) w_c
   }
   double x = 0.0, ap = 1.0;
   for (int64_t t0 = c0; t0 < c1; t0 += TS) {
@@ -285,17 +287,30 @@ __global__ void __launch_bounds__(MT) modal_chunk_end_kernel(ScanArgs a) {
       if (two) coef[TS * ncs + (idx / nc) * ncs + idx % nc] = coef_for(a, idx % nc, r, t0 + idx / nc, 1);
     }
     __syncthreads();
-    if (live)
-      for (int tt = 0; tt < nt; ++tt) {
-        double e0 = 0.0, e1 = 0.0;
-        for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
-        if (two)
+    if (live) {
+      if (two) {
+        for (int tt = 0; tt < nt; ++tt) {
+          double e0 = 0.0, e1 = 0.0;
+          for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
           for (int c = 0; c < nc; ++c) e1 = fma(b[c], coef[TS * ncs + tt * ncs + c], e1);
-        x = fma(an, x, fma(q0, e0, q1 * e1));
-        ap *= an;
+          x = fma(an, x, fma(q0, e0, q1 * e1));
+        }
+      } else {
+        for (int tt = 0; tt < nt; ++tt) {
+          double e0 = 0.0;
+          for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
+          x = fma(an, x, e0);
+        }
       }
+    }
   }
   if (live) {
+    // a^len by repeated squaring
+    double base = an;
+    for (int64_t e = c1 - c0; e > 0; e >>= 1) {
+      if (e & 1) ap *= base;
+      base *= base;
+    }
     a.xend[((int64_t)g * a.ntraj + r) * a.n0 + nmode] = x;
     a.apow[((int64_t)g * a.ntraj + r) * a.n0 + nmode] = ap;
   }
@@ -340,6 +355,8 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
     x = (g == 0) ? a.x[(int64_t)r * a.n0 + nmode]
                  : a.xstart[((int64_t)g * a.ntraj + r) * a.n0 + nmode];
     for (int c = 0; c < nc; ++c) b[c] = a.B[nmode + (int64_t)bcol(a, c, r) * a.n0];
+    if (!two)
+      for (int c = 0; c < nc; ++c) b[c] *= q0;   // as in modal_chunk_end_kernel
   }
   for (int p = 0; p < P; ++p)
     Gs[p * MT + tid] = live ? a.Gt[nmode + (int64_t)(a.paired ? r : p) * a.n0] : 0.0;
@@ -352,11 +369,15 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
     }
     __syncthreads();
     for (int tt = 0; tt < nt; ++tt) {
-      double e0 = 0.0, e1 = 0.0;
+      double e0 = 0.0;
       for (int c = 0; c < nc; ++c) e0 = fma(b[c], coef[tt * ncs + c], e0);
-      if (two)
+      if (two) {
+        double e1 = 0.0;
         for (int c = 0; c < nc; ++c) e1 = fma(b[c], coef[TS * ncs + tt * ncs + c], e1);
-      x = fma(an, x, fma(q0, e0, q1 * e1));
+        x = fma(an, x, fma(q0, e0, q1 * e1));
+      } else {
+        x = fma(an, x, e0);
+      }
       X[tid * (TS + 1) + tt] = live ? x : 0.0;
       const int64_t k1 = t0 + tt + 1;   // state index after this step
       if (live && a.stride > 0 && a.Xsnap && k1 % a.stride == 0)
@@ -425,7 +446,7 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
   if (ms->precision == EC_PREC_FP32 || ms->precision == EC_PREC_FP32X2)
     return skinny32_product(s, ms->u32, n0, trans_u, N, K, Y, lds, C, ldc, &ms->sk, st);
   if (ms->precision == EC_PREC_FP64) {
-    if (ms->gemm == EC_GEMM_TENSOR && !trans_u && n0 >= PRESPLIT_MIN) {
+    if (ms->gemm != EC_GEMM_FP64 && !trans_u && n0 >= PRESPLIT_MIN) {
       if (!ms->usplit.slices && !ms->usplit_tried) {
         ms->usplit_tried = true;
         if (oz_presplit(s, N_, n0, n0, ms->U, n0, &ms->usplit) != EC_OK)
@@ -437,7 +458,7 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
         if (rc != EC_ERR_OOM) return rc;
       }
     }
-    gemm_auto(s, ms->gemm == EC_GEMM_TENSOR ? &ms->oz : nullptr, trans_u ? T_ : N_, N_, n0, N, K,
+    gemm_auto(s, ms->gemm != EC_GEMM_FP64 ? &ms->oz : nullptr, trans_u ? T_ : N_, N_, n0, N, K,
               1.0, ms->U, n0, Y, lds, 0.0, C, ldc, 0, st);
     return EC_OK;
   }
@@ -557,7 +578,7 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
   ms->CR = a.Ri;
   ms->ldCR = ld;
   ms->gemm = a.gemm;
-  OzWork* oz = a.gemm == EC_GEMM_TENSOR ? &ms->oz : nullptr;
+  OzWork* oz = a.gemm != EC_GEMM_FP64 ? &ms->oz : nullptr;
 
   Timer t(s);
   // a4: R_i = C_R C_R^T
@@ -603,7 +624,8 @@ ec_status modal_setup(cudaStream_t s, ModalState* ms, const ModalSetupArgs& a, e
       cleanup();
       return EC_ERR_OOM;
     }
-    sytrd_lower_blocked(s, n0, a.Li, ld, d, e, th, Vp, Wp, yp, pp, oz, a.st);
+    sytrd_lower_blocked(s, n0, a.Li, ld, d, e, th, Vp, Wp, yp, pp, oz, a.st,
+                        a.gemm == EC_GEMM_TENSOR_PAIRSYMV ? 1 : 0);
     cudaStreamSynchronize(s);
     for (double* p : {Vp, Wp, yp, pp}) cudaFree(p);
   } else {
@@ -694,10 +716,23 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   const int64_t kmax = T < SUPER ? T : SUPER;
   MS_TRY(grow_n(&ms->partial, ms->partialCap,
                 (size_t)nblk * kmax * (Pout > 0 ? Pout : 1) * nt));
-  // chunks: enough (mode tile, chunk, trajectory) CTAs for ~4 per SM, never shorter than CH_MIN
-  const int64_t gtarget = ((int64_t)4 * num_sms() + (int64_t)nblk * nt - 1) / ((int64_t)nblk * nt);
-  const int64_t maxchunks = (kmax + CH_MIN - 1) / CH_MIN;
-  const int64_t gcap = gtarget < maxchunks ? gtarget : maxchunks;
+  // time chunks: the scan is bound by the FP64 pipe, so the chunk count minimises the
+  // busiest SM's work, ceil(CTAs / SMs) x steps per chunk, with the chunk-end pass
+  // (about half a replay) added when there is more than one chunk
+  int64_t gcap = 1;
+  {
+    const int64_t sms = num_sms(), per = (int64_t)nblk * nt;
+    const int64_t gmax = std::max<int64_t>(1, std::min<int64_t>(256, kmax / CH_MIN));
+    double best = 1e300;
+    for (int64_t g = 1; g <= gmax; ++g) {
+      const double rounds = (double)((per * g + sms - 1) / sms);
+      const double cost = rounds * ((double)kmax / (double)g) * (g > 1 ? 1.5 : 1.0);
+      if (cost < 0.97 * best) {       // fewer chunks on near ties
+        best = cost;
+        gcap = g;
+      }
+    }
+  }
   MS_TRY(grow_n(&ms->chunkbuf, ms->chunkCap, (size_t)3 * (gcap > 0 ? gcap : 1) * n0 * nt));
   ScanArgs a{};
   a.n0 = n0; a.T = T; a.m = ms->m; a.S = ms->S; a.P = ms->P;

@@ -97,16 +97,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
          (1ull << 46) | (4ull << 61);
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = TN, M = TM.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = TM, N = nmma
+// (TN, or 16 / 32 for products whose B block has that few columns).
+__host__ __device__ constexpr uint32_t idesc_for(int nmma) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+         ((uint32_t)(TM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -138,6 +142,7 @@ struct OzArgs {
   int64_t ldc;
   const int* ea;           // row exponents of op(A)
   const int* eb;           // column exponents of op(B)
+  int nmma;                // MMA width and B rows per stage: TN, or 16 / 32 when N is that small
 };
 
 // Tile of a launch: row groups of GROUP_M tile rows, columns innermost within a group
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
           }
           uint8_t* sa = smem + s * STAGE_BYTES;
           uint8_t* sb = sa + A_BYTES;
-          mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+          mbar_expect_tx(&full_bar[s], A_BYTES + OZ_S * a.nmma * TK * 2);
           tma_load_3d(sa, &mapA, &full_bar[s], a.k0 + kb * TK, m0, 0);
           tma_load_3d(sb, &mapB, &full_bar[s], a.k0 + kb * TK, n0, 0);
           *(volatile int*)&issued = (int)(it + 1);
@@ -270,6 +275,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
     if (lane == 0) {
       // MMA issuer: one MMA per slice pair and 16-wide K step
       uint32_t it = 0, tc = 0;
+      const uint32_t idesc = idesc_for(a.nmma);
+      const uint32_t b_slice = (uint32_t)(a.nmma * TK * 2);   // B slices lie densely packed
       int t = blockIdx.x, m0 = 0, n0 = 0;
       bool ok = true;
       for (; ok && next_tile(a, t, m0, n0) && !*(volatile int*)&abort_flag; t += gridDim.x, ++tc) {
@@ -299,12 +306,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
               const int ti = d - si;
               if (si >= OZ_S || ti >= OZ_S) continue;
               const uint64_t da = smem_desc(sa + si * A_SLICE);
-              const uint64_t db = smem_desc(sb + ti * B_SLICE);
+              const uint64_t db = smem_desc(sb + ti * b_slice);
 #pragma unroll
               for (int kk = 0; kk < TK / 16; ++kk) {
                 // the first product into each accumulator overwrites it
                 const bool first = kb == 0 && kk == 0 && si == 0 && d <= OZ_EXACT;
-                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, first ? 0u : 1u);
               }
             }
           }
@@ -338,6 +345,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       // multiply-adds, then the shared group of the small diagonals rounded at 2^-40
 #pragma unroll 1
       for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
+        if (n0 + c0 >= a.N) break;                   // columns past C (and past nmma)
         uint32_t r[NACC][16];
 #pragma unroll
         for (int q = 0; q < NACC; ++q) tmem_ld16(lane_base + (uint32_t)(q * TN + c0), r[q]);
@@ -369,6 +377,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
       const int erow = row_ok ? a.ea[row] - 56 : 0;
 #pragma unroll 1
       for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 16) {
+        if (n0 + c0 >= a.N) break;
         uint32_t xs[32];
         tmem_ld32(lane_base + (uint32_t)(STAGE_COL + 2 * c0), xs);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -606,6 +615,9 @@ void oz_free(OzWork* w) {
 
 namespace {
 
+// MMA width (and B rows per stage) for a B block of nj columns.
+int nmma_for(int64_t nj) { return nj <= 16 ? 16 : (nj <= 32 ? 32 : TN); }
+
 // One mi x nj panel of C = alpha A B + beta C from the slices behind maps ma, mb: K in
 // chunks of OZ_KCHUNK, the first with beta, the rest accumulating.
 ec_status launch_panel(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int64_t mi,
@@ -622,6 +634,7 @@ ec_status launch_panel(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap&
   args.ea = eA;
   args.eb = eB;
   args.tri = tri;
+  args.nmma = nmma_for(nj);
   const int64_t tiles = (int64_t)args.tiles_m * args.tiles_n;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms());
   for (int64_t k0 = 0; k0 < K; k0 += OZ_KCHUNK) {
@@ -700,7 +713,7 @@ ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb
     const int64_t nj = std::min(pn, N - j0);
     split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
     CUtensorMap mb;
-    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, TN)) return EC_ERR_CUDA;
+    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, nmma_for(nj))) return EC_ERR_CUDA;
     const ec_status rc = launch_panel(s, ma, mb, a.R, nj, kuse, 1.0, beta, C + j0 * ldc, ldc,
                                       a.exps, w->exps, 0, st);
     if (rc != EC_OK) return rc;
@@ -758,7 +771,8 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
       if (tri && j0 > i0 + mi - 1) break;            // panel entirely above the diagonal
       split(s, nj, K, B + j0 * brs, brs, bks, w->maxb + pm, sB, ldk, eB);
       CUtensorMap ma, mb;
-      if (!make_slice_map(&ma, sA, mi, K, ldk, TM) || !make_slice_map(&mb, sB, nj, K, ldk, TN))
+      if (!make_slice_map(&ma, sA, mi, K, ldk, TM) ||
+          !make_slice_map(&mb, sB, nj, K, ldk, nmma_for(nj)))
         return EC_ERR_CUDA;
       // a tri panel on the diagonal (i0 == j0) keeps rows >= columns; a panel below it
       // is full

@@ -16,6 +16,7 @@
 
 #include <cmath>
 
+#include "ec_ff.h"
 #include "ec_internal.h"
 #include "ec_sytrd.h"
 
@@ -498,12 +499,19 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
                : "memory");
 }
 
+// PAIR: the same products in compensated FP32 (each FP64 entry split into hi + lo
+// FP32 parts by integer operations once per tile, float-float sums, partials stored as
+// FP32 pairs in the same 8-byte slots): on GB300 this moves the product from the FP64
+// pipe (2 FMAs per SM per clock) to the FP32 and integer pipes, leaving the tile reads
+// from HBM as its bound; about 2^-46 relative per product.
+template <bool PAIR>
 __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double* A, int64_t lda,
                                                          int64_t j, const double* v, double* prow,
                                                          double* pcol, int64_t mp) {
   extern __shared__ double sbuf[];                  // two tiles, As[b][c][r] stride 65
   __shared__ double vr[2][64], vc[64];
   __shared__ double red[4][64];
+  __shared__ float2 vrp[2][64], vcp[64];
   const int64_t s0 = j + 1, m = n - s0;
   const int64_t nbk = (m + 63) / 64;
   const int64_t J = blockIdx.y, k = blockIdx.x;
@@ -512,7 +520,10 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
   const int64_t I1 = (I0 + SEG < nbk) ? I0 + SEG : nbk;
   const int tid = threadIdx.x, lo = tid & 63, qt = tid >> 6;
   const int64_t c0 = J * 64;
-  if (tid < 64) vc[tid] = (c0 + tid < m) ? v[s0 + c0 + tid] : 0.0;
+  if (tid < 64) {
+    vc[tid] = (c0 + tid < m) ? v[s0 + c0 + tid] : 0.0;
+    if (PAIR) vcp[tid] = ff::split(vc[tid]);
+  }
   auto load = [&](int64_t I, int b) {
     double* As = sbuf + b * 64 * 65;
     const int64_t r0 = I * 64;
@@ -523,10 +534,15 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
       cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + r) + (s0 + c) * lda)
                                       : (const void*)A, ok);
     }
-    if (tid < 64) vr[b][tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
+    if (tid < 64) {
+      vr[b][tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
+      if (PAIR) vrp[b][tid] = ff::split(vr[b][tid]);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   double colacc = 0.0;     // column part of (lo, qt) over the segment
+  float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;   // the same, PAIR
+  float2* red2 = reinterpret_cast<float2*>(&red[0][0]);
   load(I0, 0);
   for (int64_t I = I0; I < I1; ++I) {
     const int b = (int)((I - I0) & 1);
@@ -538,41 +554,94 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
     }
     __syncthreads();
     const double* As = sbuf + b * 64 * 65;
-    // row part: thread (row lo, quarter qt of the columns)
-    double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-    for (int cc = 0; cc < 16; cc += 2) {
-      a0 = fma(As[(qt * 16 + cc) * 65 + lo], vc[qt * 16 + cc], a0);
-      a1 = fma(As[(qt * 16 + cc + 1) * 65 + lo], vc[qt * 16 + cc + 1], a1);
-    }
-    // column part: thread (column lo, quarter qt of the rows); the diagonal tile's
-    // diagonal is counted once (in the row part)
-    double b0 = 0.0, b1 = 0.0;
-#pragma unroll
-    for (int rr = 0; rr < 16; rr += 2) {
-      const int ra = qt * 16 + rr, rb = ra + 1;
-      const double xa = (I != J || ra > lo) ? As[lo * 65 + ra] : 0.0;
-      const double xb = (I != J || rb > lo) ? As[lo * 65 + rb] : 0.0;
-      b0 = fma(xa, vr[b][ra], b0);
-      b1 = fma(xb, vr[b][rb], b1);
-    }
-    colacc += b0 + b1;
-    red[qt][lo] = a0 + a1;
-    __syncthreads();
     const int64_t r0 = I * 64;
-    if (tid < 64 && r0 + tid < m)
-      prow[J * mp + r0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-    __syncthreads();                               // red and the buffer are reused
+    if constexpr (PAIR) {
+      // split the tile in place (each 8-byte slot becomes its FP32 pair)
+      double* Aw = sbuf + b * 64 * 65;
+      float2* A2w = reinterpret_cast<float2*>(Aw);
+      for (int q = tid; q < 64 * 64; q += 256) {
+        const int idx = (q >> 6) * 65 + (q & 63);
+        A2w[idx] = ff::split(Aw[idx]);
+      }
+      __syncthreads();
+      const float2* A2 = reinterpret_cast<const float2*>(As);
+      float rh0 = 0.f, rl0 = 0.f, rh1 = 0.f, rl1 = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < 16; cc += 2) {
+        const float2 x0 = A2[(qt * 16 + cc) * 65 + lo], y0 = vcp[qt * 16 + cc];
+        const float2 x1 = A2[(qt * 16 + cc + 1) * 65 + lo], y1 = vcp[qt * 16 + cc + 1];
+        ff::madd(rh0, rl0, x0.x, x0.y, y0.x, y0.y);
+        ff::madd(rh1, rl1, x1.x, x1.y, y1.x, y1.y);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 16; rr += 2) {
+        const int ra = qt * 16 + rr, rb = ra + 1;
+        const float2 xa = (I != J || ra > lo) ? A2[lo * 65 + ra] : make_float2(0.f, 0.f);
+        const float2 xb = (I != J || rb > lo) ? A2[lo * 65 + rb] : make_float2(0.f, 0.f);
+        ff::madd(ch0, cl0, xa.x, xa.y, vrp[b][ra].x, vrp[b][ra].y);
+        ff::madd(ch1, cl1, xb.x, xb.y, vrp[b][rb].x, vrp[b][rb].y);
+      }
+      ff::add(rh0, rl0, rh1, rl1);
+      red2[qt * 64 + lo] = make_float2(rh0, rl0);
+      __syncthreads();
+      if (tid < 64 && r0 + tid < m) {
+        float h = red2[tid].x, l = red2[tid].y;
+        ff::add(h, l, red2[64 + tid].x, red2[64 + tid].y);
+        ff::add(h, l, red2[128 + tid].x, red2[128 + tid].y);
+        ff::add(h, l, red2[192 + tid].x, red2[192 + tid].y);
+        reinterpret_cast<float2*>(prow)[J * mp + r0 + tid] = make_float2(h, l);
+      }
+      __syncthreads();                             // red and the buffer are reused
+    } else {
+      // row part: thread (row lo, quarter qt of the columns)
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int cc = 0; cc < 16; cc += 2) {
+        a0 = fma(As[(qt * 16 + cc) * 65 + lo], vc[qt * 16 + cc], a0);
+        a1 = fma(As[(qt * 16 + cc + 1) * 65 + lo], vc[qt * 16 + cc + 1], a1);
+      }
+      // column part: thread (column lo, quarter qt of the rows); the diagonal tile's
+      // diagonal is counted once (in the row part)
+      double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+      for (int rr = 0; rr < 16; rr += 2) {
+        const int ra = qt * 16 + rr, rb = ra + 1;
+        const double xa = (I != J || ra > lo) ? As[lo * 65 + ra] : 0.0;
+        const double xb = (I != J || rb > lo) ? As[lo * 65 + rb] : 0.0;
+        b0 = fma(xa, vr[b][ra], b0);
+        b1 = fma(xb, vr[b][rb], b1);
+      }
+      colacc += b0 + b1;
+      red[qt][lo] = a0 + a1;
+      __syncthreads();
+      if (tid < 64 && r0 + tid < m)
+        prow[J * mp + r0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+      __syncthreads();                             // red and the buffer are reused
+    }
   }
-  red[qt][lo] = colacc;
-  __syncthreads();
-  if (tid < 64 && c0 + tid < m)
-    pcol[k * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+  if constexpr (PAIR) {
+    ff::add(ch0, cl0, ch1, cl1);
+    red2[qt * 64 + lo] = make_float2(ch0, cl0);
+    __syncthreads();
+    if (tid < 64 && c0 + tid < m) {
+      float h = red2[tid].x, l = red2[tid].y;
+      ff::add(h, l, red2[64 + tid].x, red2[64 + tid].y);
+      ff::add(h, l, red2[128 + tid].x, red2[128 + tid].y);
+      ff::add(h, l, red2[192 + tid].x, red2[192 + tid].y);
+      reinterpret_cast<float2*>(pcol)[k * mp + c0 + tid] = make_float2(h, l);
+    }
+  } else {
+    red[qt][lo] = colacc;
+    __syncthreads();
+    if (tid < 64 && c0 + tid < m)
+      pcol[k * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+  }
 }
 
 // As p_kernel, with the panel's corrections: for rows r > j,
 //   p_r = tau ( (A22 v)_r - V[r, 0:i] y1 - W[r, 0:i] y2 ),
 // then w = p - (tau/2)(p^T v) v by the last CTA.
+template <bool PAIR>
 __global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, const double* v,
                                                       const double* tau, const double* prow,
                                                       const double* pcol, int64_t mp,
@@ -594,21 +663,43 @@ __global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, cons
   for (int64_t r = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t rl = r - (j + 1), blk = rl >> 6;
-    double q0 = 0.0, q1 = 0.0, c0 = 0.0, c1 = 0.0;
-    int64_t b = 0;
-    for (; b + 1 <= blk; b += 2) {
-      q0 += prow[b * mp + rl];
-      q1 += prow[(b + 1) * mp + rl];
-    }
-    if (b <= blk) q0 += prow[b * mp + rl];
     const int64_t nseg = (nbk - blk + SEG - 1) / SEG;
-    b = 0;
-    for (; b + 1 < nseg; b += 2) {
-      c0 += pcol[b * mp + rl];
-      c1 += pcol[(b + 1) * mp + rl];
+    double q;
+    if constexpr (PAIR) {
+      const float2* pr2 = reinterpret_cast<const float2*>(prow);
+      const float2* pc2 = reinterpret_cast<const float2*>(pcol);
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      int64_t b = 0;
+      for (; b + 1 <= blk; b += 2) {
+        const float2 x0 = pr2[b * mp + rl], x1 = pr2[(b + 1) * mp + rl];
+        ff::add(h0, l0, x0.x, x0.y);
+        ff::add(h1, l1, x1.x, x1.y);
+      }
+      if (b <= blk) ff::add(h0, l0, pr2[b * mp + rl].x, pr2[b * mp + rl].y);
+      b = 0;
+      for (; b + 1 < nseg; b += 2) {
+        const float2 x0 = pc2[b * mp + rl], x1 = pc2[(b + 1) * mp + rl];
+        ff::add(h0, l0, x0.x, x0.y);
+        ff::add(h1, l1, x1.x, x1.y);
+      }
+      if (b < nseg) ff::add(h0, l0, pc2[b * mp + rl].x, pc2[b * mp + rl].y);
+      q = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+    } else {
+      double q0 = 0.0, q1 = 0.0, c0 = 0.0, c1 = 0.0;
+      int64_t b = 0;
+      for (; b + 1 <= blk; b += 2) {
+        q0 += prow[b * mp + rl];
+        q1 += prow[(b + 1) * mp + rl];
+      }
+      if (b <= blk) q0 += prow[b * mp + rl];
+      b = 0;
+      for (; b + 1 < nseg; b += 2) {
+        c0 += pcol[b * mp + rl];
+        c1 += pcol[(b + 1) * mp + rl];
+      }
+      if (b < nseg) c0 += pcol[b * mp + rl];
+      q = (q0 + q1) + (c0 + c1);
     }
-    if (b < nseg) c0 += pcol[b * mp + rl];
-    double q = (q0 + q1) + (c0 + c1);
     double e0 = 0.0, e1 = 0.0;
     for (int c = 0; c < i; ++c) {
       e0 = fma(V[r + c * ldv], ys[c], e0);
@@ -662,11 +753,14 @@ constexpr int STRIP_SMEM = 2 * 64 * 65 * (int)sizeof(double);
 
 void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, double* e,
                          double* tau, double* V, double* W, double* y, double* partial,
-                         OzWork* oz, const DevStatus* st) {
+                         OzWork* oz, const DevStatus* st, int pair_symv) {
   static std::atomic<unsigned long long> attr_set{0};
-  if (first_on_device(attr_set))
-    cudaFuncSetAttribute(symv_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (first_on_device(attr_set)) {
+    cudaFuncSetAttribute(symv_strip_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          STRIP_SMEM);
+    cudaFuncSetAttribute(symv_strip_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         STRIP_SMEM);
+  }
   const int sms = num_sms();
   const int pgrid = 2 * sms;
   const int64_t mp = n;                            // stride of the per-block partials
@@ -689,13 +783,22 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
             n, A, lda, j, V, W, n, i);
       house_col_kernel<<<1, HT, 0, ::ec::counted(s)>>>(n, A, lda, j, vj, d, e, tau, st);
       const int64_t nbk = (len + 63) / 64;
-      symv_strip_kernel<<<dim3((unsigned)((nbk + SEG - 1) / SEG), (unsigned)nbk), 256,
-                          STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj, prow, pcol, mp);
+      const dim3 sg((unsigned)((nbk + SEG - 1) / SEG), (unsigned)nbk);
+      if (pair_symv)
+        symv_strip_kernel<true><<<sg, 256, STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj, prow,
+                                                                          pcol, mp);
+      else
+        symv_strip_kernel<false><<<sg, 256, STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj,
+                                                                           prow, pcol, mp);
       if (i > 0)
         latrd_dots_kernel<<<(unsigned)i, 256, 0, ::ec::counted(s)>>>(n, j, V, W, n, vj, y);
       const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;
-      p_latrd_kernel<<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(
-          n, j, vj, tau, prow, pcol, mp, V, W, n, i, y, wj, dots, counter);
+      if (pair_symv)
+        p_latrd_kernel<true><<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(
+            n, j, vj, tau, prow, pcol, mp, V, W, n, i, y, wj, dots, counter);
+      else
+        p_latrd_kernel<false><<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(
+            n, j, vj, tau, prow, pcol, mp, V, W, n, i, y, wj, dots, counter);
     }
     // the panel's rank-2nb update of the trailing lower triangle
     const int64_t t0 = b + nb, m = n - t0;

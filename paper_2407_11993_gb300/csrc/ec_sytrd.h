@@ -21,11 +21,13 @@ void sytrd_lower(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, d
 // product reads each element of the trailing triangle once (64 x 64 tiles, both
 // contributions per element, partials summed in a fixed order).  Identical reflectors
 // in exact arithmetic.  Scratch: V, W (n x 64), y (128), partial
-// (sytrd_blocked_scratch(n) doubles).
+// (sytrd_blocked_scratch(n) doubles).  pair_symv = 1 runs the symmetric product in
+// compensated FP32 (FP64 entries split into FP32 hi/lo pairs, about 2^-46 relative per
+// product; reflectors, updates and everything else stay FP64-accurate).
 int64_t sytrd_blocked_scratch(int64_t n);
 void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, double* d, double* e,
                          double* tau, double* V, double* W, double* y, double* partial,
-                         OzWork* oz, const DevStatus* st);
+                         OzWork* oz, const DevStatus* st, int pair_symv = 0);
 
 // Y (n x ncol) <- Q Y with Q = H_0 ... H_{n-3} from sytrd_lower.  Scratch: V (n x 64),
 // G, T (64 x 64), W, W2 (64 x ncol), ws (ws_cap doubles, for the split-K product

@@ -129,16 +129,26 @@ void trtri_lower(cudaStream_t s, int64_t n, const double* C, int64_t ldc, const 
   cudaMemsetAsync(W, 0, sizeof(double) * (size_t)ldw * n, s);
   set_identity_blocks_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256,
                                0, ::ec::counted(s)>>>(n, W, ldw);
-  for (int64_t k = 0; k < n; k += NB) {
-    const int kb = (int)((n - k) < NB ? (n - k) : NB);
-    const int64_t ncols = k + kb;
-    const double* Dk = Dinv + (k / NB) * NB * NB;
-    double* Wk = W + k;
-    gemm_auto(s, oz, N_, N_, kb, ncols, kb, 1.0, Dk, NB, Wk, ldw, 0.0, Wk, ldw, 0, st);
-    const int64_t rest = n - k - kb;
-    if (rest > 0)
-      gemm_auto(s, oz, N_, N_, rest, ncols, kb, -1.0, C + (k + kb) + k * ldc, ldc, Wk, ldw, 1.0,
-                W + k + kb, ldw, 0, st);
+  // two-level blocking as in the triangular solves: rank-64 steps inside each 192-row
+  // panel, one rank-192 update of the rows below it
+  constexpr int64_t PW = 192;
+  for (int64_t k0 = 0; k0 < n; k0 += PW) {
+    const int64_t pe = (k0 + PW) < n ? (k0 + PW) : n;
+    for (int64_t k = k0; k < pe; k += NB) {
+      const int kb = (int)((n - k) < NB ? (n - k) : NB);
+      const int64_t ncols = k + kb;
+      const double* Dk = Dinv + (k / NB) * NB * NB;
+      double* Wk = W + k;
+      gemm_auto(s, oz, N_, N_, kb, ncols, kb, 1.0, Dk, NB, Wk, ldw, 0.0, Wk, ldw, 0, st);
+      const int64_t inner = pe - k - kb;
+      if (inner > 0)
+        gemm_auto(s, oz, N_, N_, inner, ncols, kb, -1.0, C + (k + kb) + k * ldc, ldc, Wk, ldw,
+                  1.0, W + k + kb, ldw, 0, st);
+    }
+    const int64_t rest = n - pe;
+    if (rest > 0)   // W[pe:, 0:pe] -= C[pe:, k0:pe] W[k0:pe, 0:pe]
+      gemm_auto(s, oz, N_, N_, rest, pe, pe - k0, -1.0, C + pe + k0 * ldc, ldc, W + k0, ldw, 1.0,
+                W + pe, ldw, 0, st);
   }
 }
 

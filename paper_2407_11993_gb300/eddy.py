@@ -21,6 +21,7 @@ EC_SOLVE_INVERSE, EC_SOLVE_SUBSTITUTION = 0, 1
 EC_PREC_FP64, EC_PREC_BF16, EC_PREC_BF16X3 = 0, 1, 2
 EC_PREC_FP32 = 3
 EC_PREC_FP32X2 = 4
+_GEMM = {"tensor": 0, "fp64": 1, "tensor_pairsymv": 2}
 _PREC = {"fp64": EC_PREC_FP64, "bf16": EC_PREC_BF16, "bf16x3": EC_PREC_BF16X3, "fp32": EC_PREC_FP32,
          "fp32x2": EC_PREC_FP32X2}
 
@@ -276,15 +277,15 @@ class ThetaMethod:
             raise ValueError("rhs must be 'sum', 'independent' or 'paired'")
         if not 0 <= int(tile_variant) <= 3:
             raise ValueError("tile_variant must be 0 (autotune) or 1 .. 3")
-        if setup_gemm not in ("tensor", "fp64"):
-            raise ValueError("setup_gemm must be 'tensor' or 'fp64'")
+        if setup_gemm not in _GEMM:
+            raise ValueError("setup_gemm must be 'tensor', 'fp64' or 'tensor_pairsymv'")
         cfg = ec_config(EC_FORM_MODAL if form == "modal" else EC_FORM_PLAIN, float(theta),
                         float(dt), c_void_p(stream or 0), int(device), int(spin_limit),
                         int(bool(profile)),
                         EC_SOLVE_SUBSTITUTION if solver == "substitution" else EC_SOLVE_INVERSE,
                         _PREC[precision], 1 if integrator == "exact" else 0,
                         {"sum": 0, "independent": 1, "paired": 2}[rhs], int(refine_steps),
-                        int(tile_variant), 1 if setup_gemm == "fp64" else 0,
+                        int(tile_variant), _GEMM[setup_gemm],
                         int(bool(release_inputs)))
         self.rhs = rhs
         self.log_path = log_path

@@ -217,6 +217,51 @@ def gemm_case(args) -> dict:
             "fp64_equiv_tflops": 2.0 * M * N * K / best / 1e12, "max_err_rel_absAB": err}
 
 
+def compare_setup_case(args) -> dict:
+    """The modal setup with the tridiagonalisation's symmetric products in FP64 (tensor
+    path) and in compensated FP32 (tensor_pairsymv) on the headline recipe at size --n:
+    setup seconds per phase, tau and the first T steps' outputs of the two, and sampled
+    eigen-residuals ||L u - tau R u|| / (||L u|| + tau ||R u||) of each (host products)."""
+    import numpy as np
+
+    from paper_2407_11993_gb300 import eddy
+    from workloads import synth
+
+    p = synth.config4(T=args.T, n=args.n)
+    out = {"n": args.n, "T": args.T}
+    res = {}
+    idx = None
+    for g in ("tensor", "tensor_pairsymv"):
+        tm = eddy.ThetaMethod("modal", p.theta, p.dt, profile=True, setup_gemm=g,
+                              release_inputs=True)
+        tm.setup(p.L, p.R, None, p.M, None, p.C)
+        tms = tm.timings()
+        pr, sn = tm.run(p.T, p.src, None, p.snap_stride)
+        tau, U = tm.modes()
+        tm.close()
+        n0 = tau.size
+        if idx is None:
+            idx = np.unique(np.linspace(0, n0 - 1, 16).astype(int))
+        Us = np.ascontiguousarray(U[:, idx])
+        del U
+        LU, RU = p.L @ Us, p.R @ Us
+        eres = np.linalg.norm(LU - RU * tau[idx], axis=0) / (
+            np.linalg.norm(LU, axis=0) + tau[idx] * np.linalg.norm(RU, axis=0))
+        gram = Us.T @ RU
+        res[g] = (tau, np.asarray(pr), np.asarray(sn))
+        out[g] = {k: tms[k] for k in ("factor_ms", "reduce_ms", "tridiag_ms", "eig_ms",
+                                       "backtransform_ms", "setup_ms")}
+        out[g].update(eigen_residual_max=float(eres.max()),
+                      r_orthonormality_max=float(np.abs(gram - np.eye(idx.size)).max()))
+    (t0, p0, s0), (t1, p1, s1) = res["tensor"], res["tensor_pairsymv"]
+    out["tau_rel_max"] = float(np.max(np.abs(t1 - t0)) / np.max(np.abs(t0)))
+    out["probe_rel_per_trace"] = float((np.linalg.norm(p1 - p0, axis=1) /
+                                        np.linalg.norm(p0, axis=1)).max())
+    out["snapshot_rel_per_snapshot"] = float((np.linalg.norm(s1 - s0, axis=0) /
+                                              np.linalg.norm(s0, axis=0)).max()) if s0.size else None
+    return out
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--form", choices=["plain", "modal"], default="plain")
@@ -226,7 +271,7 @@ def main() -> None:
     ap.add_argument("--no-electrodes", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp32x2", "bf16", "bf16x3"])
     ap.add_argument("--refine", type=int, default=0, help="plain fp32: refinement sweeps per step")
-    ap.add_argument("--setup-gemm", default="tensor", choices=["tensor", "fp64"],
+    ap.add_argument("--setup-gemm", default="tensor", choices=["tensor", "fp64", "tensor_pairsymv"],
                     help="arithmetic units of the setup's large dense products")
     ap.add_argument("--config4", action="store_true",
                     help="the N=65,536 headline recipe (one coil, 4 pickups, dt = 0.1 us, no "
@@ -247,6 +292,8 @@ def main() -> None:
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="one FP64-accurate tensor-core product of this shape")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--compare-setup", action="store_true",
+                    help="modal setup with FP64 vs compensated-FP32 symmetric products")
     ap.add_argument("--grad-config5", action="store_true",
                     help="the differentiation workload (N=4096, T=5000, checkpoints every 250)")
     args = ap.parse_args()
@@ -266,6 +313,9 @@ def main() -> None:
         return
     if args.grad_config5:
         print(json.dumps(grad_config5_case(args)))
+        return
+    if args.compare_setup:
+        print(json.dumps(compare_setup_case(args)))
         return
     if args.gemm:
         print(json.dumps(gemm_case(args)))

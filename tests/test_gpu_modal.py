@@ -222,11 +222,13 @@ def test_twenty_thousand_steps_against_oracle(eddy, form):
     assert scaled < TOL
 
 
-@pytest.mark.parametrize("n,setup_gemm", [(2048, "tensor"), (4096, "tensor"), (2048, "fp64")])
+@pytest.mark.parametrize("n,setup_gemm", [(2048, "tensor"), (4096, "tensor"), (2048, "fp64"),
+                                          (4096, "tensor_pairsymv")])
 def test_eigen_invariants_large(eddy, n, setup_gemm):
     """U^T R U = 1 and U^T L U = diag(tau) (Sec. 3.2) at sizes where the divide and
     conquer merges and the blocked back-transformation run many levels; tau against the
-    oracle's generalised eigenvalues."""
+    oracle's generalised eigenvalues.  The same bounds hold for the compensated-FP32
+    symmetric products of the tridiagonalisation."""
     p = synth.small(n, T=1, seed=n + 7, electrodes=False, coil=True)
     tm = eddy.ThetaMethod("modal", p.theta, p.dt, setup_gemm=setup_gemm)
     tm.setup(p.L, p.R, None, p.M, None, p.C)
@@ -259,11 +261,12 @@ def test_theta_zero_explicit_euler(eddy, form):
     assert rel_snaps(snaps, ref.snaps) < TOL
 
 
-@pytest.mark.parametrize("setup_gemm", ["tensor", "fp64"])
+@pytest.mark.parametrize("setup_gemm", ["tensor", "fp64", "tensor_pairsymv"])
 @pytest.mark.parametrize("n", [65, 700, 2100])
 def test_setup_arithmetic_paths(eddy, n, setup_gemm):
-    """Both arithmetic paths of the setup's dense products (tensor-core FP64 emulation,
-    the default, and the FP64 CUDA cores) give the oracle's trajectory; sizes span the
+    """The arithmetic paths of the setup's dense products (tensor-core FP64 emulation,
+    the default, the FP64 CUDA cores, and the tensor path with the tridiagonalisation's
+    symmetric products in compensated FP32) give the oracle's trajectory; sizes span the
     blocked tridiagonalisation's panels, several compact-WY groups and divide-and-conquer
     merges of 1024+ rows."""
     p = synth.small(n, T=30, seed=n + 5, electrodes=True, coil=True, snap_stride=10)

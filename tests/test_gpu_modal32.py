@@ -141,3 +141,24 @@ def test_set_precision_reuses_the_modes(eddy):
     assert np.array_equal(p64, p64b) and np.array_equal(s64, s64b)
     assert np.array_equal(px, pd) and np.array_equal(sx, sd)
     assert rel_traces(px, p64) < 1e-10 and rel_snaps(sx, s64) < 1e-10
+
+
+@pytest.mark.parametrize("keep,stride", [(None, 3), (1500, 1), (4099, 30)])
+def test_fp64_reconstruction_from_kept_slices(eddy, keep, stride):
+    """From N0 = 4096 on, FP64 snapshot reconstructions multiply U's kept tensor-core
+    slices (narrow MMAs for up to 32 columns).  Against the FP64-core path of the same
+    setup arithmetic (no kept slices) on 1 to 30 snapshot columns and truncated modes, at the
+    FP64 bar (the two setups round differently)."""
+    p = synth.small(4100, 30, seed=3, electrodes=False, coil=True, probes=4, snap_stride=stride)
+    outs = {}
+    for g in ("tensor", "fp64"):
+        tm = eddy.ThetaMethod("modal", p.theta, p.dt, setup_gemm=g)
+        tm.setup(p.L, p.R, None, p.M, None, p.C)
+        if keep:
+            tm.set_mode_count(keep)
+        outs[g] = tm.run(p.T, p.src, None, stride)
+        tm.close()
+    (pt, st_), (pf, sf) = outs["tensor"], outs["fp64"]
+    ep, es = rel_traces(pt, pf), rel_snaps(st_, sf)
+    print(f"kept slices keep={keep} stride={stride}: per-trace {ep:.2e}, per-snapshot {es:.2e}")
+    assert ep < 1e-10 and es < 1e-10

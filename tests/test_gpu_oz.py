@@ -44,7 +44,10 @@ def _exact(A, B, ta=False, tb=False):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (127, 65, 33), (128, 64, 192), (129, 63, 193),
-                                   (300, 200, 385), (64, 1000, 1500)])
+                                   (300, 200, 385), (64, 1000, 1500),
+                                   # narrow products (MMA width 16 / 32)
+                                   (4096, 4, 1000), (257, 16, 200), (300, 17, 385), (700, 32, 64),
+                                   (129, 33, 97)])
 def test_integer_inputs_are_exact(eddy, M, N, K):
     rng = np.random.default_rng(M * 7 + N + K)
     A = rng.integers(-1000, 1001, size=(M, K)).astype(np.float64)
@@ -54,7 +57,8 @@ def test_integer_inputs_are_exact(eddy, M, N, K):
 
 
 @pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
-@pytest.mark.parametrize("M,N,K", [(127, 65, 33), (300, 200, 385), (513, 130, 1000)])
+@pytest.mark.parametrize("M,N,K", [(127, 65, 33), (300, 200, 385), (513, 130, 1000),
+                                   (2000, 5, 3000), (300, 20, 385)])
 def test_random_within_fp64_bound(eddy, M, N, K, ta, tb):
     rng = np.random.default_rng(M + 3 * N + 5 * K + 11 * ta + 13 * tb)
     A = rng.standard_normal((K, M) if ta else (M, K))
