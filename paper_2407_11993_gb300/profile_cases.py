@@ -253,6 +253,20 @@ def compare_setup_case(args) -> dict:
                                        "backtransform_ms", "setup_ms")}
         out[g].update(eigen_residual_max=float(eres.max()),
                       r_orthonormality_max=float(np.abs(gram - np.eye(idx.size)).max()))
+    # the plain form on the same recipe as the common reference of both
+    tp = eddy.ThetaMethod("plain", p.theta, p.dt, release_inputs=True)
+    tp.setup(p.L, p.R, None, p.M, None, p.C)
+    pp, sp = (np.asarray(x) for x in tp.run(p.T, p.src, None, p.snap_stride))
+    tp.close()
+
+    def rel_cols(a, b, axis):
+        num = np.linalg.norm(a - b, axis=axis)
+        den = np.linalg.norm(b, axis=axis)
+        return float((num / np.where(den > 0, den, 1.0)).max()) if a.size else None
+
+    for g in ("tensor", "tensor_pairsymv"):
+        out[g]["vs_plain_probe_rel_per_trace"] = rel_cols(res[g][1], pp, 1)
+        out[g]["vs_plain_snapshot_rel"] = rel_cols(res[g][2], sp, 0)
     (t0, p0, s0), (t1, p1, s1) = res["tensor"], res["tensor_pairsymv"]
     out["tau_rel_max"] = float(np.max(np.abs(t1 - t0)) / np.max(np.abs(t0)))
     out["probe_rel_per_trace"] = float((np.linalg.norm(p1 - p0, axis=1) /
