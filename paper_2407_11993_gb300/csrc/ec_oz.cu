@@ -429,6 +429,248 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
                  : "memory");
 }
 
+// ---- few-column products from kept slices (stream-K) ------------------------
+// C (M x N, N <= 32) = A B with A's slices cut once (OzSplit) and K long: the work is
+// the list of (row tile, 192-long K chunk) items in tile-major order, cut into equal
+// contiguous ranges, one per CTA, so every SM streams the same share of A's slices in a
+// single launch.  Each chunk's six accumulators go to one of two TMEM sets (the MMAs of
+// the next chunk run while the epilogue folds this one); the epilogue turns every chunk
+// into binary64 (exact integer, one rounding) and sums the chunks of a tile in FP64
+// registers.  A tile whose chunks all lie in one range is stored; a tile cut between two
+// ranges is added by both CTAs into the zeroed C with atomicAdd -- two addends onto zero,
+// so the result does not depend on their order.
+constexpr int NW_EPI_WARPS = 4;                         // one per TMEM lane quarter
+constexpr int NW_THREADS = (2 + NW_EPI_WARPS) * 32;
+constexpr int NW_NMAX = 32;
+constexpr int NW_SET_COLS = NACC * NW_NMAX;             // 192 columns per accumulator set
+constexpr int NW_TMEM_COLS = 512;
+constexpr int NW_B_BYTES = OZ_S * NW_NMAX * TK * 2;     // 16 KB
+constexpr int NW_STAGE = A_BYTES + NW_B_BYTES;          // 80 KB
+constexpr int NW_SMEM = STAGES * NW_STAGE + 1024;
+static_assert(2 * NW_SET_COLS <= NW_TMEM_COLS, "two accumulator sets exceed tensor memory");
+
+struct NarrowArgs {
+  int M, N, nmma;          // rows, columns (<= nmma), MMA width (16 or 32)
+  int K, nkc;              // K and its 192-long chunks
+  int64_t items, per_cta;  // (tile, chunk) items and the items of one CTA's range
+  double* C;
+  int64_t ldc;
+  const int* ea;
+  const int* eb;
+};
+
+__global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
+    const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+    const NarrowArgs a, DevStatus* st) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2],
+      acc_empty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag, issued, consumed, skip;
+  if (threadIdx.x == 0) skip = *(volatile int*)&st->code;
+  __syncthreads();
+  if (skip) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * a.per_cta;
+  const int64_t i1 = (i0 + a.per_cta) < a.items ? (i0 + a.per_cta) : a.items;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(NW_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], NW_EPI_WARPS);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t b_bytes = (uint32_t)(OZ_S * a.nmma * TK * 2);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int64_t i = i0; i < i1 && !*(volatile int*)&abort_flag; ++i) {
+        const int tile = (int)(i / a.nkc), kc = (int)(i % a.nkc);
+        const int kbeg = kc * OZ_KCHUNK;
+        const int klen = (a.K - kbeg) < OZ_KCHUNK ? (a.K - kbeg) : OZ_KCHUNK;
+        const int nkb = (klen + TK - 1) / TK;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int q = (int)(it % STAGES);
+          const uint32_t use = it / STAGES;
+          if (it >= STAGES && !mbar_wait(&empty_bar[q], (use - 1) & 1, st, 51)) {
+            *(volatile int*)&abort_flag = 1;
+            break;
+          }
+          uint8_t* sa = smem + q * NW_STAGE;
+          uint8_t* sb = sa + A_BYTES;
+          mbar_expect_tx(&full_bar[q], A_BYTES + b_bytes);
+          tma_load_3d(sa, &mapA, &full_bar[q], kbeg + kb * TK, tile * TM, 0);
+          tma_load_3d(sb, &mapB, &full_bar[q], kbeg + kb * TK, 0, 0);
+          *(volatile int*)&issued = (int)(it + 1);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_for(a.nmma);
+      const uint32_t b_slice = (uint32_t)(a.nmma * TK * 2);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t i = i0; ok && i < i1 && !*(volatile int*)&abort_flag; ++i) {
+        const int64_t li = i - i0;
+        const int set = (int)(li & 1);
+        const int kc = (int)(i % a.nkc);
+        const int kbeg = kc * OZ_KCHUNK;
+        const int klen = (a.K - kbeg) < OZ_KCHUNK ? (a.K - kbeg) : OZ_KCHUNK;
+        const int nkb = (klen + TK - 1) / TK;
+        // the epilogue must have taken this set's previous chunk
+        if (li >= 2 && !mbar_wait(&acc_empty[set], (uint32_t)(((li >> 1) - 1) & 1), st, 56)) {
+          *(volatile int*)&abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tset = tmem + (uint32_t)(set * NW_SET_COLS);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int q = (int)(it % STAGES);
+          if (!mbar_wait(&full_bar[q], (it / STAGES) & 1, st, 52)) {
+            *(volatile int*)&abort_flag = 1;
+            ok = false;
+            break;
+          }
+          *(volatile int*)&consumed = (int)(it + 1);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + q * NW_STAGE);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int d = 0; d <= OZ_DMAX; ++d) {
+            const int acc = d < OZ_EXACT ? d : OZ_EXACT;
+            const uint32_t tacc = tset + (uint32_t)(acc * a.nmma);
+#pragma unroll
+            for (int si = 0; si <= d; ++si) {
+              const int ti = d - si;
+              if (si >= OZ_S || ti >= OZ_S) continue;
+              const uint64_t da = smem_desc(sa + si * A_SLICE);
+              const uint64_t db = smem_desc(sb + ti * b_slice);
+#pragma unroll
+              for (int kk = 0; kk < TK / 16; ++kk) {
+                const bool first = kb == 0 && kk == 0 && si == 0 && d <= OZ_EXACT;
+                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, first ? 0u : 1u);
+              }
+            }
+          }
+          mma_commit(&empty_bar[q]);
+        }
+        mma_commit(&acc_full[set]);
+      }
+      mma_commit(&done_bar);
+    }
+  } else {
+    // epilogue: warp 2 + q reads TMEM lanes 32 q .. 32 q + 31 (rows of the tile)
+    const int quarter = warp - 2;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    double acc[NW_NMAX];
+#pragma unroll
+    for (int j = 0; j < NW_NMAX; ++j) acc[j] = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const int64_t li = i - i0;
+      const int set = (int)(li & 1);
+      const int tile = (int)(i / a.nkc), kc = (int)(i % a.nkc);
+      if (!mbar_wait(&acc_full[set], (uint32_t)((li >> 1) & 1), st, 57)) {
+        *(volatile int*)&abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (*(volatile int*)&abort_flag) break;
+      const int row = tile * TM + quarter * 32 + lane;
+      const bool row_ok = row < a.M;
+      const int erow = row_ok ? a.ea[row] - 56 : 0;
+#pragma unroll
+      for (int g = 0; g < NW_NMAX / 16; ++g) {
+        if (g * 16 >= a.nmma) break;
+        uint32_t r[NACC][16];
+#pragma unroll
+        for (int q = 0; q < NACC; ++q)
+          tmem_ld16(lane_base + (uint32_t)(set * NW_SET_COLS + q * a.nmma + g * 16), r[q]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = g * 16 + j;
+          const int i0v = __float2int_rn(__uint_as_float(r[0][j]));
+          const int i1v = __float2int_rn(__uint_as_float(r[1][j]) * 256.0f);
+          const int i2v = __float2int_rn(__uint_as_float(r[2][j]) * 65536.0f);
+          const int i3v = __float2int_rn(__uint_as_float(r[3][j]) * 16777216.0f);
+          const int i4v = __float2int_rn(__uint_as_float(r[4][j]) * 4294967296.0f);
+          const int igv = __float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);
+          int64_t X = (int64_t)(i0v * 256 + i1v) * 4294967296ll;
+          X += (int64_t)i2v * (1 << 24);
+          X += (int64_t)i3v * (1 << 16);
+          X += (int64_t)i4v * (1 << 8);
+          X += igv;
+          const int sc = erow + (col < a.N ? a.eb[col] : 0);
+          uint64_t bits;
+          if (!oz::i64_scaled_to_f64_bits_fast(X, sc, &bits)) {
+            const double slow = X == 0 ? 0.0 : ldexp((double)X, sc);
+            bits = (uint64_t)__double_as_longlong(slow);
+          }
+          acc[col] += __longlong_as_double((long long)bits);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) dev::mbar_arrive(&acc_empty[set]);
+      // the tile's last chunk in this range: store, or add when another range has
+      // (or will have) the rest of the tile
+      const bool last_here = kc == a.nkc - 1 || i + 1 == i1;
+      if (last_here) {
+        const int64_t tile_first = (int64_t)tile * a.nkc;
+        const bool whole = tile_first >= i0 && kc == a.nkc - 1;
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < NW_NMAX; ++j) {
+            if (j >= a.N) break;
+            double* cp = a.C + (int64_t)row + (int64_t)j * a.ldc;
+            if (whole) *cp = acc[j];
+            else atomicAdd(cp, acc[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NW_NMAX; ++j) acc[j] = 0.0;
+      }
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(&done_bar, 0, st, 53)) abort_flag = 1;
+    if (abort_flag)
+      for (int it = consumed; it < issued; ++it)
+        mbar_wait(&full_bar[it % STAGES], (it / STAGES) & 1, st, 54);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(NW_TMEM_COLS)
+                 : "memory");
+}
+
 // ---- operand split --------------------------------------------------------
 // Logical operand X (R x K): element (r, k) at src[r * rs + k * ks] (one of rs, ks is 1).
 constexpr int ST = 64;   // split tile: 64 rows x 64 K
@@ -709,6 +951,38 @@ ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb
   // the map covers kuse columns of the slices (ldk stays a.ldk): reads past kuse are zero
   if (!make_slice_map_ld(&ma, a.slices, a.R, kuse, ldk, a.R, TM)) return EC_ERR_CUDA;
   const int64_t brs = tb == N_ ? ldb : 1, bks = tb == N_ ? 1 : ldb;
+  if (N <= NW_NMAX && beta == 0.0) {
+    // few columns: one stream-K launch over all (row tile, K chunk) items
+    static std::atomic<unsigned long long> nw_attr{0};
+    if (first_on_device(nw_attr))
+      cudaFuncSetAttribute(oz_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
+    split(s, N, kuse, B, brs, bks, w->maxb, w->slices, ldk, w->exps);
+    const int nm = nmma_for(N);
+    CUtensorMap mb;
+    if (!make_slice_map(&mb, w->slices, N, kuse, ldk, nm)) return EC_ERR_CUDA;
+    NarrowArgs na{};
+    na.M = (int)a.R;
+    na.N = (int)N;
+    na.nmma = nm;
+    na.K = (int)kuse;
+    na.nkc = (int)((kuse + OZ_KCHUNK - 1) / OZ_KCHUNK);
+    const int64_t tiles = (a.R + TM - 1) / TM;
+    na.items = tiles * na.nkc;
+    // ranges of at least one tile's chunks, so a tile is cut between two ranges at most
+    int64_t grid = std::min<int64_t>((int64_t)num_sms(), na.items / na.nkc);
+    if (grid < 1) grid = 1;
+    na.per_cta = (na.items + grid - 1) / grid;
+    grid = (na.items + na.per_cta - 1) / na.per_cta;
+    na.C = C;
+    na.ldc = ldc;
+    na.ea = a.exps;
+    na.eb = w->exps;
+    if (cudaMemset2DAsync(C, sizeof(double) * (size_t)ldc, 0, sizeof(double) * (size_t)a.R,
+                          (size_t)N, s) != cudaSuccess)
+      return EC_ERR_CUDA;
+    oz_narrow_kernel<<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(ma, mb, na, st);
+    return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+  }
   for (int64_t j0 = 0; j0 < N; j0 += pn) {
     const int64_t nj = std::min(pn, N - j0);
     split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
@@ -796,6 +1070,10 @@ extern "C" ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, 
   if (!A || !B || !C) return EC_ERR_ARG;
   const int64_t arows = ta ? K : M, brows = tb ? N : K;
   if (lda < (arows > 1 ? arows : 1) || ldb < (brows > 1 ? brows : 1) || ldc < M) return EC_ERR_ARG;
+  if ((lower & ~3) != 0) return EC_ERR_ARG;
+  const bool presplit = (lower & 2) != 0 && K > 0;
+  lower &= 1;
+  if (presplit && (lower || alpha != 1.0)) return EC_ERR_ARG;
   if (lower && M != N) return EC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   DevStatus* st = nullptr;
@@ -805,8 +1083,18 @@ extern "C" ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, 
   }
   cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
   OzWork w;
-  ec_status rc = oz_gemm(s, ta ? T_ : N_, tb ? T_ : N_, M, N, K, alpha, A, lda, B, ldb, beta, C,
-                         ldc, lower ? 1 : 0, &w, st);
+  ec_status rc = EC_OK;
+  if (presplit) {
+    OzSplit sa;
+    rc = oz_presplit(s, ta ? T_ : N_, M, K, A, lda, &sa);
+    if (rc == EC_OK)
+      rc = oz_gemm_presplit(s, sa, K, tb ? T_ : N_, N, B, ldb, beta, C, ldc, &w, st);
+    cudaStreamSynchronize(s);
+    oz_split_free(&sa);
+  } else {
+    rc = oz_gemm(s, ta ? T_ : N_, tb ? T_ : N_, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                 lower ? 1 : 0, &w, st);
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   DevStatus h{};
   if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);

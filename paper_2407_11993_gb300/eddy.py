@@ -169,9 +169,12 @@ def gemm_bf16(A, B, C=None, stream=None):
 
 
 def gemm_f64_emulated(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, ta: bool = False,
-                      tb: bool = False, lower: bool = False, stream=None):
+                      tb: bool = False, lower: bool = False, stream=None,
+                      kept_slices: bool = False):
     """C = alpha op(A) op(B) + beta C to FP64 accuracy on the tensor cores (CUDA float64
-    tensors, any memory order is copied to column-major; returns C as a tensor)."""
+    tensors, any memory order is copied to column-major; returns C as a tensor).
+    kept_slices: the path of the modal snapshot products (op(A) cut once into its own
+    slice buffer; alpha = 1, no lower-triangle mode)."""
     import torch
     opA = A.t() if ta else A
     opB = B.t() if tb else B
@@ -188,7 +191,8 @@ def gemm_f64_emulated(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, ta: b
         C.t().contiguous()
     check(lib().ec_gemm_f64_emulated(int(ta), int(tb), M, N, K, float(alpha),
                                      c_void_p(Acm.data_ptr()), lda, c_void_p(Bcm.data_ptr()), ldb,
-                                     float(beta), c_void_p(Ct.data_ptr()), max(1, M), int(lower),
+                                     float(beta), c_void_p(Ct.data_ptr()), max(1, M),
+                                     int(lower) | (2 if kept_slices else 0),
                                      c_void_p(stream or 0)), "ec_gemm_f64_emulated")
     return Ct.t()
 

@@ -111,3 +111,25 @@ def test_zero_rows_and_columns(eddy):
     C = _run(eddy, A, B)
     assert np.all(C[5] == 0.0) and np.all(C[:, 7] == 0.0)
     assert np.all(np.abs(C - _exact(A, B)) <= 70 * U * (np.abs(A) @ np.abs(B)))
+
+
+@pytest.mark.parametrize("M,N,K", [(20000, 4, 1000), (19500, 30, 700), (4100, 1, 4099),
+                                   (300, 32, 385), (129, 17, 193), (33000, 8, 250)])
+def test_kept_slices_stream_k(eddy, M, N, K):
+    """The modal snapshot path (A's slices kept, one stream-K launch for N <= 32): with
+    more row tiles than SMs some tiles are cut between two CTAs and added to the zeroed C
+    by both (two addends: order-independent).  Integer inputs are exact; the result is the
+    same as the per-call path bit for bit on random inputs only up to FP64 rounding, so
+    random inputs are checked against the FP64 bound."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.integers(-1000, 1001, size=(M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, size=(K, N)).astype(np.float64)
+    C = eddy.gemm_f64_emulated(_cuda(A), _cuda(B), kept_slices=True).cpu().numpy()
+    assert np.array_equal(C, _exact(A, B))
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    C1 = eddy.gemm_f64_emulated(_cuda(A), _cuda(B), kept_slices=True).cpu().numpy()
+    C2 = eddy.gemm_f64_emulated(_cuda(A), _cuda(B), kept_slices=True).cpu().numpy()
+    assert np.array_equal(C1, C2)                       # run to run
+    bound = 4.0 * K * 2.0 ** -53 * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(C1 - A @ B) <= bound + 1e-300)
