@@ -14,6 +14,30 @@
 namespace ec {
 namespace ff {
 
+// The same split with fewer integer operations: lo is the 29 bits below hi converted
+// by one integer-to-float instruction (rounded to 24 bits) and scaled by a power of two
+// built from the exponent.  a = hi + lo + r, |r| < 2^-47 |a|; lo is 0 when its scale
+// would leave FP32's normal range (|a| below about 2^-74); other cases as split().
+__device__ __forceinline__ float2 split_fast(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+  const unsigned sgn = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int eh = e - 896;
+  const unsigned mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  const int es = e - 948;                                // biased exponent of 2^(e - 1075)
+  const float scale = es >= 1 ? __int_as_float((int)(sgn | ((unsigned)es << 23))) : 0.f;
+  float2 r;
+  r.x = __int_as_float((int)(sgn | ((unsigned)eh << 23) | mh));
+  r.y = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+  if (eh < 1 || eh > 254) {
+    r.x = e == 2047 ? __int_as_float((int)(sgn | 0x7FC00000u))
+                    : (eh > 254 ? __int_as_float((int)(sgn | 0x7F800000u)) : 0.f);
+    r.y = 0.f;
+  }
+  return r;
+}
+
 // a = hi + lo + r with |r| < 2^-47 |a|: hi is a truncated to 24 significant bits, lo
 // the next 24 bits (truncated).  Magnitudes below FP32's normal range contribute 0; a
 // non-finite or out-of-range a gives hi = NaN / +-inf.

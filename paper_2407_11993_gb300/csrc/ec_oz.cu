@@ -582,8 +582,9 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
       mma_commit(&done_bar);
     }
   } else {
-    // epilogue: warp 2 + q reads TMEM lanes 32 q .. 32 q + 31 (rows of the tile)
-    const int quarter = warp - 2;
+    // epilogue: a warp may read only TMEM lanes 32 (warp % 4) .. + 31: warps 2..5 cover
+    // the four lane quarters (rows of the tile)
+    const int quarter = warp & 3;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     double acc[NW_NMAX];
 #pragma unroll

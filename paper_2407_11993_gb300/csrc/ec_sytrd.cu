@@ -489,7 +489,8 @@ __global__ void __launch_bounds__(256) symv_tile_kernel(int64_t n, const double*
 // every tile (prow[J][rows of I]) and keeps the column part of its whole segment in
 // registers, written once (pcol[k][columns of J]).  For a row r of block B:
 //   (A22 v)[r] = sum_{J <= B} prow[J][r] + sum_{k < nseg(B)} pcol[k][r],
-// nseg(B) = ceil((nbk - B) / SEG), summed in that order by p_latrd_kernel.
+// nseg(B) = ceil((nbk - B) / SEG); p_latrd_kernel adds them in a fixed order (eight
+// interleaved partial sums, then those in order).
 constexpr int SEG = 16;
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
@@ -527,12 +528,24 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
   auto load = [&](int64_t I, int b) {
     double* As = sbuf + b * 64 * 65;
     const int64_t r0 = I * 64;
-    for (int q = tid; q < 64 * 64; q += 256) {
-      const int rr = q & 63, cc = q >> 6;
-      const int64_t r = r0 + rr, c = c0 + cc;
-      const bool ok = r < m && c < m && (I != J || rr >= cc);
-      cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + r) + (s0 + c) * lda)
-                                      : (const void*)A, ok);
+    if (PAIR && I != J) {
+      // the FP32 pair of A[r, c] (r > c) is kept at position (c, r): read it transposed,
+      // consecutive threads along c
+      for (int q = tid; q < 64 * 64; q += 256) {
+        const int cc = q & 63, rr = q >> 6;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        const bool ok = r < m && c < m;
+        cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + c) + (s0 + r) * lda)
+                                        : (const void*)A, ok);
+      }
+    } else {
+      for (int q = tid; q < 64 * 64; q += 256) {
+        const int rr = q & 63, cc = q >> 6;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        const bool ok = r < m && c < m && (I != J || rr >= cc);
+        cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + r) + (s0 + c) * lda)
+                                        : (const void*)A, ok);
+      }
     }
     if (tid < 64) {
       vr[b][tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
@@ -556,14 +569,17 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
     const double* As = sbuf + b * 64 * 65;
     const int64_t r0 = I * 64;
     if constexpr (PAIR) {
-      // split the tile in place (each 8-byte slot becomes its FP32 pair)
-      double* Aw = sbuf + b * 64 * 65;
-      float2* A2w = reinterpret_cast<float2*>(Aw);
-      for (int q = tid; q < 64 * 64; q += 256) {
-        const int idx = (q >> 6) * 65 + (q & 63);
-        A2w[idx] = ff::split(Aw[idx]);
+      if (I == J) {
+        // the diagonal tile comes from the FP64 lower triangle: split it in place (each
+        // 8-byte slot becomes its FP32 pair); the others arrived as pairs
+        double* Aw = sbuf + b * 64 * 65;
+        float2* A2w = reinterpret_cast<float2*>(Aw);
+        for (int q = tid; q < 64 * 64; q += 256) {
+          const int idx = (q >> 6) * 65 + (q & 63);
+          A2w[idx] = ff::split_fast(Aw[idx]);
+        }
+        __syncthreads();
       }
-      __syncthreads();
       const float2* A2 = reinterpret_cast<const float2*>(As);
       float rh0 = 0.f, rl0 = 0.f, rh1 = 0.f, rl1 = 0.f;
 #pragma unroll
@@ -638,6 +654,31 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
   }
 }
 
+// FP32 pair copies of the trailing lower triangle A[t0:, t0:] for the compensated
+// symmetric product: the pair of A[r, c] (r > c) is written to the free upper position
+// (c, r), through a shared-memory transpose so that both sides are coalesced.  One CTA
+// per 64 x 64 tile (I, J), I >= J, of the trailing block.
+__global__ void __launch_bounds__(256) pair_upper_kernel(int64_t n, double* A, int64_t lda,
+                                                         int64_t t0) {
+  __shared__ float2 T2[64][65];
+  const int64_t I = blockIdx.x, J = blockIdx.y;
+  if (I < J) return;
+  const int64_t m = n - t0, r0 = t0 + I * 64, c0 = t0 + J * 64;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < 64 * 64; q += 256) {
+    const int rr = q & 63, cc = q >> 6;                 // read down the columns
+    const int64_t r = r0 + rr, c = c0 + cc;
+    if (r - t0 < m && c - t0 < m && r > c) T2[cc][rr] = ff::split_fast(A[r + c * lda]);
+  }
+  __syncthreads();
+  float2* A2 = reinterpret_cast<float2*>(A);
+  for (int q = tid; q < 64 * 64; q += 256) {
+    const int cc = q & 63, rr = q >> 6;                 // write along the rows
+    const int64_t r = r0 + rr, c = c0 + cc;
+    if (r - t0 < m && c - t0 < m && r > c) A2[c + r * lda] = T2[cc][rr];
+  }
+}
+
 // As p_kernel, with the panel's corrections: for rows r > j,
 //   p_r = tau ( (A22 v)_r - V[r, 0:i] y1 - W[r, 0:i] y2 ),
 // then w = p - (tau/2)(p^T v) v by the last CTA.
@@ -658,57 +699,70 @@ __global__ void __launch_bounds__(256) p_latrd_kernel(int64_t n, int64_t j, cons
   const int64_t len = n - j - 1;
   double dot = 0.0;
   const int64_t nbk = (len + 63) / 64;
-  // one thread per row (the grid covers the rows once); the partials of the row are
-  // added in block / segment order, two independent chains each
-  for (int64_t r = j + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t rl = r - (j + 1), blk = rl >> 6;
-    const int64_t nseg = (nbk - blk + SEG - 1) / SEG;
-    double q;
-    if constexpr (PAIR) {
-      const float2* pr2 = reinterpret_cast<const float2*>(prow);
-      const float2* pc2 = reinterpret_cast<const float2*>(pcol);
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-      int64_t b = 0;
-      for (; b + 1 <= blk; b += 2) {
-        const float2 x0 = pr2[b * mp + rl], x1 = pr2[(b + 1) * mp + rl];
-        ff::add(h0, l0, x0.x, x0.y);
-        ff::add(h1, l1, x1.x, x1.y);
+  // 32 rows per pass: the 8 warps split each row's partials (warp q takes partials
+  // q, q + 8, ...), their sums are added in warp order, and warp 0 finishes the rows
+  __shared__ double part[8][32];
+  const int rlane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  for (int64_t g0 = (int64_t)blockIdx.x * 32; g0 < len; g0 += (int64_t)gridDim.x * 32) {
+    const int64_t rl = g0 + rlane;
+    double acc = 0.0;
+    if (rl < len) {
+      const int64_t blk = rl >> 6;
+      const int64_t nseg = (nbk - blk + SEG - 1) / SEG;
+      if constexpr (PAIR) {
+        const float2* pr2 = reinterpret_cast<const float2*>(prow);
+        const float2* pc2 = reinterpret_cast<const float2*>(pcol);
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        int64_t b = wq;
+        for (; b + 8 <= blk; b += 16) {
+          const float2 x0 = pr2[b * mp + rl], x1 = pr2[(b + 8) * mp + rl];
+          ff::add(h0, l0, x0.x, x0.y);
+          ff::add(h1, l1, x1.x, x1.y);
+        }
+        if (b <= blk) ff::add(h0, l0, pr2[b * mp + rl].x, pr2[b * mp + rl].y);
+        b = wq;
+        for (; b + 8 < nseg; b += 16) {
+          const float2 x0 = pc2[b * mp + rl], x1 = pc2[(b + 8) * mp + rl];
+          ff::add(h0, l0, x0.x, x0.y);
+          ff::add(h1, l1, x1.x, x1.y);
+        }
+        if (b < nseg) ff::add(h0, l0, pc2[b * mp + rl].x, pc2[b * mp + rl].y);
+        acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+      } else {
+        double q0 = 0.0, q1 = 0.0;
+        int64_t b = wq;
+        for (; b + 8 <= blk; b += 16) {
+          q0 += prow[b * mp + rl];
+          q1 += prow[(b + 8) * mp + rl];
+        }
+        if (b <= blk) q0 += prow[b * mp + rl];
+        b = wq;
+        for (; b + 8 < nseg; b += 16) {
+          q0 += pcol[b * mp + rl];
+          q1 += pcol[(b + 8) * mp + rl];
+        }
+        if (b < nseg) q0 += pcol[b * mp + rl];
+        acc = q0 + q1;
       }
-      if (b <= blk) ff::add(h0, l0, pr2[b * mp + rl].x, pr2[b * mp + rl].y);
-      b = 0;
-      for (; b + 1 < nseg; b += 2) {
-        const float2 x0 = pc2[b * mp + rl], x1 = pc2[(b + 1) * mp + rl];
-        ff::add(h0, l0, x0.x, x0.y);
-        ff::add(h1, l1, x1.x, x1.y);
-      }
-      if (b < nseg) ff::add(h0, l0, pc2[b * mp + rl].x, pc2[b * mp + rl].y);
-      q = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
-    } else {
-      double q0 = 0.0, q1 = 0.0, c0 = 0.0, c1 = 0.0;
-      int64_t b = 0;
-      for (; b + 1 <= blk; b += 2) {
-        q0 += prow[b * mp + rl];
-        q1 += prow[(b + 1) * mp + rl];
-      }
-      if (b <= blk) q0 += prow[b * mp + rl];
-      b = 0;
-      for (; b + 1 < nseg; b += 2) {
-        c0 += pcol[b * mp + rl];
-        c1 += pcol[(b + 1) * mp + rl];
-      }
-      if (b < nseg) c0 += pcol[b * mp + rl];
-      q = (q0 + q1) + (c0 + c1);
     }
-    double e0 = 0.0, e1 = 0.0;
-    for (int c = 0; c < i; ++c) {
-      e0 = fma(V[r + c * ldv], ys[c], e0);
-      e1 = fma(W[r + c * ldv], ys[64 + c], e1);
+    part[wq][rlane] = acc;
+    __syncthreads();
+    if (wq == 0 && rl < len) {
+      double q = part[0][rlane];
+#pragma unroll
+      for (int w2 = 1; w2 < 8; ++w2) q += part[w2][rlane];
+      const int64_t r = j + 1 + rl;
+      double e0 = 0.0, e1 = 0.0;
+      for (int c = 0; c < i; ++c) {
+        e0 = fma(V[r + c * ldv], ys[c], e0);
+        e1 = fma(W[r + c * ldv], ys[64 + c], e1);
+      }
+      q = (q - e0) - e1;
+      q *= t;
+      p[r] = q;
+      dot = fma(q, v[r], dot);
     }
-    q = (q - e0) - e1;
-    q *= t;
-    p[r] = q;
-    dot = fma(q, v[r], dot);
+    __syncthreads();
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -771,6 +825,13 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
   unsigned* counter = reinterpret_cast<unsigned*>(dots + pgrid);
   cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   const int64_t jend = n - 2;                      // columns 0 .. n-3 carry a reflector
+  auto refresh_pairs = [&](int64_t t0) {
+    const int64_t tb = (n - t0 + 63) / 64;
+    if (pair_symv && tb > 0)
+      pair_upper_kernel<<<dim3((unsigned)tb, (unsigned)tb), 256, 0, ::ec::counted(s)>>>(n, A, lda,
+                                                                                        t0);
+  };
+  refresh_pairs(0);
   for (int64_t b = 0; b < jend; b += NB) {
     const int nb = (int)((jend - b) < NB ? (jend - b) : NB);
     for (int i = 0; i < nb; ++i) {
@@ -792,7 +853,7 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
                                                                            prow, pcol, mp);
       if (i > 0)
         latrd_dots_kernel<<<(unsigned)i, 256, 0, ::ec::counted(s)>>>(n, j, V, W, n, vj, y);
-      const int64_t pg = (len + 255) / 256 < pgrid ? (len + 255) / 256 : pgrid;
+      const int64_t pg = (len + 31) / 32 < pgrid ? (len + 31) / 32 : pgrid;
       if (pair_symv)
         p_latrd_kernel<true><<<(unsigned)pg, 256, 0, ::ec::counted(s)>>>(
             n, j, vj, tau, prow, pcol, mp, V, W, n, i, y, wj, dots, counter);
@@ -807,6 +868,7 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
                 1, st);
       gemm_auto(s, oz, N_, T_, m, m, nb, -1.0, W + t0, n, V + t0, n, 1.0, A + t0 + t0 * lda, lda,
                 1, st);
+      refresh_pairs(t0);
     }
   }
   tail_kernel<<<1, 1, 0, ::ec::counted(s)>>>(n, A, lda, d, e);

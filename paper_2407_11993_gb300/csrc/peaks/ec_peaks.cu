@@ -99,6 +99,47 @@ __global__ void __launch_bounds__(256) dmma_loop(int iters, double seed, double*
   if (s == 123.456) sink[blockIdx.x] = s;
 }
 
+// Both FP64 paths at once: even warps run the FMA loop, odd warps the mma.sync loop.
+// If the two share one unit the combined rate equals either alone; if they are separate
+// it approaches their sum.
+__global__ void __launch_bounds__(256) mixed64_loop(int iters, double seed, double* sink) {
+  const int w = threadIdx.x >> 5;
+  double s = 0.0;
+  if ((w & 1) == 0) {
+    double a[ACC];
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) a[j] = seed + threadIdx.x * 1e-9 + j;
+    const double x = 0.999999, y = 1e-7;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < ACC; ++j) a[j] = fma(a[j], x, y);
+    }
+#pragma unroll
+    for (int j = 0; j < ACC; ++j) s += a[j];
+  } else {
+    const double av = seed + (threadIdx.x & 31) * 1e-9, bv = 0.5 + (threadIdx.x & 7) * 1e-9;
+    double c[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      c[j][0] = 0.0;
+      c[j][1] = 0.0;
+    }
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+            : "+d"(c[j][0]), "+d"(c[j][1])
+            : "d"(av), "d"(bv));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1];
+  }
+  if (s == 123.456) sink[blockIdx.x] = s;
+}
+
 template <typename F>
 double best_ms(F launch, int reps) {
   cudaEvent_t a, b;
@@ -125,8 +166,9 @@ double best_ms(F launch, int reps) {
 
 // out[0] FP64 FMA TFLOP/s (the faster of a register-operand loop and a shared-memory
 // fed loop), out[1] FP64 mma.sync TFLOP/s, out[2] FP32 FMA TFLOP/s,
-// out[3] SM count, out[4] SM clock the device reports (MHz).  Returns 0 on success,
-// else the CUDA error code.
+// out[3] SM count, out[4] SM clock the device reports (MHz), out[5] FP64 TFLOP/s with
+// half the warps on each FP64 path at once.  Returns 0 on success, else the CUDA error
+// code.
 extern "C" int ec_peak_probe(int reps, double* out) {
   if (!out || reps < 1) return 1;
   int dev = 0, sms = 0, clk = 0;
@@ -147,6 +189,10 @@ extern "C" int ec_peak_probe(int reps, double* out) {
   const double tmma = best_ms([&] { dmma_loop<<<blocks, threads>>>(itmma, 1.0, sink); }, reps);
   const double t32 = best_ms(
       [&] { ffma_loop<<<blocks, threads>>>(it32, 1.0f, reinterpret_cast<float*>(sink)); }, reps);
+  // mixed: half the warps do fl64 / 2 of FMA work, half do flmma / 2 of mma work
+  const double tmix =
+      best_ms([&] { mixed64_loop<<<blocks, threads>>>(it64, 1.0, sink); }, reps);
+  const double flmix = 0.5 * fl64 + 0.5 * (2.0 * 8 * 8 * 4 * 4.0 * (double)it64 * blocks * (threads / 32));
   const cudaError_t e = cudaGetLastError();
   cudaFree(sink);
   if (e != cudaSuccess) return (int)e;
@@ -155,5 +201,6 @@ extern "C" int ec_peak_probe(int reps, double* out) {
   out[2] = fl32 / (t32 * 1e-3) / 1e12;
   out[3] = sms;
   out[4] = clk / 1000.0;
+  out[5] = flmix / (tmix * 1e-3) / 1e12;
   return 0;
 }

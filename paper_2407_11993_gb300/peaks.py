@@ -20,12 +20,13 @@ def measure(reps: int = 5) -> dict:
     lib = ctypes.CDLL(path)
     lib.ec_peak_probe.restype = ctypes.c_int
     lib.ec_peak_probe.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
-    out = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * 6)()
     rc = lib.ec_peak_probe(int(reps), out)
     if rc != 0:
         raise RuntimeError(f"peak probe failed with CUDA error {rc}")
     return {"fp64_fma_tflops": out[0], "fp64_mma_tflops": out[1], "fp32_fma_tflops": out[2],
-            "sms": int(out[3]), "sm_clock_mhz_reported": out[4], "reps": int(reps)}
+            "sms": int(out[3]), "sm_clock_mhz_reported": out[4],
+            "fp64_fma_and_mma_together_tflops": out[5], "reps": int(reps)}
 
 
 if __name__ == "__main__":
