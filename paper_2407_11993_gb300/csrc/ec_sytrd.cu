@@ -654,116 +654,6 @@ __global__ void __launch_bounds__(256) symv_strip_kernel(int64_t n, const double
   }
 }
 
-// The compensated symmetric product with the pair copy (the kernel behind
-// EC_GEMM_TENSOR_PAIRSYMV): the same tiles, partial sums and their layout as
-// symv_strip_kernel<true>, with 128 threads and a three-tile ring.  Thread (warp w, lane)
-// owns row (and column) 16 w + (lane & 15) of a tile and half h = lane >> 4 of its
-// columns (rows): the two halves of a row part meet by one shuffle, so a tile needs no
-// shared-memory reduction and two barriers.  Two CTAs per SM keep four tiles in flight.
-constexpr int PS_STAGES = 3;
-constexpr int PS_SMEM = PS_STAGES * 64 * 65 * (int)sizeof(double);
-
-__global__ void __launch_bounds__(128, 2) symv_pair_kernel(int64_t n, const double* A, int64_t lda,
-                                                           int64_t j, const double* v,
-                                                           double* prow, double* pcol,
-                                                           int64_t mp) {
-  extern __shared__ double sbuf[];                  // PS_STAGES tiles, [c][r] stride 65
-  __shared__ float2 vrp[PS_STAGES][64], vcp[64];
-  const int64_t s0 = j + 1, m = n - s0;
-  const int64_t nbk = (m + 63) / 64;
-  const int64_t J = blockIdx.y, k = blockIdx.x;
-  const int64_t I0 = J + k * SEG;
-  if (I0 >= nbk) return;
-  const int64_t I1 = (I0 + SEG < nbk) ? I0 + SEG : nbk;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int me = 16 * w + (lane & 15), h = lane >> 4;
-  const int64_t c0 = J * 64;
-  if (tid < 64) vcp[tid] = ff::split_fast((c0 + tid < m) ? v[s0 + c0 + tid] : 0.0);
-  auto load = [&](int64_t I, int b) {
-    double* As = sbuf + b * 64 * 65;
-    const int64_t r0 = I * 64;
-    if (I != J) {
-      // pairs of A[r, c] (r > c) kept at (c, r): read transposed, threads along c
-      for (int q = tid; q < 64 * 64; q += 128) {
-        const int cc = q & 63, rr = q >> 6;
-        const int64_t r = r0 + rr, c = c0 + cc;
-        const bool ok = r < m && c < m;
-        cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + c) + (s0 + r) * lda)
-                                        : (const void*)A, ok);
-      }
-    } else {
-      // the diagonal tile from the FP64 lower triangle (split after arrival)
-      for (int q = tid; q < 64 * 64; q += 128) {
-        const int rr = q & 63, cc = q >> 6;
-        const int64_t r = r0 + rr, c = c0 + cc;
-        const bool ok = r < m && c < m && rr >= cc;
-        cp_async8(&As[cc * 65 + rr], ok ? (const void*)(A + (s0 + r) + (s0 + c) * lda)
-                                        : (const void*)A, ok);
-      }
-    }
-    if (tid < 64) vrp[b][tid] = ff::split_fast((r0 + tid < m) ? v[s0 + r0 + tid] : 0.0);
-  };
-  float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;   // column part over the segment
-  load(I0, 0);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  if (I0 + 1 < I1) load(I0 + 1, 1);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int64_t I = I0; I < I1; ++I) {
-    const int b = (int)((I - I0) % PS_STAGES);
-    // the buffer of tile I + 2 last held tile I - 1, released by the barrier below
-    if (I + 2 < I1) load(I + 2, (b + 2) % PS_STAGES);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 2;" ::: "memory");
-    __syncthreads();
-    double* Aw = sbuf + b * 64 * 65;
-    if (I == J) {
-      float2* A2w = reinterpret_cast<float2*>(Aw);
-      for (int q = tid; q < 64 * 64; q += 128) {
-        const int idx = (q >> 6) * 65 + (q & 63);
-        A2w[idx] = ff::split_fast(Aw[idx]);
-      }
-      __syncthreads();
-    }
-    const float2* A2 = reinterpret_cast<const float2*>(Aw);
-    // row part: row me, columns 32 h .. 32 h + 31
-    float rh0 = 0.f, rl0 = 0.f, rh1 = 0.f, rl1 = 0.f;
-#pragma unroll
-    for (int cc = 0; cc < 32; cc += 2) {
-      const int ca = 32 * h + cc;
-      const float2 x0 = A2[ca * 65 + me], y0 = vcp[ca];
-      const float2 x1 = A2[(ca + 1) * 65 + me], y1 = vcp[ca + 1];
-      ff::madd(rh0, rl0, x0.x, x0.y, y0.x, y0.y);
-      ff::madd(rh1, rl1, x1.x, x1.y, y1.x, y1.y);
-    }
-    // column part: column me, rows 32 h .. 32 h + 31 (the diagonal tile's diagonal is
-    // counted once, in the row part)
-#pragma unroll
-    for (int rr = 0; rr < 32; rr += 2) {
-      const int ra = 32 * h + rr, rb = ra + 1;
-      const float2 xa = (I != J || ra > me) ? A2[me * 65 + ra] : make_float2(0.f, 0.f);
-      const float2 xb = (I != J || rb > me) ? A2[me * 65 + rb] : make_float2(0.f, 0.f);
-      ff::madd(ch0, cl0, xa.x, xa.y, vrp[b][ra].x, vrp[b][ra].y);
-      ff::madd(ch1, cl1, xb.x, xb.y, vrp[b][rb].x, vrp[b][rb].y);
-    }
-    ff::add(rh0, rl0, rh1, rl1);
-    const float oh = __shfl_xor_sync(0xffffffffu, rh0, 16);
-    const float ol = __shfl_xor_sync(0xffffffffu, rl0, 16);
-    if (h == 0) {
-      ff::add(rh0, rl0, oh, ol);
-      const int64_t r = I * 64 + me;
-      if (r < m) reinterpret_cast<float2*>(prow)[J * mp + r] = make_float2(rh0, rl0);
-    }
-    __syncthreads();                                 // buffer b may be refilled
-  }
-  ff::add(ch0, cl0, ch1, cl1);
-  const float oh = __shfl_xor_sync(0xffffffffu, ch0, 16);
-  const float ol = __shfl_xor_sync(0xffffffffu, cl0, 16);
-  if (h == 0) {
-    ff::add(ch0, cl0, oh, ol);
-    if (c0 + me < m) reinterpret_cast<float2*>(pcol)[k * mp + c0 + me] = make_float2(ch0, cl0);
-  }
-}
-
 // FP32 pair copies of the trailing lower triangle A[t0:, t0:] for the compensated
 // symmetric product: the pair of A[r, c] (r > c) is written to the free upper position
 // (c, r), through a shared-memory transpose so that both sides are coalesced.  One CTA
@@ -924,7 +814,6 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
                          STRIP_SMEM);
     cudaFuncSetAttribute(symv_strip_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          STRIP_SMEM);
-    cudaFuncSetAttribute(symv_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM);
   }
   const int sms = num_sms();
   const int pgrid = 2 * sms;
@@ -957,7 +846,7 @@ void sytrd_lower_blocked(cudaStream_t s, int64_t n, double* A, int64_t lda, doub
       const int64_t nbk = (len + 63) / 64;
       const dim3 sg((unsigned)((nbk + SEG - 1) / SEG), (unsigned)nbk);
       if (pair_symv)
-        symv_pair_kernel<<<sg, 128, PS_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj, prow,
+        symv_strip_kernel<true><<<sg, 256, STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj, prow,
                                                                           pcol, mp);
       else
         symv_strip_kernel<false><<<sg, 256, STRIP_SMEM, ::ec::counted(s)>>>(n, A, lda, j, vj,
