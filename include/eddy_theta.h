@@ -366,10 +366,10 @@ EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, 
  * counterpart):  C = alpha op(A) op(B) + beta C, op(X) = X (t = 0) or X^T (t = 1).
  * Device pointers, column-major FP64 with leading dimensions lda, ldb, ldc; op(A) is
  * M x K, op(B) is K x N.  `lower` holds flags: bit 0 (value 1, M = N) updates only the
- * lower triangle of C; bit 1 (value 2, with alpha = 1 and bit 0 clear) runs the path of
- * the modal snapshot products: op(A)'s slices are cut once into their own buffer and
- * the product reads them (for N <= 32 and beta = 0 as one stream-K launch over all row
- * tiles and K chunks).
+ * lower triangle of C; bit 1 (value 2, with alpha = 1, beta = 0 and bit 0 clear) runs the
+ * path of the modal snapshot products: op(A)'s slices are cut once into their own buffer
+ * (64 KB blocks in the kernel's shared-memory image) and the product reads them, one
+ * stream-K launch over all row tiles and K chunks per group of up to 32 columns.
  * Each row of op(A) and column of op(B) is scaled by a power of two and cut into eight
  * 8-bit integer slices held exactly in BF16; the slice products (tcgen05, FP32
  * accumulation kept exact per slice diagonal) are recombined in integer arithmetic.

@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
   double* coef = smem;                  // [2][TS][ncs]
   double* X = coef + 2 * TS * ncs;      // [MT][TS + 1]
   double* Gs = X + MT * (TS + 1);       // [P][MT]
+  double* gred = Gs + P * MT;           // [MT]: group sums of the probe product
   const int g = blockIdx.y, r = blockIdx.z;
   int64_t c0, c1;
   chunk_range(a, g, c0, c1);
@@ -384,15 +385,42 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
         a.Xsnap[nmode + ((k1 / a.stride - 1) * a.ntraj + r) * a.n0] = x;
     }
     __syncthreads();
-    for (int o = tid; o < P * nt; o += MT) {
-      const int p = o / nt, tt = o % nt;
-      const double* gp = Gs + p * MT;
-      double s0 = 0.0, s1 = 0.0;
-      for (int n = 0; n < MT; n += 2) {
-        s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
-        s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
+    // probe block product: P x nt outputs, each a sum over the CTA's MT modes; with few
+    // outputs the modes are cut into G groups so that every thread works, and the G
+    // group sums are added in group order
+    const int npo = P * nt;
+    int G = 1;
+    while (G * 2 * npo <= MT) G *= 2;
+    if (G == 1) {
+      for (int o = tid; o < npo; o += MT) {
+        const int p = o / nt, tt = o % nt;
+        const double* gp = Gs + p * MT;
+        double s0 = 0.0, s1 = 0.0;
+        for (int n = 0; n < MT; n += 2) {
+          s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
+          s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
+        }
+        a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
       }
-      a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
+    } else {
+      const int o = tid % npo, g = tid / npo, nb = MT / G;
+      if (g < G) {
+        const int p = o / nt, tt = o % nt;
+        const double* gp = Gs + p * MT;
+        double s0 = 0.0, s1 = 0.0;
+        for (int n = g * nb; n < (g + 1) * nb; n += 2) {
+          s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
+          s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
+        }
+        gred[g * npo + o] = s0 + s1;
+      }
+      __syncthreads();
+      if (tid < npo) {
+        const int p = tid / nt, tt = tid % nt;
+        double v = gred[tid];
+        for (int gg = 1; gg < G; ++gg) v += gred[gg * npo + tid];
+        a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = v;
+      }
     }
   }
   if (live && g == a.nchunk - 1) a.xout[(int64_t)r * a.n0 + nmode] = x;
@@ -447,14 +475,14 @@ ec_status modal_product(cudaStream_t s, ModalState* ms, int trans_u, int64_t N, 
     return skinny32_product(s, ms->u32, n0, trans_u, N, K, Y, lds, C, ldc, &ms->sk, st);
   if (ms->precision == EC_PREC_FP64) {
     if (ms->gemm != EC_GEMM_FP64 && !trans_u && n0 >= PRESPLIT_MIN) {
-      if (!ms->usplit.slices && !ms->usplit_tried) {
+      if (!ms->usplit.blocks && !ms->usplit_tried) {
         ms->usplit_tried = true;
         if (oz_presplit(s, N_, n0, n0, ms->U, n0, &ms->usplit) != EC_OK)
           oz_split_free(&ms->usplit);               // no room: the per-call paths below
       }
-      if (ms->usplit.slices) {
-        const ec_status rc = oz_gemm_presplit(s, ms->usplit, K, N_, N, Y, lds, 0.0, C, ldc,
-                                              &ms->oz, st);
+      if (ms->usplit.blocks) {
+        const ec_status rc = oz_gemm_presplit(s, ms->usplit, K, N_, N, Y, lds, C, ldc, &ms->oz,
+                                              st);
         if (rc != EC_ERR_OOM) return rc;
       }
     }
@@ -745,7 +773,7 @@ ec_status modal_run(cudaStream_t s, ModalState* ms, const StepArgs& sa,
   a.Xsnap = nsnap > 0 ? ms->Xsnap : nullptr; a.stride = nsnap > 0 ? sa.snap_stride : 0;
   const int ncs = a.ncoef > 0 ? a.ncoef : 1;
   const size_t smem1 = sizeof(double) * (size_t)(2 * TS * ncs);
-  const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + Pout * MT);
+  const size_t smem2 = sizeof(double) * (size_t)(2 * TS * ncs + MT * (TS + 1) + Pout * MT + MT);
   static std::atomic<unsigned long long> attr_set{0};
   if (first_on_device(attr_set))
     cudaFuncSetAttribute(modal_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -445,14 +445,21 @@ constexpr int NW_NMAX = 32;
 constexpr int NW_SET_COLS = NACC * NW_NMAX;             // 192 columns per accumulator set
 constexpr int NW_TMEM_COLS = 512;
 constexpr int NW_B_BYTES = OZ_S * NW_NMAX * TK * 2;     // 16 KB
-constexpr int NW_STAGE = A_BYTES + NW_B_BYTES;          // 80 KB
-constexpr int NW_SMEM = STAGES * NW_STAGE + 1024;
+constexpr int NW_MAX_STAGES = 3;
+// stages of A_BYTES + 8 nmma 64 bytes: three of 72 KB for nmma = 16, two of 80 KB for 32
+__host__ __device__ constexpr int nw_stage_bytes(int nmma) { return A_BYTES + OZ_S * nmma * TK * 2; }
+__host__ __device__ constexpr int nw_stages(int nmma) { return nmma <= 16 ? 3 : 2; }
+constexpr int NW_SMEM = 3 * nw_stage_bytes(16) + 1024;
+static_assert(NW_SMEM >= 2 * nw_stage_bytes(32) + 1024, "ring sized for the widest stage");
 static_assert(2 * NW_SET_COLS <= NW_TMEM_COLS, "two accumulator sets exceed tensor memory");
 
 struct NarrowArgs {
   int M, N, nmma;          // rows, columns (<= nmma), MMA width (16 or 32)
   int K, nkc;              // K and its 192-long chunks
   int64_t items, per_cta;  // (tile, chunk) items and the items of one CTA's range
+  int stages, stage_bytes; // ring depth and stride (nw_stages / nw_stage_bytes of nmma)
+  const uint8_t* Ablk;     // A's kept slices, 64 KB per (row tile, K block)
+  int64_t nkb;             // K blocks of A
   double* C;
   int64_t ldc;
   const int* ea;
@@ -460,10 +467,9 @@ struct NarrowArgs {
 };
 
 __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
-    const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-    const NarrowArgs a, DevStatus* st) {
+    const __grid_constant__ CUtensorMap mapB, const NarrowArgs a, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2],
+  __shared__ __align__(8) uint64_t full_bar[NW_MAX_STAGES], empty_bar[NW_MAX_STAGES], acc_full[2],
       acc_empty[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued, consumed, skip;
@@ -483,7 +489,7 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    for (int q = 0; q < STAGES; ++q) {
+    for (int q = 0; q < a.stages; ++q) {
       mbar_init(&full_bar[q], 1);
       mbar_init(&empty_bar[q], 1);
     }
@@ -512,16 +518,19 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
         const int klen = (a.K - kbeg) < OZ_KCHUNK ? (a.K - kbeg) : OZ_KCHUNK;
         const int nkb = (klen + TK - 1) / TK;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int q = (int)(it % STAGES);
-          const uint32_t use = it / STAGES;
-          if (it >= STAGES && !mbar_wait(&empty_bar[q], (use - 1) & 1, st, 51)) {
+          const int q = (int)(it % (uint32_t)a.stages);
+          const uint32_t use = it / (uint32_t)a.stages;
+          if (it >= (uint32_t)a.stages && !mbar_wait(&empty_bar[q], (use - 1) & 1, st, 51)) {
             *(volatile int*)&abort_flag = 1;
             break;
           }
-          uint8_t* sa = smem + q * NW_STAGE;
+          uint8_t* sa = smem + q * a.stage_bytes;
           uint8_t* sb = sa + A_BYTES;
           mbar_expect_tx(&full_bar[q], A_BYTES + b_bytes);
-          tma_load_3d(sa, &mapA, &full_bar[q], kbeg + kb * TK, tile * TM, 0);
+          // A: one contiguous 64 KB block, already in the swizzled shared-memory image
+          dev::bulk_g2s(sa,
+                        a.Ablk + ((int64_t)tile * a.nkb + kbeg / TK + kb) * (int64_t)A_BYTES,
+                        A_BYTES, &full_bar[q]);
           tma_load_3d(sb, &mapB, &full_bar[q], kbeg + kb * TK, 0, 0);
           *(volatile int*)&issued = (int)(it + 1);
         }
@@ -548,15 +557,15 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t tset = tmem + (uint32_t)(set * NW_SET_COLS);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int q = (int)(it % STAGES);
-          if (!mbar_wait(&full_bar[q], (it / STAGES) & 1, st, 52)) {
+          const int q = (int)(it % (uint32_t)a.stages);
+          if (!mbar_wait(&full_bar[q], (it / (uint32_t)a.stages) & 1, st, 52)) {
             *(volatile int*)&abort_flag = 1;
             ok = false;
             break;
           }
           *(volatile int*)&consumed = (int)(it + 1);
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = smem_u32(smem + q * NW_STAGE);
+          const uint32_t sa = smem_u32(smem + q * a.stage_bytes);
           const uint32_t sb = sa + A_BYTES;
 #pragma unroll
           for (int d = 0; d <= OZ_DMAX; ++d) {
@@ -662,7 +671,7 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
     if (!mbar_wait(&done_bar, 0, st, 53)) abort_flag = 1;
     if (abort_flag)
       for (int it = consumed; it < issued; ++it)
-        mbar_wait(&full_bar[it % STAGES], (it / STAGES) & 1, st, 54);
+        mbar_wait(&full_bar[it % a.stages], (it / a.stages) & 1, st, 54);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -813,6 +822,48 @@ ec_status grow_ws(OzWork* w, int64_t slice_elems, int64_t rows) {
 
 // Split rows [r0, r0 + R) of the logical operand into slices at `out` (ld ldk) with
 // exponents at `exps`; maxb is scratch of R entries.
+// Kept slices in the narrow kernel's shared-memory image: CTA (row tile t, K block kb),
+// thread r = row of the tile; block (t, kb) holds slice s at s * A_SLICE, row r at 64 r,
+// and the 16-byte chunk c (K values 8c .. 8c + 7) at chunk position c ^ ((r >> 1) & 3),
+// the 64-byte swizzle the tensor-core descriptors read.  Rows >= R and K >= K are zero.
+__global__ void __launch_bounds__(TM) oz_split_blocked_kernel(int64_t R, int64_t K,
+                                                              const double* src, int64_t rs,
+                                                              int64_t ks,
+                                                              const unsigned long long* maxb,
+                                                              uint8_t* out, int64_t nkb,
+                                                              int* exps) {
+  const int64_t t = blockIdx.x, kb = blockIdx.y;
+  const int r = threadIdx.x;
+  const int64_t row = t * TM + r;
+  const bool live = row < R;
+  const int e = live ? oz::row_exponent(maxb[row]) : 0;
+  if (live && kb == 0) exps[row] = e;
+  uint8_t* blk = out + (t * nkb + kb) * (int64_t)A_BYTES + (int64_t)r * 64;
+  const int swz = (r >> 1) & 3;
+  for (int c = 0; c < 4; ++c) {
+    int d[8][OZ_S];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t k = kb * TK + 8 * c + j;
+      const double v = (live && k < K) ? src[row * rs + k * ks] : 0.0;
+      oz::digits8(oz::f64_to_fixed64((uint64_t)__double_as_longlong(v), e), d[j]);
+    }
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      const float sc = __int_as_float((127 - 8 * s) << 23);   // 2^-8s
+      uint32_t w4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 pr = __floats2bfloat162_rn((float)d[2 * q][s] * sc,
+                                                        (float)d[2 * q + 1][s] * sc);
+        w4[q] = *reinterpret_cast<const uint32_t*>(&pr);
+      }
+      *reinterpret_cast<uint4*>(blk + s * A_SLICE + ((c ^ swz) * 16)) =
+          make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+  }
+}
+
 void split(cudaStream_t s, int64_t R, int64_t K, const double* src, int64_t rs, int64_t ks,
            unsigned long long* maxb, __nv_bfloat16* out, int64_t ldk, int* exps) {
   cudaMemsetAsync(maxb, 0, sizeof(unsigned long long) * (size_t)R, s);
@@ -904,9 +955,10 @@ ec_status oz_presplit(cudaStream_t s, Op ta, int64_t R, int64_t K, const double*
   oz_split_free(out);
   if (R <= 0 || K <= 0) return EC_ERR_ARG;
   if (R > (1ll << 30)) return EC_ERR_UNSUPPORTED;
-  const int64_t ldk = (K + 7) / 8 * 8;
+  const int64_t tiles = (R + TM - 1) / TM, nkb = (K + TK - 1) / TK;
+  if (nkb > 65535) return EC_ERR_UNSUPPORTED;
   unsigned long long* maxb = nullptr;
-  if (device_alloc((void**)&out->slices, sizeof(__nv_bfloat16) * (size_t)OZ_S * R * ldk) !=
+  if (device_alloc((void**)&out->blocks, (size_t)A_BYTES * (size_t)tiles * (size_t)nkb) !=
           cudaSuccess ||
       device_alloc((void**)&out->exps, sizeof(int) * (size_t)R) != cudaSuccess ||
       device_alloc((void**)&maxb, sizeof(unsigned long long) * (size_t)R) != cudaSuccess) {
@@ -916,82 +968,77 @@ ec_status oz_presplit(cudaStream_t s, Op ta, int64_t R, int64_t K, const double*
     return EC_ERR_OOM;
   }
   const int64_t ars = ta == N_ ? 1 : lda, aks = ta == N_ ? lda : 1;
-  split(s, R, K, A, ars, aks, maxb, out->slices, ldk, out->exps);
+  cudaMemsetAsync(maxb, 0, sizeof(unsigned long long) * (size_t)R, s);
+  oz_absmax_kernel<<<dim3((unsigned)((R + ST - 1) / ST), (unsigned)((K + ST - 1) / ST)), 256, 0,
+                     ::ec::counted(s)>>>(R, K, A, ars, aks, maxb);
+  oz_split_blocked_kernel<<<dim3((unsigned)tiles, (unsigned)nkb), TM, 0, ::ec::counted(s)>>>(
+      R, K, A, ars, aks, maxb, out->blocks, nkb, out->exps);
   cudaStreamSynchronize(s);
   cudaFree(maxb);
   out->R = R;
   out->K = K;
-  out->ldk = ldk;
+  out->nkb = nkb;
   return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
 }
 
 void oz_split_free(OzSplit* a) {
-  if (a->slices) cudaFree(a->slices);
+  if (a->blocks) cudaFree(a->blocks);
   if (a->exps) cudaFree(a->exps);
   *a = OzSplit{};
 }
 
 ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb, int64_t N,
-                           const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                           OzWork* w, DevStatus* st) {
+                           const double* B, int64_t ldb, double* C, int64_t ldc, OzWork* w,
+                           DevStatus* st) {
   if (N <= 0 || a.R <= 0) return EC_OK;
-  if (!w || !a.slices || kuse <= 0 || kuse > a.K) return EC_ERR_ARG;
+  if (!w || !a.blocks || kuse <= 0 || kuse > a.K) return EC_ERR_ARG;
   if (N > (1ll << 30)) return EC_ERR_UNSUPPORTED;
   if (!tensor_map_encode_fn()) return EC_ERR_UNSUPPORTED;
-  set_kernel_attributes();
-  const int64_t ldk = a.ldk;                 // B's slices share A's K layout
+  static std::atomic<unsigned long long> nw_attr{0};
+  if (first_on_device(nw_attr))
+    cudaFuncSetAttribute(oz_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
+  const int64_t ldk = a.nkb * TK;            // B's slices padded like A's K blocks
   const int64_t per_row = (int64_t)OZ_S * ldk;
-  int64_t pn = w->cap_elems / per_row / TN * TN;
-  if (pn < TN) pn = TN;
-  if (pn > N) pn = N;
   {
-    const ec_status g = grow_ws(w, per_row * pn, pn);
+    const ec_status g = grow_ws(w, per_row * NW_NMAX, NW_NMAX);
     if (g != EC_OK) return g;
   }
-  CUtensorMap ma;
-  // the map covers kuse columns of the slices (ldk stays a.ldk): reads past kuse are zero
-  if (!make_slice_map_ld(&ma, a.slices, a.R, kuse, ldk, a.R, TM)) return EC_ERR_CUDA;
   const int64_t brs = tb == N_ ? ldb : 1, bks = tb == N_ ? 1 : ldb;
-  if (N <= NW_NMAX && beta == 0.0) {
-    // few columns: one stream-K launch over all (row tile, K chunk) items
-    static std::atomic<unsigned long long> nw_attr{0};
-    if (first_on_device(nw_attr))
-      cudaFuncSetAttribute(oz_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
-    split(s, N, kuse, B, brs, bks, w->maxb, w->slices, ldk, w->exps);
-    const int nm = nmma_for(N);
+  const int64_t tiles = (a.R + TM - 1) / TM;
+  const int nkc = (int)((kuse + OZ_KCHUNK - 1) / OZ_KCHUNK);
+  // ranges of at least one tile's chunks, so a tile is cut between two ranges at most
+  const int64_t items = tiles * nkc;
+  int64_t grid = std::min<int64_t>((int64_t)num_sms(), items / nkc);
+  if (grid < 1) grid = 1;
+  const int64_t per_cta = (items + grid - 1) / grid;
+  grid = (items + per_cta - 1) / per_cta;
+  if (cudaMemset2DAsync(C, sizeof(double) * (size_t)ldc, 0, sizeof(double) * (size_t)a.R,
+                        (size_t)N, s) != cudaSuccess)
+    return EC_ERR_CUDA;
+  for (int64_t j0 = 0; j0 < N; j0 += NW_NMAX) {
+    const int64_t nj = std::min<int64_t>(NW_NMAX, N - j0);
+    split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
+    const int nm = nmma_for(nj);
     CUtensorMap mb;
-    if (!make_slice_map(&mb, w->slices, N, kuse, ldk, nm)) return EC_ERR_CUDA;
+    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, nm)) return EC_ERR_CUDA;
     NarrowArgs na{};
     na.M = (int)a.R;
-    na.N = (int)N;
+    na.N = (int)nj;
     na.nmma = nm;
     na.K = (int)kuse;
-    na.nkc = (int)((kuse + OZ_KCHUNK - 1) / OZ_KCHUNK);
-    const int64_t tiles = (a.R + TM - 1) / TM;
-    na.items = tiles * na.nkc;
-    // ranges of at least one tile's chunks, so a tile is cut between two ranges at most
-    int64_t grid = std::min<int64_t>((int64_t)num_sms(), na.items / na.nkc);
-    if (grid < 1) grid = 1;
-    na.per_cta = (na.items + grid - 1) / grid;
-    grid = (na.items + na.per_cta - 1) / na.per_cta;
-    na.C = C;
+    na.nkc = nkc;
+    na.stages = nw_stages(nm);
+    na.stage_bytes = nw_stage_bytes(nm);
+    na.items = items;
+    na.per_cta = per_cta;
+    na.C = C + j0 * ldc;
     na.ldc = ldc;
     na.ea = a.exps;
     na.eb = w->exps;
-    if (cudaMemset2DAsync(C, sizeof(double) * (size_t)ldc, 0, sizeof(double) * (size_t)a.R,
-                          (size_t)N, s) != cudaSuccess)
-      return EC_ERR_CUDA;
-    oz_narrow_kernel<<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(ma, mb, na, st);
-    return cudaGetLastError() == cudaSuccess ? EC_OK : EC_ERR_CUDA;
-  }
-  for (int64_t j0 = 0; j0 < N; j0 += pn) {
-    const int64_t nj = std::min(pn, N - j0);
-    split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
-    CUtensorMap mb;
-    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, nmma_for(nj))) return EC_ERR_CUDA;
-    const ec_status rc = launch_panel(s, ma, mb, a.R, nj, kuse, 1.0, beta, C + j0 * ldc, ldc,
-                                      a.exps, w->exps, 0, st);
-    if (rc != EC_OK) return rc;
+    na.Ablk = a.blocks;
+    na.nkb = a.nkb;
+    oz_narrow_kernel<<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(mb, na, st);
+    if (cudaGetLastError() != cudaSuccess) return EC_ERR_CUDA;
   }
   return EC_OK;
 }
@@ -1074,7 +1121,7 @@ extern "C" ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, 
   if ((lower & ~3) != 0) return EC_ERR_ARG;
   const bool presplit = (lower & 2) != 0 && K > 0;
   lower &= 1;
-  if (presplit && (lower || alpha != 1.0)) return EC_ERR_ARG;
+  if (presplit && (lower || alpha != 1.0 || beta != 0.0)) return EC_ERR_ARG;
   if (lower && M != N) return EC_ERR_SHAPE;
   cudaStream_t s = (cudaStream_t)stream;
   DevStatus* st = nullptr;
@@ -1089,7 +1136,7 @@ extern "C" ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, 
     OzSplit sa;
     rc = oz_presplit(s, ta ? T_ : N_, M, K, A, lda, &sa);
     if (rc == EC_OK)
-      rc = oz_gemm_presplit(s, sa, K, tb ? T_ : N_, N, B, ldb, beta, C, ldc, &w, st);
+      rc = oz_gemm_presplit(s, sa, K, tb ? T_ : N_, N, B, ldb, C, ldc, &w, st);
     cudaStreamSynchronize(s);
     oz_split_free(&sa);
   } else {

@@ -39,19 +39,23 @@ ec_status oz_gemm(cudaStream_t s, Op ta, Op tb, int64_t M, int64_t N, int64_t K,
 // The slices of a fixed left operand op(A) (R x K, rows scaled by their own powers of
 // two), cut once and reused by every later product with it: a product with few right
 // columns then reads 16 bytes per entry of A instead of splitting A again (24 bytes of
-// traffic per entry on top).  Memory: 16 R ldk bytes.
+// traffic per entry on top).  Layout: blocks of 128 rows x 32 K (64 KB, all eight slices)
+// stored as the tensor-core kernel's shared-memory image (64-byte swizzle applied), so
+// that each block arrives with one contiguous bulk copy.  Memory: 16 x (R rounded up to
+// 128) x (K rounded up to 32) bytes.
 struct OzSplit {
-  __nv_bfloat16* slices = nullptr;      // [8][R][ldk]
+  uint8_t* blocks = nullptr;            // [row tile][K block][slice][128 rows][64 B]
   int* exps = nullptr;                  // R
-  int64_t R = 0, K = 0, ldk = 0;
+  int64_t R = 0, K = 0, nkb = 0;        // nkb: K blocks of 32
 };
 // EC_ERR_OOM when the slices do not fit (out stays empty).
 ec_status oz_presplit(cudaStream_t s, Op ta, int64_t R, int64_t K, const double* A, int64_t lda,
                       OzSplit* out);
 void oz_split_free(OzSplit* a);
-// C = op(A)[:, :kuse] op(B) + beta C with op(A) from `a` (kuse <= a.K), op(B) kuse x N.
+// C = op(A)[:, :kuse] op(B) with op(A) from `a` (kuse <= a.K), op(B) kuse x N; C is
+// overwritten (beta = 0).  Column groups of up to 32, one stream-K launch each.
 ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb, int64_t N,
-                           const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                           OzWork* w, DevStatus* st);
+                           const double* B, int64_t ldb, double* C, int64_t ldc, OzWork* w,
+                           DevStatus* st);
 
 }  // namespace ec

@@ -114,11 +114,12 @@ def test_zero_rows_and_columns(eddy):
 
 
 @pytest.mark.parametrize("M,N,K", [(20000, 4, 1000), (19500, 30, 700), (4100, 1, 4099),
-                                   (300, 32, 385), (129, 17, 193), (33000, 8, 250)])
+                                   (300, 32, 385), (129, 17, 193), (33000, 8, 250),
+                                   (700, 40, 300), (20000, 70, 33)])
 def test_kept_slices_stream_k(eddy, M, N, K):
-    """The modal snapshot path (A's slices kept, one stream-K launch for N <= 32): with
-    more row tiles than SMs some tiles are cut between two CTAs and added to the zeroed C
-    by both (two addends: order-independent).  Integer inputs are exact; the result is the
+    """The modal snapshot path (A's slices kept as swizzled 64 KB blocks, one stream-K
+    launch per group of up to 32 columns): with more row tiles than SMs some tiles are cut
+    between two CTAs and added to the zeroed C by both (two addends: order-independent).  Integer inputs are exact; the result is the
     same as the per-call path bit for bit on random inputs only up to FP64 rounding, so
     random inputs are checked against the FP64 bound."""
     rng = np.random.default_rng(M + N + K)
