@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
           *(volatile int*)&consumed = (int)(it + 1);
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-          const uint32_t sb = sa + A_BYTES;
+          const uint64_t dA0 = smem_desc(sa), dB0 = smem_desc(sa + A_BYTES);
 #pragma unroll
           for (int d = 0; d <= OZ_DMAX; ++d) {
             const int acc = d < OZ_EXACT ? d : OZ_EXACT;
@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
             for (int si = 0; si <= d; ++si) {
               const int ti = d - si;
               if (si >= OZ_S || ti >= OZ_S) continue;
-              const uint64_t da = smem_desc(sa + si * A_SLICE);
-              const uint64_t db = smem_desc(sb + ti * b_slice);
+              const uint64_t da = dA0 + (uint64_t)((si * A_SLICE) >> 4);
+              const uint64_t db = dB0 + (uint64_t)((ti * b_slice) >> 4);
 #pragma unroll
               for (int kk = 0; kk < TK / 16; ++kk) {
                 // the first product into each accumulator overwrites it
@@ -446,6 +446,7 @@ constexpr int NW_SET_COLS = NACC * NW_NMAX;             // 192 columns per accum
 constexpr int NW_TMEM_COLS = 512;
 constexpr int NW_B_BYTES = OZ_S * NW_NMAX * TK * 2;     // 16 KB
 constexpr int NW_MAX_STAGES = 3;
+constexpr int NW_COPIES = 8;                            // bulk copies per A stage (8 KB each)
 // stages of A_BYTES + 8 nmma 64 bytes: three of 72 KB for nmma = 16, two of 80 KB for 32
 __host__ __device__ constexpr int nw_stage_bytes(int nmma) { return A_BYTES + OZ_S * nmma * TK * 2; }
 __host__ __device__ constexpr int nw_stages(int nmma) { return nmma <= 16 ? 3 : 2; }
@@ -466,6 +467,7 @@ struct NarrowArgs {
   const int* eb;
 };
 
+template <int NMMA>
 __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
     const __grid_constant__ CUtensorMap mapB, const NarrowArgs a, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
@@ -510,36 +512,52 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
   const uint32_t b_bytes = (uint32_t)(OZ_S * a.nmma * TK * 2);
 
   if (warp == 0) {
-    if (lane == 0) {
-      uint32_t it = 0;
-      for (int64_t i = i0; i < i1 && !*(volatile int*)&abort_flag; ++i) {
-        const int tile = (int)(i / a.nkc), kc = (int)(i % a.nkc);
-        const int kbeg = kc * OZ_KCHUNK;
-        const int klen = (a.K - kbeg) < OZ_KCHUNK ? (a.K - kbeg) : OZ_KCHUNK;
-        const int nkb = (klen + TK - 1) / TK;
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int q = (int)(it % (uint32_t)a.stages);
-          const uint32_t use = it / (uint32_t)a.stages;
-          if (it >= (uint32_t)a.stages && !mbar_wait(&empty_bar[q], (use - 1) & 1, st, 51)) {
+    // producer warp: lane 0 waits for a free stage and posts the byte count; the A block
+    // then goes as NW_COPIES bulk copies issued by as many lanes (one copy per lane keeps
+    // several requests in flight), B as one tensor copy
+    uint32_t it = 0;
+    bool stop = false;
+    for (int64_t i = i0; i < i1 && !stop; ++i) {
+      const int tile = (int)(i / a.nkc), kc = (int)(i % a.nkc);
+      const int kbeg = kc * OZ_KCHUNK;
+      const int klen = (a.K - kbeg) < OZ_KCHUNK ? (a.K - kbeg) : OZ_KCHUNK;
+      const int nkb = (klen + TK - 1) / TK;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int q = (int)(it % (uint32_t)a.stages);
+        const uint32_t use = it / (uint32_t)a.stages;
+        int ok = 1;
+        if (lane == 0) {
+          if (*(volatile int*)&abort_flag ||
+              (it >= (uint32_t)a.stages && !mbar_wait(&empty_bar[q], (use - 1) & 1, st, 51))) {
             *(volatile int*)&abort_flag = 1;
-            break;
+            ok = 0;
+          } else {
+            mbar_expect_tx(&full_bar[q], A_BYTES + b_bytes);
           }
-          uint8_t* sa = smem + q * a.stage_bytes;
-          uint8_t* sb = sa + A_BYTES;
-          mbar_expect_tx(&full_bar[q], A_BYTES + b_bytes);
-          // A: one contiguous 64 KB block, already in the swizzled shared-memory image
-          dev::bulk_g2s(sa,
-                        a.Ablk + ((int64_t)tile * a.nkb + kbeg / TK + kb) * (int64_t)A_BYTES,
-                        A_BYTES, &full_bar[q]);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          stop = true;
+          break;
+        }
+        uint8_t* sa = smem + q * a.stage_bytes;
+        uint8_t* sb = sa + A_BYTES;
+        // A: one 64 KB block, already in the swizzled shared-memory image
+        const uint8_t* src = a.Ablk + ((int64_t)tile * a.nkb + kbeg / TK + kb) * (int64_t)A_BYTES;
+        if (lane < NW_COPIES)
+          dev::bulk_g2s(sa + lane * (A_BYTES / NW_COPIES), src + lane * (A_BYTES / NW_COPIES),
+                        A_BYTES / NW_COPIES, &full_bar[q]);
+        if (lane == 0) {
           tma_load_3d(sb, &mapB, &full_bar[q], kbeg + kb * TK, 0, 0);
           *(volatile int*)&issued = (int)(it + 1);
         }
+        __syncwarp();
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_for(a.nmma);
-      const uint32_t b_slice = (uint32_t)(a.nmma * TK * 2);
+      constexpr uint32_t idesc = idesc_for(NMMA);
+      constexpr uint32_t b_slice = (uint32_t)(NMMA * TK * 2);
       uint32_t it = 0;
       bool ok = true;
       for (int64_t i = i0; ok && i < i1 && !*(volatile int*)&abort_flag; ++i) {
@@ -566,21 +584,25 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
           *(volatile int*)&consumed = (int)(it + 1);
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(smem + q * a.stage_bytes);
-          const uint32_t sb = sa + A_BYTES;
+          // descriptors of the stage, offsets in 16-byte units added per slice and K step
+          // (the address field cannot overflow below 256 KB of shared memory)
+          const uint64_t dA0 = smem_desc(sa), dB0 = smem_desc(sa + A_BYTES);
+          const uint32_t kb0 = kb == 0 ? 0u : 1u;
 #pragma unroll
           for (int d = 0; d <= OZ_DMAX; ++d) {
             const int acc = d < OZ_EXACT ? d : OZ_EXACT;
-            const uint32_t tacc = tset + (uint32_t)(acc * a.nmma);
+            const uint32_t tacc = tset + (uint32_t)(acc * NMMA);
 #pragma unroll
             for (int si = 0; si <= d; ++si) {
               const int ti = d - si;
               if (si >= OZ_S || ti >= OZ_S) continue;
-              const uint64_t da = smem_desc(sa + si * A_SLICE);
-              const uint64_t db = smem_desc(sb + ti * b_slice);
+              const uint64_t da = dA0 + (uint64_t)((si * A_SLICE) >> 4);
+              const uint64_t db = dB0 + (uint64_t)((ti * b_slice) >> 4);
 #pragma unroll
               for (int kk = 0; kk < TK / 16; ++kk) {
-                const bool first = kb == 0 && kk == 0 && si == 0 && d <= OZ_EXACT;
-                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, first ? 0u : 1u);
+                // the first product into each accumulator (first K block) overwrites it
+                const uint32_t accum = (kk == 0 && si == 0 && d <= OZ_EXACT) ? kb0 : 1u;
+                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, accum);
               }
             }
           }
@@ -595,9 +617,9 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
     // the four lane quarters (rows of the tile)
     const int quarter = warp & 3;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    double acc[NW_NMAX];
+    double acc[NMMA];
 #pragma unroll
-    for (int j = 0; j < NW_NMAX; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NMMA; ++j) acc[j] = 0.0;
     for (int64_t i = i0; i < i1; ++i) {
       const int64_t li = i - i0;
       const int set = (int)(li & 1);
@@ -612,12 +634,11 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
       const bool row_ok = row < a.M;
       const int erow = row_ok ? a.ea[row] - 56 : 0;
 #pragma unroll
-      for (int g = 0; g < NW_NMAX / 16; ++g) {
-        if (g * 16 >= a.nmma) break;
+      for (int g = 0; g < NMMA / 16; ++g) {
         uint32_t r[NACC][16];
 #pragma unroll
         for (int q = 0; q < NACC; ++q)
-          tmem_ld16(lane_base + (uint32_t)(set * NW_SET_COLS + q * a.nmma + g * 16), r[q]);
+          tmem_ld16(lane_base + (uint32_t)(set * NW_SET_COLS + q * NMMA + g * 16), r[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -653,7 +674,7 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
         const bool whole = tile_first >= i0 && kc == a.nkc - 1;
         if (row_ok) {
 #pragma unroll
-          for (int j = 0; j < NW_NMAX; ++j) {
+          for (int j = 0; j < NMMA; ++j) {
             if (j >= a.N) break;
             double* cp = a.C + (int64_t)row + (int64_t)j * a.ldc;
             if (whole) *cp = acc[j];
@@ -661,7 +682,7 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
           }
         }
 #pragma unroll
-        for (int j = 0; j < NW_NMAX; ++j) acc[j] = 0.0;
+        for (int j = 0; j < NMMA; ++j) acc[j] = 0.0;
       }
     }
   }
@@ -996,7 +1017,10 @@ ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb
   if (!tensor_map_encode_fn()) return EC_ERR_UNSUPPORTED;
   static std::atomic<unsigned long long> nw_attr{0};
   if (first_on_device(nw_attr))
-    cudaFuncSetAttribute(oz_narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
+  {
+    cudaFuncSetAttribute(oz_narrow_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
+    cudaFuncSetAttribute(oz_narrow_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, NW_SMEM);
+  }
   const int64_t ldk = a.nkb * TK;            // B's slices padded like A's K blocks
   const int64_t per_row = (int64_t)OZ_S * ldk;
   {
@@ -1037,7 +1061,10 @@ ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb
     na.eb = w->exps;
     na.Ablk = a.blocks;
     na.nkb = a.nkb;
-    oz_narrow_kernel<<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(mb, na, st);
+    if (nm == 16)
+      oz_narrow_kernel<16><<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(mb, na, st);
+    else
+      oz_narrow_kernel<32><<<(unsigned)grid, NW_THREADS, NW_SMEM, ::ec::counted(s)>>>(mb, na, st);
     if (cudaGetLastError() != cudaSuccess) return EC_ERR_CUDA;
   }
   return EC_OK;
