@@ -453,28 +453,6 @@ __host__ __device__ constexpr int nw_stages(int nmma) { return nmma <= 16 ? 3 : 
 constexpr int NW_SMEM = 3 * nw_stage_bytes(16) + 1024;
 static_assert(NW_SMEM >= 2 * nw_stage_bytes(32) + 1024, "ring sized for the widest stage");
 static_assert(2 * NW_SET_COLS <= NW_TMEM_COLS, "two accumulator sets exceed tensor memory");
-// A operand in tensor memory: the eight slices of one 16-wide K step, 8 columns each,
-// two buffers (K steps alternate) after the accumulator sets
-constexpr int NW_ACOL = 2 * NW_SET_COLS;                 // 384
-static_assert(NW_ACOL + 2 * OZ_S * 8 <= NW_TMEM_COLS, "A buffers exceed tensor memory");
-
-// D (tensor memory) += A (tensor memory) B (shared memory), kind::f16.
-__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
-                                            uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-// 128 rows x 256 bits (16 BF16 of each row) from shared memory (matrix descriptor) into
-// tensor memory: row i to lane i, 8 columns.
-__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
-  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc)
-               : "memory");
-}
 
 struct NarrowArgs {
   int M, N, nmma;          // rows, columns (<= nmma), MMA width (16 or 32)
@@ -610,28 +588,21 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
           // (the address field cannot overflow below 256 KB of shared memory)
           const uint64_t dA0 = smem_desc(sa), dB0 = smem_desc(sa + A_BYTES);
           const uint32_t kb0 = kb == 0 ? 0u : 1u;
-          // each slice of A goes to tensor memory once per 16-wide K step and serves all
-          // the slice pairs it belongs to (read from shared memory once instead of 4.5
-          // times on average); tcgen05 copies and MMAs of one thread run in issue order
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk) {
-            const uint32_t abuf = tmem + (uint32_t)(NW_ACOL + kk * OZ_S * 8);
+          for (int d = 0; d <= OZ_DMAX; ++d) {
+            const int acc = d < OZ_EXACT ? d : OZ_EXACT;
+            const uint32_t tacc = tset + (uint32_t)(acc * NMMA);
 #pragma unroll
-            for (int si = 0; si < OZ_S; ++si)
-              tmem_cp_128x256b(abuf + (uint32_t)(8 * si),
-                               dA0 + (uint64_t)((si * A_SLICE) >> 4) + 2 * kk);
+            for (int si = 0; si <= d; ++si) {
+              const int ti = d - si;
+              if (si >= OZ_S || ti >= OZ_S) continue;
+              const uint64_t da = dA0 + (uint64_t)((si * A_SLICE) >> 4);
+              const uint64_t db = dB0 + (uint64_t)((ti * b_slice) >> 4);
 #pragma unroll
-            for (int d = 0; d <= OZ_DMAX; ++d) {
-              const int acc = d < OZ_EXACT ? d : OZ_EXACT;
-              const uint32_t tacc = tset + (uint32_t)(acc * NMMA);
-#pragma unroll
-              for (int si = 0; si <= d; ++si) {
-                const int ti = d - si;
-                if (si >= OZ_S || ti >= OZ_S) continue;
-                const uint64_t db = dB0 + (uint64_t)((ti * b_slice) >> 4);
+              for (int kk = 0; kk < TK / 16; ++kk) {
                 // the first product into each accumulator (first K block) overwrites it
                 const uint32_t accum = (kk == 0 && si == 0 && d <= OZ_EXACT) ? kb0 : 1u;
-                mma_bf16_ts(tacc, abuf + (uint32_t)(8 * si), db + 2 * kk, idesc, accum);
+                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, accum);
               }
             }
           }
