@@ -386,13 +386,15 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
     }
     __syncthreads();
     // probe block product: P x nt outputs, each a sum over the CTA's MT modes; with few
-    // outputs the modes are cut into G groups so that every thread works, and the G
-    // group sums are added in group order
-    const int npo = P * nt;
+    // outputs the modes are cut into G groups so that every thread works, and the G group
+    // sums are added in group order.  G depends on P only (not on nt), so every step's
+    // sum has the same shape wherever the step falls in a block: runs split at any step
+    // and resumed give the same bits.
+    const int npf = P * TS;
     int G = 1;
-    while (G * 2 * npo <= MT) G *= 2;
+    while (G * 2 * npf <= MT) G *= 2;
     if (G == 1) {
-      for (int o = tid; o < npo; o += MT) {
+      for (int o = tid; o < P * nt; o += MT) {
         const int p = o / nt, tt = o % nt;
         const double* gp = Gs + p * MT;
         double s0 = 0.0, s1 = 0.0;
@@ -403,22 +405,21 @@ __global__ void __launch_bounds__(MT) modal_scan_kernel(ScanArgs a) {
         a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = s0 + s1;
       }
     } else {
-      const int o = tid % npo, g = tid / npo, nb = MT / G;
-      if (g < G) {
-        const int p = o / nt, tt = o % nt;
+      const int o = tid % npf, g = tid / npf, nb = MT / G;
+      const int p = o / TS, tt = o % TS;
+      if (g < G && tt < nt) {
         const double* gp = Gs + p * MT;
         double s0 = 0.0, s1 = 0.0;
         for (int n = g * nb; n < (g + 1) * nb; n += 2) {
           s0 = fma(gp[n], X[n * (TS + 1) + tt], s0);
           s1 = fma(gp[n + 1], X[(n + 1) * (TS + 1) + tt], s1);
         }
-        gred[g * npo + o] = s0 + s1;
+        gred[g * npf + o] = s0 + s1;
       }
       __syncthreads();
-      if (tid < npo) {
-        const int p = tid / nt, tt = tid % nt;
+      if (tid < npf && tt < nt) {
         double v = gred[tid];
-        for (int gg = 1; gg < G; ++gg) v += gred[gg * npo + tid];
+        for (int gg = 1; gg < G; ++gg) v += gred[gg * npf + tid];
         a.partial[(((int64_t)r * gridDim.x + blockIdx.x) * a.kn + (t0 - a.k0) + tt) * P + p] = v;
       }
     }
