@@ -444,7 +444,6 @@ constexpr int NW_THREADS = (2 + NW_EPI_WARPS) * 32;
 constexpr int NW_NMAX = 32;
 constexpr int NW_SET_COLS = NACC * NW_NMAX;             // 192 columns per accumulator set
 constexpr int NW_TMEM_COLS = 512;
-constexpr int NW_B_BYTES = OZ_S * NW_NMAX * TK * 2;     // 16 KB
 constexpr int NW_MAX_STAGES = 3;
 constexpr int NW_COPIES = 8;                            // bulk copies per A stage (8 KB each)
 // stages of A_BYTES + 8 nmma 64 bytes: three of 72 KB for nmma = 16, two of 80 KB for 32

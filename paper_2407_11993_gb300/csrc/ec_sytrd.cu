@@ -415,75 +415,9 @@ __global__ void __launch_bounds__(256) latrd_dots_kernel(int64_t n, int64_t j, c
   }
 }
 
-// Symmetric product over the trailing lower triangle, one CTA per 64 x 64 tile (I, J),
-// I >= J, of A22 = A[s0:, s0:] (s0 = j + 1, m = n - s0):
-//   prow[J][r] = sum_{c in J} A[r, c] v[c]   for r in block I  (diagonal tile: c <= r)
-//   pcol[I][c] = sum_{r in I} A[r, c] v[r]   for c in block J  (diagonal tile: r > c)
-// (partials indexed by block, stride mp), so that for a row r of block I
-//   (A22 v)[r] = sum_{J <= I} prow[J][r] + sum_{I' >= I} pcol[I'][r],
-// summed in that fixed order by p_latrd_kernel.  Each element is read once and used
-// for both of its contributions.
-__global__ void __launch_bounds__(256) symv_tile_kernel(int64_t n, const double* A, int64_t lda,
-                                                        int64_t j, const double* v, double* prow,
-                                                        double* pcol, int64_t mp) {
-  __shared__ double As[64][65];     // As[c][r] = A[row0 + r, col0 + c]
-  __shared__ double vr[64], vc[64];
-  __shared__ double red[4][64];
-  int64_t I, J;
-  {
-    const int64_t t = blockIdx.x;
-    int64_t q = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while (q * (q + 1) / 2 > t) --q;
-    while ((q + 1) * (q + 2) / 2 <= t) ++q;
-    I = q;
-    J = t - q * (q + 1) / 2;
-  }
-  const int64_t s0 = j + 1, m = n - s0;
-  const int64_t r0 = I * 64, c0 = J * 64;      // offsets inside A22
-  const int tid = threadIdx.x;
-  for (int q = tid; q < 64 * 64; q += 256) {
-    const int rr = q & 63, cc = q >> 6;
-    const int64_t r = r0 + rr, c = c0 + cc;
-    double a = 0.0;
-    if (r < m && c < m && (I != J || rr >= cc)) a = A[(s0 + r) + (s0 + c) * lda];
-    As[cc][rr] = a;
-  }
-  if (tid < 64) {
-    vr[tid] = (r0 + tid < m) ? v[s0 + r0 + tid] : 0.0;
-    vc[tid] = (c0 + tid < m) ? v[s0 + c0 + tid] : 0.0;
-  }
-  __syncthreads();
-  const int lo = tid & 63, qt = tid >> 6;
-  // row part: thread (row lo, quarter qt of the columns)
-  double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-  for (int cc = 0; cc < 16; cc += 2) {
-    a0 = fma(As[qt * 16 + cc][lo], vc[qt * 16 + cc], a0);
-    a1 = fma(As[qt * 16 + cc + 1][lo], vc[qt * 16 + cc + 1], a1);
-  }
-  red[qt][lo] = a0 + a1;
-  __syncthreads();
-  if (tid < 64 && r0 + tid < m)
-    prow[J * mp + r0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-  __syncthreads();
-  // column part: thread (column lo, quarter qt of the rows); the diagonal tile's
-  // diagonal is counted once (in the row part)
-  double b0 = 0.0, b1 = 0.0;
-#pragma unroll
-  for (int rr = 0; rr < 16; rr += 2) {
-    const int ra = qt * 16 + rr, rb = ra + 1;
-    const double xa = (I != J || ra > lo) ? As[lo][ra] : 0.0;
-    const double xb = (I != J || rb > lo) ? As[lo][rb] : 0.0;
-    b0 = fma(xa, vr[ra], b0);
-    b1 = fma(xb, vr[rb], b1);
-  }
-  red[qt][lo] = b0 + b1;
-  __syncthreads();
-  if (tid < 64 && c0 + tid < m)
-    pcol[I * mp + c0 + tid] = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-}
-
-// Column-strip form of the same product: CTA (k, J) takes the tiles (I, J) with
+// Symmetric product over the trailing lower triangle A22 = A[s0:, s0:] (s0 = j + 1,
+// m = n - s0), each element read once and used for both of its contributions, in
+// 64 x 64 tiles (I, J), I >= J, by column strips: CTA (k, J) takes the tiles (I, J) with
 // I in [J + k SEG, J + (k+1) SEG) of the 64-column strip J, loads each tile with
 // asynchronous 8-byte copies while the previous one is used, writes the row part of
 // every tile (prow[J][rows of I]) and keeps the column part of its whole segment in
