@@ -705,7 +705,8 @@ def main():
                          "products in compensated FP32 and report its time and errors "
                          "(about 4.5 more minutes at N=65536)")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the plain step's FP32-pair precision variant")
+                    help="skip the precision variants (plain FP32-pair factor; modal FP32 pair, "
+                         "FP32, split BF16 and BF16 products)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
