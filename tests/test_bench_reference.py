@@ -33,3 +33,23 @@ def test_clock_summary_reads_throttle_reasons():
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["sw_power_cap"]
     assert bench.ClockSampler.summarize([])["sm_mhz"] is None
+
+
+def test_stated_error_helpers():
+    """The bench's per-output errors: per probe trace (rows), per snapshot (columns), and
+    the functional scale max |dy| / (||C_p|| max ||I||), checked on hand-made arrays."""
+    import numpy as np
+    import bench
+    ref = np.array([[3.0, 4.0], [1e-6, 0.0]])          # two probe traces
+    got = ref + np.array([[0.0, 5e-3], [1e-8, 0.0]])
+    # trace 0: 5e-3 / 5 = 1e-3; trace 1: 1e-8 / 1e-6 = 1e-2 -> the small trace decides
+    assert abs(bench._per_trace(got, ref) - 1e-2) < 1e-12
+    snaps = np.array([[1.0, 0.0], [0.0, 2.0]])          # two snapshots (columns)
+    s2 = snaps + np.array([[1e-3, 0.0], [0.0, 0.0]])
+    assert abs(bench._per_snapshot(s2, snaps) - 1e-3) < 1e-15
+    assert bench._per_snapshot(np.zeros((2, 0)), np.zeros((2, 0))) is None
+    C = np.array([[2.0, 0.0], [0.0, 1.0]])
+    # max |dy| per probe: 5e-3 and 1e-8; ||C_p|| = 2 and 1; max ||I|| = 2: on this scale
+    # the small trace's error is negligible
+    f = bench._functional(got, ref, C, snaps)
+    assert abs(f - max(5e-3 / (2 * 2), 1e-8 / (1 * 2))) < 1e-15
