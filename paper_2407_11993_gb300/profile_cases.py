@@ -199,7 +199,8 @@ def gemm_case(args) -> dict:
     def call():
         rc = eddy.lib().ec_gemm_f64_emulated(0, 0, M, N, K, 1.0, c_void_p(A.data_ptr()), M,
                                              c_void_p(B.data_ptr()), K, 0.0,
-                                             c_void_p(C.data_ptr()), M, 0, None)
+                                             c_void_p(C.data_ptr()), M,
+                                             2 if args.kept else 0, None)
         if rc != 0:
             raise RuntimeError(f"ec_gemm_f64_emulated: {rc}")
 
@@ -213,7 +214,7 @@ def gemm_case(args) -> dict:
         best = min(best, time.perf_counter() - t0)
     ref = A.t() @ B.t()
     err = float(((C.t() - ref).abs() / (A.t().abs() @ B.t().abs())).max())
-    return {"M": M, "N": N, "K": K, "best_call_s": best,
+    return {"M": M, "N": N, "K": K, "kept": bool(args.kept), "best_call_s": best,
             "fp64_equiv_tflops": 2.0 * M * N * K / best / 1e12, "max_err_rel_absAB": err}
 
 
@@ -306,6 +307,8 @@ def main() -> None:
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="one FP64-accurate tensor-core product of this shape")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--kept", action="store_true",
+                    help="--gemm through the kept-slice path (A cut once per call, stream-K)")
     ap.add_argument("--compare-setup", action="store_true",
                     help="modal setup with FP64 vs compensated-FP32 symmetric products")
     ap.add_argument("--grad-config5", action="store_true",
