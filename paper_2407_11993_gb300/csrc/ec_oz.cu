@@ -433,8 +433,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 // C (M x N, N <= 32) = A B with A's slices cut once (OzSplit) and K long: the work is
 // the list of (row tile, 192-long K chunk) items in tile-major order, cut into equal
 // contiguous ranges, one per CTA, so every SM streams the same share of A's slices in a
-// single launch.  Each chunk's six accumulators go to one of two TMEM sets (the MMAs of
-// the next chunk run while the epilogue folds this one); the epilogue turns every chunk
+// single launch.  Per A slice s and 16-long K step one MMA multiplies it by B's slices
+// t = 0 .. 7 - s at once: B's slices lie in shared memory in reverse order (slot p holds
+// slice 7 - p), so the window of slots s .. 7 is N = (8 - s) nmma wide and its column
+// block j always holds diagonal s + t = 7 - j.  Eight MMAs per K step (N = 8 nmma down to
+// nmma) do the 36 slice pairs' work; a chunk's eight diagonal accumulators go to one of
+// two TMEM sets (the MMAs of the next chunk run while the epilogue folds this one).  The
+// first MMA of a chunk (s = 0) spans every block and overwrites it.  The epilogue turns every chunk
 // into binary64 (exact integer, one rounding) and sums the chunks of a tile in FP64
 // registers.  A tile whose chunks all lie in one range is stored; a tile cut between two
 // ranges is added by both CTAs into the zeroed C with atomicAdd -- two addends onto zero,
@@ -442,10 +447,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const __grid_con
 constexpr int NW_EPI_WARPS = 4;                         // one per TMEM lane quarter
 constexpr int NW_THREADS = (2 + NW_EPI_WARPS) * 32;
 constexpr int NW_NMAX = 32;
-constexpr int NW_SET_COLS = NACC * NW_NMAX;             // 192 columns per accumulator set
+constexpr int NW_DIAGS = OZ_DMAX + 1;                   // diagonals s + t = 0 .. 7
+constexpr int NW_SET_COLS = NW_DIAGS * NW_NMAX;         // 256 columns per accumulator set
 constexpr int NW_TMEM_COLS = 512;
 constexpr int NW_MAX_STAGES = 3;
 constexpr int NW_COPIES = 8;                            // bulk copies per A stage (8 KB each)
+static_assert(NW_COPIES == OZ_S, "one copy lane per B slice");
 // stages of A_BYTES + 8 nmma 64 bytes: three of 72 KB for nmma = 16, two of 80 KB for 32
 __host__ __device__ constexpr int nw_stage_bytes(int nmma) { return A_BYTES + OZ_S * nmma * TK * 2; }
 __host__ __device__ constexpr int nw_stages(int nmma) { return nmma <= 16 ? 3 : 2; }
@@ -543,19 +550,19 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
         uint8_t* sb = sa + A_BYTES;
         // A: one 64 KB block, already in the swizzled shared-memory image
         const uint8_t* src = a.Ablk + ((int64_t)tile * a.nkb + kbeg / TK + kb) * (int64_t)A_BYTES;
-        if (lane < NW_COPIES)
+        if (lane < NW_COPIES) {
           dev::bulk_g2s(sa + lane * (A_BYTES / NW_COPIES), src + lane * (A_BYTES / NW_COPIES),
                         A_BYTES / NW_COPIES, &full_bar[q]);
-        if (lane == 0) {
-          tma_load_3d(sb, &mapB, &full_bar[q], kbeg + kb * TK, 0, 0);
-          *(volatile int*)&issued = (int)(it + 1);
+          // B slice t = lane into slot 7 - t
+          tma_load_3d(sb + (OZ_S - 1 - lane) * (b_bytes / OZ_S), &mapB, &full_bar[q],
+                      kbeg + kb * TK, 0, lane);
         }
+        if (lane == 0) *(volatile int*)&issued = (int)(it + 1);
         __syncwarp();
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_for(NMMA);
       constexpr uint32_t b_slice = (uint32_t)(NMMA * TK * 2);
       uint32_t it = 0;
       bool ok = true;
@@ -588,21 +595,15 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
           const uint64_t dA0 = smem_desc(sa), dB0 = smem_desc(sa + A_BYTES);
           const uint32_t kb0 = kb == 0 ? 0u : 1u;
 #pragma unroll
-          for (int d = 0; d <= OZ_DMAX; ++d) {
-            const int acc = d < OZ_EXACT ? d : OZ_EXACT;
-            const uint32_t tacc = tset + (uint32_t)(acc * NMMA);
+          for (int si = 0; si < OZ_S; ++si) {
+            // slots si .. 7 hold B slices 7 - si .. 0: diagonal 7 - j in column block j
+            const uint64_t da = dA0 + (uint64_t)((si * A_SLICE) >> 4);
+            const uint64_t db = dB0 + (uint64_t)((si * b_slice) >> 4);
 #pragma unroll
-            for (int si = 0; si <= d; ++si) {
-              const int ti = d - si;
-              if (si >= OZ_S || ti >= OZ_S) continue;
-              const uint64_t da = dA0 + (uint64_t)((si * A_SLICE) >> 4);
-              const uint64_t db = dB0 + (uint64_t)((ti * b_slice) >> 4);
-#pragma unroll
-              for (int kk = 0; kk < TK / 16; ++kk) {
-                // the first product into each accumulator (first K block) overwrites it
-                const uint32_t accum = (kk == 0 && si == 0 && d <= OZ_EXACT) ? kb0 : 1u;
-                mma_bf16(tacc, da + 2 * kk, db + 2 * kk, idesc, accum);
-              }
+            for (int kk = 0; kk < TK / 16; ++kk) {
+              // the chunk's first MMA (slice 0 spans all eight blocks) overwrites the set
+              const uint32_t accum = (kk == 0 && si == 0) ? kb0 : 1u;
+              mma_bf16(tset, da + 2 * kk, db + 2 * kk, idesc_for((OZ_S - si) * NMMA), accum);
             }
           }
           mma_commit(&empty_bar[q]);
@@ -634,10 +635,12 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
       const int erow = row_ok ? a.ea[row] - 56 : 0;
 #pragma unroll
       for (int g = 0; g < NMMA / 16; ++g) {
-        uint32_t r[NACC][16];
+        // r[d]: diagonal d, in column block 7 - d of the set
+        uint32_t r[NW_DIAGS][16];
 #pragma unroll
-        for (int q = 0; q < NACC; ++q)
-          tmem_ld16(lane_base + (uint32_t)(set * NW_SET_COLS + q * NMMA + g * 16), r[q]);
+        for (int d = 0; d < NW_DIAGS; ++d)
+          tmem_ld16(lane_base + (uint32_t)(set * NW_SET_COLS + (OZ_DMAX - d) * NMMA + g * 16),
+                    r[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -647,7 +650,10 @@ __global__ void __launch_bounds__(NW_THREADS, 1) oz_narrow_kernel(
           const int i2v = __float2int_rn(__uint_as_float(r[2][j]) * 65536.0f);
           const int i3v = __float2int_rn(__uint_as_float(r[3][j]) * 16777216.0f);
           const int i4v = __float2int_rn(__uint_as_float(r[4][j]) * 4294967296.0f);
-          const int igv = __float2int_rn(__uint_as_float(r[OZ_EXACT][j]) * 1099511627776.0f);
+          // diagonals 5 .. 7 summed in FP32 first, as one shared accumulator would
+          const float tail = __uint_as_float(r[5][j]) +
+                             (__uint_as_float(r[6][j]) + __uint_as_float(r[7][j]));
+          const int igv = __float2int_rn(tail * 1099511627776.0f);
           int64_t X = (int64_t)(i0v * 256 + i1v) * 4294967296ll;
           X += (int64_t)i2v * (1 << 24);
           X += (int64_t)i3v * (1 << 16);
@@ -794,12 +800,12 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 // 3-D map over the slices of an R x K operand: (k, row, slice), box TK x box_rows x 8;
 // consecutive slices lie Rs * ldk elements apart (Rs >= R).
 bool make_slice_map_ld(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
-                       int64_t ldk, int64_t Rs, int box_rows) {
+                       int64_t ldk, int64_t Rs, int box_rows, int box_slices = OZ_S) {
   EncodeTiledFn fn = (EncodeTiledFn)tensor_map_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)OZ_S};
   cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(Rs * ldk) * 2};
-  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+  cuuint32_t box[3] = {(cuuint32_t)TK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
   cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -807,8 +813,8 @@ bool make_slice_map_ld(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, i
 }
 
 bool make_slice_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t R, int64_t K,
-                    int64_t ldk, int box_rows) {
-  return make_slice_map_ld(map, base, R, K, ldk, R, box_rows);
+                    int64_t ldk, int box_rows, int box_slices = OZ_S) {
+  return make_slice_map_ld(map, base, R, K, ldk, R, box_rows, box_slices);
 }
 
 ec_status grow_ws(OzWork* w, int64_t slice_elems, int64_t rows) {
@@ -1043,7 +1049,7 @@ ec_status oz_gemm_presplit(cudaStream_t s, const OzSplit& a, int64_t kuse, Op tb
     split(s, nj, kuse, B + j0 * brs, brs, bks, w->maxb, w->slices, ldk, w->exps);
     const int nm = nmma_for(nj);
     CUtensorMap mb;
-    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, nm)) return EC_ERR_CUDA;
+    if (!make_slice_map(&mb, w->slices, nj, kuse, ldk, nm, 1)) return EC_ERR_CUDA;
     NarrowArgs na{};
     na.M = (int)a.R;
     na.N = (int)nj;
