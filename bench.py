@@ -258,6 +258,30 @@ def _functional(a, b, C, snaps):
     return float((np.abs(a - b).max(axis=1) / (cn * Inorm)).max())
 
 
+def _snapshot_view(run_ms, scan_ms, chunks, n0, nsnap, hbm_gbs):
+    """The modal chunk's time outside the scan against the bytes of U's kept slices.
+
+    From N_0 = 4096 on, an FP64 modal run reconstructs its nsnap snapshots per chunk from
+    U's kept tensor-core slices (16 B per entry of U, read once per group of up to 32
+    columns).  Everything of the chunk that is not the scan (the product, its operand split
+    and zeroing, the probe reduction) is charged to it, so the rate is a lower bound on the
+    product's own."""
+    if nsnap <= 0 or chunks <= 0 or n0 < 4096:
+        return None
+    ms = (run_ms - scan_ms) / chunks
+    if ms <= 0:
+        return None
+    groups = -(-nsnap // 32)
+    nbytes = 16.0 * n0 * n0 * groups
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": "oz_narrow_kernel (snapshots from U's kept slices)",
+            "snapshots_per_chunk": nsnap, "bytes_per_chunk": nbytes,
+            "ms_per_chunk_outside_scan": ms, "achieved_lower_bound": gbs, "peak": hbm_gbs,
+            "unit": "GB/s", "frac_lower_bound": gbs / hbm_gbs,
+            "note": "modal run time minus scan time per chunk (library CUDA events), "
+                    "against 16 n0^2 bytes per group of <= 32 snapshot columns"}
+
+
 def our_arm(args) -> None:
     import numpy as np
     import torch
@@ -430,6 +454,10 @@ def our_arm(args) -> None:
                                       fp["fp64_fma_tflops"],
                               "peak_note": "FP64 FMA loop over all SMs, measured in this run "
                                            "(paper_2407_11993_gb300.peaks)"}}
+    sv = _snapshot_view(total("run_ms", "modal"), total("scan_ms", "modal"), args.steps, n0,
+                        nsn, hbm)
+    if sv is not None:
+        roofline["modal_snapshot_view"] = sv
     traffic_path = os.path.join(ROOT, "profiles", "tile_trmv_n8192.md")
     try:
         tv = {}

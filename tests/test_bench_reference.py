@@ -53,3 +53,22 @@ def test_stated_error_helpers():
     # the small trace's error is negligible
     f = bench._functional(got, ref, C, snaps)
     assert abs(f - max(5e-3 / (2 * 2), 1e-8 / (1 * 2))) < 1e-15
+
+
+def test_snapshot_view():
+    """The modal snapshot product's rate from the chunk time outside the scan: bytes of
+    U's kept slices (16 n0^2 per group of up to 32 columns) over (run - scan) per chunk;
+    none below the kept-slice size or without snapshots."""
+    import bench
+    # 10 chunks, 130 ms run, 30 ms scan -> 10 ms per chunk; n0 = 8192, 4 snapshots:
+    # 16 * 8192^2 B = 1.073741824 GB in 10 ms = 107.3741824 GB/s
+    v = bench._snapshot_view(130.0, 30.0, 10, 8192, 4, 1000.0)
+    assert abs(v["ms_per_chunk_outside_scan"] - 10.0) < 1e-12
+    assert abs(v["achieved_lower_bound"] - 107.3741824) < 1e-9
+    assert abs(v["frac_lower_bound"] - 0.1073741824) < 1e-12
+    # 33 snapshots are two column groups: twice the bytes, twice the rate
+    v2 = bench._snapshot_view(130.0, 30.0, 10, 8192, 33, 1000.0)
+    assert abs(v2["achieved_lower_bound"] - 2 * 107.3741824) < 1e-9
+    assert bench._snapshot_view(130.0, 30.0, 10, 4095, 4, 1000.0) is None
+    assert bench._snapshot_view(130.0, 30.0, 10, 8192, 0, 1000.0) is None
+    assert bench._snapshot_view(30.0, 30.0, 10, 8192, 4, 1000.0) is None
