@@ -95,7 +95,9 @@ OZ_HD int64_t f64_to_fixed64(uint64_t bits, int e) {
   const int shift = ex + 64 - e;              // F = m * 2^shift
   uint64_t mag;
   if (shift >= 0) {
-    mag = shift > 10 ? 0 : (m << shift);      // shift <= 10 for |a| < 2^(e-1); guard anyway
+    // |a| < 2^(e-1) keeps shift <= 10 for a normal a (m >= 2^52) and <= 11 for a
+    // subnormal one (m < 2^52, a row whose largest entry is subnormal): |F| < 2^63 either way
+    mag = shift > 11 ? 0 : (m << shift);
   } else if (shift <= -64) {
     mag = 0;
   } else {
