@@ -275,9 +275,9 @@ def _snapshot_view(run_ms, scan_ms, chunks, n0, nsnap, hbm_gbs):
     nbytes = 16.0 * n0 * n0 * groups
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"kernel": "oz_narrow_kernel (snapshots from U's kept slices)",
-            "snapshots_per_chunk": nsnap, "bytes_per_chunk": nbytes,
-            "ms_per_chunk_outside_scan": ms, "achieved_lower_bound": gbs, "peak": hbm_gbs,
-            "unit": "GB/s", "frac_lower_bound": gbs / hbm_gbs,
+            "snapshots_per_chunk": int(nsnap), "bytes_per_chunk": float(nbytes),
+            "ms_per_chunk_outside_scan": float(ms), "achieved_lower_bound": float(gbs),
+            "peak": float(hbm_gbs), "unit": "GB/s", "frac_lower_bound": float(gbs / hbm_gbs),
             "note": "modal run time minus scan time per chunk (library CUDA events), "
                     "against 16 n0^2 bytes per group of <= 32 snapshot columns"}
 
