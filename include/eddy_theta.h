@@ -374,10 +374,11 @@ EC_API ec_status ec_gemm_bf16(int64_t M, int64_t N, int64_t K, const double* A, 
  * 8-bit integer slices held exactly in BF16; the slice products (tcgen05, FP32
  * accumulation kept exact per slice diagonal) are recombined in integer arithmetic.
  * Error per entry: below 2^-60 sqrt(K) max_k|op(A)_ik| max_k|op(B)_kj| plus one FP64
- * rounding per 192-long K chunk, comparable to an FP64 GEMM.  Entries must be finite: a NaN or infinity does not propagate as in an FP64
- * GEMM but leaves its row of C (column, for op(B)) meaningless; the setup paths refuse
- * non-finite inputs before they reach this product.  Allocates a temporary workspace
- * (about 16 (M + N) K bytes, in panels beyond 4 GB).  Synchronous. */
+ * rounding per 192-long K chunk, comparable to an FP64 GEMM.  Entries must be finite: a
+ * NaN or infinity does not propagate as in an FP64 GEMM but leaves its row of C (column,
+ * for op(B)) meaningless; the setup paths refuse non-finite inputs before they reach this
+ * product.  Allocates a temporary workspace (about 16 (M + N) K bytes, in panels beyond
+ * 4 GB).  Synchronous. */
 EC_API ec_status ec_gemm_f64_emulated(int ta, int tb, int64_t M, int64_t N, int64_t K,
                                       double alpha, const double* A, int64_t lda, const double* B,
                                       int64_t ldb, double beta, double* C, int64_t ldc, int lower,
