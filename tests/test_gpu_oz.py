@@ -89,6 +89,34 @@ def test_alpha_beta_and_lower_triangle(eddy):
     assert np.all(np.abs(C2 - ex2) <= (K + 2) * U * ab2)
 
 
+@pytest.mark.parametrize("kept", [False, True])
+def test_subnormal_rows_and_columns(eddy, kept):
+    """Rows of A (and a column of B) whose largest entry is subnormal keep every bit of
+    their fixed-point image (mantissa shift 11 against the row exponent -1021): their
+    products meet the per-row / per-column bound like any other.  Against a large column
+    the subnormal rows give normal results, which a flushed row would leave at zero; the
+    results that fall in the subnormal range carry their final rounding (a few units of
+    2^-1074), hence the absolute slack."""
+    import torch
+    rng = np.random.default_rng(41)
+    M, N, K = 300, 20, 257
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    sub = [3, 150, 299]
+    A[sub] *= 1e-310                            # subnormal rows
+    B[:, 7] *= 1e-310                           # a subnormal column
+    B[:, 3] *= 1e12                             # a large column
+    C = eddy.gemm_f64_emulated(_cuda(A), _cuda(B), kept_slices=kept).cpu().numpy()
+    torch.cuda.synchronize()
+    ex = _exact(A, B)
+    rowmax = np.abs(A).max(axis=1)[:, None]
+    colmax = np.abs(B).max(axis=0)[None, :]
+    err = np.abs(C - ex).astype(np.float64)
+    assert np.all(err <= 2.0 ** -50 * np.sqrt(K) * rowmax * colmax + 1e-320)
+    for i in sub:
+        assert abs(C[i, 3]) > 2.0 ** -1022
+
+
 def test_wide_dynamic_range(eddy):
     """Entries spread over 12 decades inside rows and columns: the error is relative to
     each row's and column's largest entry (the split's scale)."""
